@@ -1,0 +1,252 @@
+/*
+ * fastergs.h -- C ABI of libfastergs.so: one 3D Gaussian Splatting training
+ * step on an NVIDIA GB300 (sm_103a), as described by Faster-GS (arXiv
+ * 2602.09999): preprocess, duplicate + radix sort + tile ranges, tile
+ * blending, L1 + D-SSIM loss, blend backward, preprocess backward, Adam.
+ *
+ * Conventions shared by every entry point
+ *  - All data pointers are DEVICE pointers unless a comment says "host".
+ *  - The caller owns every buffer: parameters, gradients, Adam moments,
+ *    images, targets and the workspace.  The library never allocates,
+ *    frees or synchronises, except fgs_get_error (which synchronises).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).
+ *    Every call is asynchronous on it and may be captured in a CUDA graph
+ *    as long as the view sizes stay the same between replays.
+ *  - Return value: FGS_OK (0) or a negative FGS_ERR_* code for an error the
+ *    host can see (bad pointer, shape, degree, dtype, workspace size, launch
+ *    failure).  Errors found on the device (instance capacity exceeded)
+ *    set sticky bits in the workspace header read by fgs_get_error; no
+ *    kernel traps.
+ *  - Gradients are overwritten, never accumulated.
+ *  - Layouts are row-major; a [n,3] array is n consecutive triples.
+ *
+ * Gaussian parameters (Sec. 2.1 of the paper; fgs_params.data[] order):
+ *   0 means       [n,3]  float32
+ *   1 log_scales  [n,3]  float32   (scale = exp, Sec. 2.1 activations)
+ *   2 quats       [n,4]  float32   (w,x,y,z; normalised in the kernel)
+ *   3 opacity     [n]    float32   (logit; sigmoid in the kernel)
+ *   4 sh_dc       [n,3]  float32 / bf16 / fp16 (SH band 0, separate buffer
+ *                                               as in Sec. 3.2 "Rasterization
+ *                                               Kernel Fusion")
+ *   5 sh_rest     [n,15,3] same dtype as sh_dc (bands 1..3)
+ */
+#ifndef FASTERGS_H
+#define FASTERGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FGS_TILE 16          /* tile edge in pixels (Sec. 3.1) */
+#define FGS_MAX_VIEWS 16     /* views per batched call */
+#define FGS_NUM_GROUPS 6     /* parameter groups in fgs_params */
+
+enum fgs_status {
+    FGS_OK = 0,
+    FGS_ERR_NULL = -1,       /* a required pointer is NULL */
+    FGS_ERR_SHAPE = -2,      /* n <= 0, n too large, or bad image size */
+    FGS_ERR_SH_DEGREE = -3,  /* SH degree outside 0..3 */
+    FGS_ERR_WORKSPACE = -4,  /* workspace layout does not match the call or is too small */
+    FGS_ERR_DTYPE = -5,      /* unsupported storage type for a group */
+    FGS_ERR_CUDA = -6,       /* a kernel launch failed */
+    FGS_ERR_VIEWS = -7,      /* n_views outside 1..FGS_MAX_VIEWS */
+    FGS_ERR_ALIGN = -8,      /* a pointer is not 16-byte aligned */
+    FGS_ERR_ARG = -9         /* another argument is out of range */
+};
+
+/* Sticky bits set on the device, read by fgs_get_error. */
+enum fgs_device_flags {
+    FGS_FLAG_CAPACITY = 1u   /* instances exceeded k_max; the extra ones were dropped */
+};
+
+enum fgs_dtype { FGS_F32 = 0, FGS_BF16 = 1, FGS_F16 = 2 };
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).
+ * R: world->camera rotation, row-major; t: translation (Eq. 1, W = [R|t]).
+ * fx, fy, cx, cy: intrinsics in pixels (Eq. 1-2; Suppl. B.1 uses the
+ * intrinsics directly instead of a projection matrix).  Pixel (u, v) is
+ * sampled at (u + 0.5, v + 0.5).  near_plane: Gaussians with camera depth
+ * <= near_plane are not rendered.  cam_pos: camera centre in world space,
+ * used for the SH view direction. */
+typedef struct fgs_camera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_plane;
+    float cam_pos[3];
+} fgs_camera;
+
+/* One tensor per parameter group (order above), each with its storage
+ * type.  Used for parameters, gradients (always FGS_F32) and the two Adam
+ * moments. */
+typedef struct fgs_params {
+    int64_t n;
+    void *data[FGS_NUM_GROUPS];
+    int32_t dtype[FGS_NUM_GROUPS];
+} fgs_params;
+
+/* Sub-arrays of the caller-allocated workspace (byte offsets from its
+ * start; every offset is 256-byte aligned).  Offset 0 always holds the
+ * header: uint32 flags, uint32 reserved, uint64 instance count of the last
+ * forward (may exceed k_max), uint32 counters. */
+enum fgs_ws_slot {
+    FGS_WS_HEADER = 0,
+    FGS_WS_SCREEN,      /* 48-byte records [n_views*n]: float4 (mu2D, conic a, b),
+                           float4 (conic c, o, k = 2 ln(255 o), depth),
+                           float4 (rgb, bits: clamp mask 0..2, visible 3) */
+    FGS_WS_RECT,        /* ushort4 [n_views*n]: tile rectangle x0, y0, x1, y1 (inclusive) */
+    FGS_WS_LOCAL_OFF,   /* uint32 [n_views*n]: CTA-local exclusive prefix of tile counts */
+    FGS_WS_BLOCK_SUM,   /* uint32 [n_views*ceil(n/256)+1]: prefix of CTA totals */
+    FGS_WS_KEYS,        /* uint64 [k_max]: (global tile << 32) | depth bits */
+    FGS_WS_VALS,        /* uint32 [k_max]: Gaussian index */
+    FGS_WS_KEYS_ALT,    /* uint64 [k_max]: sort ping-pong buffer */
+    FGS_WS_VALS_ALT,    /* uint32 [k_max] */
+    FGS_WS_SORT_HIST,   /* uint32 radix histograms */
+    FGS_WS_RANGES,      /* uint2 [total_tiles]: [start, end) of each tile's list */
+    FGS_WS_T_FINAL,     /* float [total_pixels]: final transmittance */
+    FGS_WS_N_CONTRIB,   /* uint32 [total_pixels]: list position of the last blended entry */
+    FGS_WS_SCREEN_GRAD, /* 48-byte records [n_views*n]: float4 dL/d(mu2D, conic a, b),
+                           float4 dL/d(conic c, o, r, g), float4 (dL/db, 0, 0, 0) */
+    FGS_WS_LOSS_MAPS,   /* float [9*total_pixels]: SSIM partial-derivative maps */
+    FGS_WS_LOSS_PART,   /* double [loss blocks*2]: per-CTA L1 / SSIM sums */
+    FGS_WS_NUM_SLOTS
+};
+
+typedef struct fgs_workspace_layout {
+    size_t total_bytes;
+    size_t offset[FGS_WS_NUM_SLOTS];
+    size_t bytes[FGS_WS_NUM_SLOTS];
+    int64_t n;
+    int64_t k_max;
+    int32_t n_views;
+    int32_t total_tiles;
+    int64_t total_pixels;
+    int32_t sort_bits;       /* key bits the radix sort orders */
+    int32_t sorted_in_alt;   /* 1: sorted keys/values end in the *_ALT slots */
+} fgs_workspace_layout;
+
+/* Workspace size and layout for n Gaussians, n_views host cameras and an
+ * instance capacity k_max ((Gaussian, tile) pairs summed over all views;
+ * the paper's model is about 8 tiles per visible Gaussian, Suppl. B.2).
+ * Pure host arithmetic.  The caller allocates at least total_bytes of
+ * 256-byte aligned device memory and passes the same layout (host struct)
+ * to the forward, loss and backward calls that share the workspace; each
+ * call checks it against its cameras.  Returns FGS_ERR_* on bad arguments
+ * (n outside 1..2^31-1, n_views outside 1..FGS_MAX_VIEWS, a camera size
+ * outside 1..65535, k_max outside 0..2^31-1). */
+int fgs_workspace_size(int64_t n, const fgs_camera *cams_host, int32_t n_views, int64_t k_max,
+                       fgs_workspace_layout *out_host);
+
+/* Forward pass for layout->n_views views (Eq. 1-4; Sec. 3.2 bounds, culling and
+ * sorting; Suppl. B.1 clamp, early stop and degeneracy tests):
+ *   preprocess -> per-CTA scan -> duplicate into (tile << 32 | depth) keys
+ *   -> LSD radix sort -> tile ranges -> front-to-back blending.
+ * cams_host gives the view sizes (grids and layout); cams_device holds the
+ * same n_views cameras in device memory and is what the kernels read, so a
+ * captured graph may be replayed with new poses.  bg: host float[3]
+ * background colour.  images: float32, the n_views images [3,H_v,W_v]
+ * concatenated.  The rendered colour is not clipped (Suppl. B.1).
+ * The workspace keeps what the backward needs (screen state, sorted lists,
+ * final transmittance, last-contributor positions). */
+int fgs_render_forward(void *ws, const fgs_workspace_layout *layout, const fgs_params *params,
+                       int32_t sh_degree, const fgs_camera *cams_host,
+                       const fgs_camera *cams_device, const float bg[3], float *images,
+                       void *stream);
+
+/* Loss of Suppl. A for each view: (1 - lambda) mean|C - C_gt| + lambda
+ * (1 - mean SSIM) with an 11x11 Gaussian window (sigma 1.5, zero padding,
+ * C1 = 0.01^2, C2 = 0.03^2), averaged over the views.  Writes the scalar
+ * loss (device float, loss_out[0]) and dL/dimages (same layout as images).
+ * Uses the workspace loss slots; call after fgs_render_forward with the
+ * same workspace. */
+int fgs_loss_l1_dssim(void *ws, const fgs_workspace_layout *layout, const fgs_camera *cams_host,
+                      const float *images, const float *targets, float lambda, float *loss_out,
+                      float *dl_dimages, void *stream);
+
+/* Backward pass: zero the screen-gradient accumulators, re-traverse every
+ * tile back to front from each pixel's last contributor (recovering T by
+ * division, Suppl. B.1), reduce per-Gaussian gradients across each warp
+ * and CTA before global atomics, then the chain rule of the preprocessing
+ * (fused activation gradients, Sec. 3.2).  grads: float32 tensors for all
+ * six groups; written for every Gaussian (zero where invisible), summed
+ * over the views.  Needs the workspace of the matching forward. */
+int fgs_render_backward(void *ws, const fgs_workspace_layout *layout, const fgs_params *params,
+                        int32_t sh_degree, const fgs_camera *cams_host,
+                        const fgs_camera *cams_device, const float bg[3],
+                        const float *dl_dimages, const fgs_params *grads, void *stream);
+
+/* Adam (Suppl. A; Sec. 3.3 own fused Adam matching PyTorch): for every
+ * element of every group, m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr/(1-b1^t) * m / (sqrt(v)/sqrt(1-b2^t) + eps), step t >= 1.
+ * As in PyTorch, 1 - b1, 1 - b2 and the bias corrections are formed in
+ * double precision and rounded to float once.
+ * lr: host float[6] in group order.  Every Gaussian is updated, including
+ * those with zero gradient (Sec. 3.3 "Fusing Backward and Optimizer").
+ * params groups 4..5 and both moments may be FGS_BF16 or FGS_F16 (math in
+ * float32, rounded to nearest on store); grads are float32. */
+int fgs_adam_step(const fgs_params *params, const fgs_params *grads, const fgs_params *exp_avg,
+                  const fgs_params *exp_avg_sq, const float lr[6], double beta1, double beta2,
+                  double eps, int32_t step, void *stream);
+
+/* Adam state kept in device memory, so that a captured graph can replay
+ * training steps without host involvement: each fgs_adam_step_device call
+ * first increments `step` on the device, derives the step sizes and the
+ * bias correction, then updates every group. */
+typedef struct fgs_adam_state {
+    double beta1, beta2, eps;  /* exact hyper-parameters (0.999 is not a float32) */
+    float lr[6];            /* base learning rates in group order (Suppl. A) */
+    float lr_means_final;   /* exponential decay target of lr[0] (Suppl. A); <= 0: constant */
+    int32_t decay_steps;    /* steps over which lr[0] decays to lr_means_final */
+    int32_t step;           /* steps taken so far; the call uses step + 1 and stores it */
+    float step_size[6];     /* written by the call: lr_t / (1 - beta1^t) */
+    float inv_bc2_sqrt;     /* written by the call: 1 / sqrt(1 - beta2^t) */
+    float beta1_f, beta2_f, one_minus_beta1_f, one_minus_beta2_f, eps_f; /* written by the call */
+} fgs_adam_state;
+
+/* Same update as fgs_adam_step with the hyper-parameters and step counter
+ * read from (and the counter written back to) `state_device`. */
+int fgs_adam_step_device(const fgs_params *params, const fgs_params *grads,
+                         const fgs_params *exp_avg, const fgs_params *exp_avg_sq,
+                         fgs_adam_state *state_device, void *stream);
+
+/* Stable LSD radix sort of (uint64 key, uint32 value) pairs on the low
+ * `bits` key bits (1..64), 8 bits per pass (Sec. 3.2 "Sorting": a single
+ * radix sort of the combined keys).  keys/vals hold the input; keys_alt /
+ * vals_alt are same-sized scratch.  The sorted result ends in keys/vals
+ * when *result_in_alt (host) is 0, else in the *_alt buffers.  scratch:
+ * device buffer of fgs_sort_scratch_bytes(n) bytes. */
+size_t fgs_sort_scratch_bytes(int64_t n);
+int fgs_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                   int64_t n, int32_t bits, void *scratch, size_t scratch_bytes,
+                   int32_t *result_in_alt, void *stream);
+
+/* Synchronises `stream`, then reads the workspace header: sticky device
+ * flags (FGS_FLAG_*) and the instance count of the last forward.  Either
+ * output pointer may be NULL.  clear != 0 resets the flags afterwards. */
+int fgs_get_error(void *ws, uint32_t *flags_host, uint64_t *instances_host, int32_t clear,
+                  void *stream);
+
+/* Optional per-kernel timing.  After fgs_profile_attach(events, labels,
+ * capacity) with `capacity` caller-created cudaEvent_t handles (host array,
+ * passed as void*) and a host array of as many label pointers, every entry
+ * point records the next event on its stream after each kernel it launches
+ * (and one before its first) and stores a static label naming the kernel;
+ * recording stops when the array is full.  The elapsed time between two
+ * consecutive events is the device time of the kernel the second one
+ * names.  fgs_profile_attach(NULL, NULL, 0) detaches; fgs_profile_count
+ * returns the number of events recorded since the last attach.  Not meant
+ * for stream capture.  Host state: one attachment per process. */
+int fgs_profile_attach(void **events, const char **labels, int32_t capacity);
+int32_t fgs_profile_count(void);
+
+/* Static description of a status code. */
+const char *fgs_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTERGS_H */

@@ -70,7 +70,8 @@ class _Camera(ctypes.Structure):
 
 
 class _Margins(ctypes.Structure):
-    _fields_ = [("rel", ctypes.c_double), ("px", ctypes.c_double),
+    _fields_ = [("rel", ctypes.c_double), ("q_rel", ctypes.c_double),
+                ("pos_rel", ctypes.c_double), ("px", ctypes.c_double),
                 ("t_rel", ctypes.c_double), ("depth_rel", ctypes.c_double),
                 ("tile_culling", ctypes.c_int32)]
 
@@ -78,16 +79,26 @@ class _Margins(ctypes.Structure):
 @dataclass
 class Margins:
     """Decision margins inside which float32 may decide a threshold test the
-    other way (zero = pure FP64 decisions), and the tile-culling switch."""
+    other way (zero = pure FP64 decisions), and the tile-culling switch.
+
+    rel: scalar thresholds (depth vs near plane, |q|, det, opacity, k);
+    q_rel: rounding of a quadratic form relative to the sum of its |terms|;
+    pos_rel: error of mu2D relative to max(1, |mu2D|) in pixels, which moves
+    the quadratic form by about 2 |C d| pos_err; px: rectangle edges;
+    t_rel: transmittance stop test; depth_rel: depth ties."""
     rel: float = 0.0
+    q_rel: float = 0.0
+    pos_rel: float = 0.0
     px: float = 0.0
     t_rel: float = 0.0
     depth_rel: float = 0.0
     tile_culling: int = 1
 
 
-# margins used when the oracle is compared with a float32 implementation
-FP32_MARGINS = Margins(rel=2e-5, px=2e-3, t_rel=1e-4, depth_rel=2e-6)
+# margins used when the oracle is compared with a float32 implementation:
+# roughly 10-30 float32 ulps of each quantity the decision depends on
+FP32_MARGINS = Margins(rel=2e-6, q_rel=1e-6, pos_rel=5e-7, px=2e-3, t_rel=1e-4,
+                       depth_rel=2e-6)
 NO_MARGINS = Margins()
 
 
@@ -124,7 +135,7 @@ def _cam_struct(cam) -> _Camera:
 
 
 def _mg_struct(m: Margins) -> _Margins:
-    return _Margins(m.rel, m.px, m.t_rel, m.depth_rel, int(m.tile_culling))
+    return _Margins(m.rel, m.q_rel, m.pos_rel, m.px, m.t_rel, m.depth_rel, int(m.tile_culling))
 
 
 def _f64(a):

@@ -50,7 +50,9 @@ typedef struct {
 /* Decision margins used to flag results that float32 may legitimately
  * decide the other way (all zero = pure FP64 decisions, nothing flagged). */
 typedef struct {
-    double rel;        /* relative margin for threshold tests */
+    double rel;        /* relative margin for scalar threshold tests */
+    double q_rel;      /* rounding of a quadratic form, relative to the sum of |terms| */
+    double pos_rel;    /* error of mu2D relative to max(1, |mu2D|) (pixels) */
     double px;         /* absolute margin (pixels) for rectangle edges */
     double t_rel;      /* relative margin for the transmittance stop test */
     double depth_rel;  /* relative depth difference treated as a tie */
@@ -348,12 +350,13 @@ static void gauss_forward(const orc_camera *cam, int sh_degree, int64_t i,
 /* Minimum of q(d) = d^T C d over the box [x0,x1] x [y0,y1] of offsets d,
  * for a positive definite C = [[a, b], [b, c]].  Zero if the origin is
  * inside; otherwise the minimum over the four edges, each a clamped 1D
- * quadratic.  Also returns the magnitude of the terms at the minimiser. */
+ * quadratic.  Also returns, at the minimiser, the sum of |terms| and
+ * |C d| (1-norm), which size the float32 error of the value. */
 static double box_qmin(double a, double b, double c, double x0, double x1, double y0, double y1,
-                       double *mag)
+                       double *mag, double *grad)
 {
-    if (x0 <= 0.0 && 0.0 <= x1 && y0 <= 0.0 && 0.0 <= y1) { *mag = 0.0; return 0.0; }
-    double best = INFINITY, bmag = 0.0;
+    if (x0 <= 0.0 && 0.0 <= x1 && y0 <= 0.0 && 0.0 <= y1) { *mag = 0.0; *grad = 0.0; return 0.0; }
+    double best = INFINITY, bmag = 0.0, bgrad = 0.0;
     const double xs[2] = {x0, x1}, ys[2] = {y0, y1};
     for (int e = 0; e < 2; ++e) {
         /* edge x = xs[e]: minimise over y */
@@ -362,16 +365,25 @@ static double box_qmin(double a, double b, double c, double x0, double x1, doubl
         if (Yv < y0) Yv = y0;
         if (Yv > y1) Yv = y1;
         double q = a * X * X + 2.0 * b * X * Yv + c * Yv * Yv;
-        if (q < best) { best = q; bmag = fabs(a * X * X) + fabs(2.0 * b * X * Yv) + fabs(c * Yv * Yv); }
+        if (q < best) {
+            best = q;
+            bmag = fabs(a * X * X) + fabs(2.0 * b * X * Yv) + fabs(c * Yv * Yv);
+            bgrad = fabs(a * X + b * Yv) + fabs(b * X + c * Yv);
+        }
         /* edge y = ys[e]: minimise over x */
         double Yf = ys[e];
         double Xv = -b * Yf / a;
         if (Xv < x0) Xv = x0;
         if (Xv > x1) Xv = x1;
         q = a * Xv * Xv + 2.0 * b * Xv * Yf + c * Yf * Yf;
-        if (q < best) { best = q; bmag = fabs(a * Xv * Xv) + fabs(2.0 * b * Xv * Yf) + fabs(c * Yf * Yf); }
+        if (q < best) {
+            best = q;
+            bmag = fabs(a * Xv * Xv) + fabs(2.0 * b * Xv * Yf) + fabs(c * Yf * Yf);
+            bgrad = fabs(a * Xv + b * Yf) + fabs(b * Xv + c * Yf);
+        }
     }
     *mag = bmag;
+    *grad = bgrad;
     return best;
 }
 
@@ -388,9 +400,9 @@ static int tile_decision(const orc_camera *cam, const orc_gauss *g, const orc_ma
     const double y_lo = ty * ORC_TILE + 0.5;
     double y_hi = ty * ORC_TILE + (ORC_TILE - 1) + 0.5;
     if (y_hi > cam->height - 0.5) y_hi = cam->height - 0.5;
-    double mag;
+    double mag, grad;
     const double qmin = box_qmin(g->conic[0], g->conic[1], g->conic[2], x_lo - g->xy[0],
-                                 x_hi - g->xy[0], y_lo - g->xy[1], y_hi - g->xy[1], &mag);
+                                 x_hi - g->xy[0], y_lo - g->xy[1], y_hi - g->xy[1], &mag, &grad);
     const int in_rect = !(g->rect[0] > g->rect[2] || g->rect[1] > g->rect[3]) &&
                         tx >= g->rect[0] / ORC_TILE && tx <= g->rect[2] / ORC_TILE &&
                         ty >= g->rect[1] / ORC_TILE && ty <= g->rect[3] / ORC_TILE;
@@ -398,7 +410,8 @@ static int tile_decision(const orc_camera *cam, const orc_gauss *g, const orc_ma
                           tx >= g->rect_narrow[0] / ORC_TILE && tx <= g->rect_narrow[2] / ORC_TILE &&
                           ty >= g->rect_narrow[1] / ORC_TILE && ty <= g->rect_narrow[3] / ORC_TILE;
     const int keep = g->visible && in_rect && (qmin <= g->k || !mg->tile_culling);
-    const double slack = mg->rel * (mag + g->k);
+    const double pos_err = mg->pos_rel * fmax(1.0, fmax(fabs(g->xy[0]), fabs(g->xy[1])));
+    const double slack = mg->q_rel * mag + mg->rel * g->k + 2.0 * pos_err * grad;
     const int marginal_cull = mg->tile_culling && fabs(qmin - g->k) <= slack;
     const int in_wide = qmin <= g->k + slack || !mg->tile_culling;
     int flags = 0;
@@ -538,14 +551,19 @@ static void pixel_walk(double px, double py, int64_t start, int64_t end, const i
         const double mag = fabs(qa) + fabs(qb) + fabs(qc);
         const double power = -0.5 * (qa + qb + qc);
         const double oG = opac[g] * exp(power);
-        const double slack = mg->rel * (1.0 + mag);
+        /* relative float32 error of o G: opacity and exp rounding, the
+         * rounding of the quadratic form and the position error of mu2D */
+        const double pos_err = mg->pos_rel * fmax(1.0, fmax(fabs(xy[2 * g]), fabs(xy[2 * g + 1])));
+        const double grad = fabs(conic[3 * g] * dx + conic[3 * g + 1] * dy) +
+                            fabs(conic[3 * g + 1] * dx + conic[3 * g + 2] * dy);
+        const double slack = mg->rel + 0.5 * mg->q_rel * mag + pos_err * grad;
         if (!keep || (f & ORC_IMARGINAL)) {
             /* a candidate float32 may decide differently: flag the pixel
              * when it would contribute here */
             if (oG >= ORC_ALPHA_MIN * (1.0 - slack)) amb = 1;
             if (!keep) continue;
         }
-        if (fabs(power) <= mg->rel * mag + (mg->rel > 0.0 ? 1e-12 : 0.0)) amb = 1;
+        if (fabs(power) <= 0.5 * mg->q_rel * mag + (mg->q_rel > 0.0 ? 1e-12 : 0.0)) amb = 1;
         if (power > 0.0) continue;
         if (fabs(oG - ORC_ALPHA_MIN) <= ORC_ALPHA_MIN * slack) amb = 1;
         if (fabs(oG - ORC_ALPHA_MAX) <= ORC_ALPHA_MAX * slack) amb = 1;
@@ -605,7 +623,7 @@ int orc_blend_brute(int32_t width, int32_t height, int64_t count, const int32_t 
                     int32_t *last_gid)
 {
     const int64_t npix = (int64_t)width * height;
-    const orc_margins none = {0.0, 0.0, 0.0, 0.0, 1};
+    const orc_margins none = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1};
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t p = 0; p < npix; ++p) {
         const int u = (int)(p % width), v = (int)(p / width);
@@ -755,7 +773,7 @@ int orc_preprocess_backward(const orc_camera *cam, int64_t n, int sh_degree, con
                             double *g_log_scales, double *g_quats, double *g_opacity,
                             double *g_sh_dc, double *g_sh_rest)
 {
-    const orc_margins none = {0.0, 0.0, 0.0, 0.0, 1};
+    const orc_margins none = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1};
     const double *R = cam->R;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {

@@ -1,0 +1,185 @@
+// adam.cu -- fused Adam update (Suppl. A: beta = (0.9, 0.999), eps = 1e-15;
+// Sec. 3.3 "Parameter Updates": one fused kernel that follows PyTorch's
+// Adam step by step).  Per element, in float32:
+//   m = m + (1 - b1) (g - m)                     (PyTorch forms m with lerp)
+//   v = b2 v + (1 - b2) g^2
+//   p = p - step_size * m / (sqrt(v) / sqrt(1 - b2^t) + eps)
+// with step_size = lr / (1 - b1^t), 1 - b1 and 1 - b2 formed in double and
+// rounded once (0.999 is not a float32), as PyTorch does.
+// Every element is updated, zero gradients included (Sec. 3.3).
+// Storage: parameters float32 / bf16 / fp16; moments float32 / bf16 / fp16.
+// An fp16 second moment is stored as sqrt(v): g^2 underflows fp16 for
+// |g| < 2.4e-4 while |g| itself stays representable.
+#include "fgs_common.cuh"
+
+namespace fgs {
+
+template <typename MT> struct VStore {
+    static __device__ __forceinline__ float load(MT x) { return to_f32(x); }
+    static __device__ __forceinline__ MT store(float v) { return from_f32<MT>(v); }
+};
+template <> struct VStore<__half> {
+    static __device__ __forceinline__ float load(__half x) { const float s = __half2float(x); return s * s; }
+    static __device__ __forceinline__ __half store(float v) { return __float2half_rn(sqrtf(v)); }
+};
+
+struct AdamScalars {
+    float step_size, inv_bc2_sqrt, b1, b2, omb1, omb2, eps;
+};
+
+// Scalars of group g: from the kernel argument, or from the device state.
+__device__ __forceinline__ AdamScalars resolve(AdamScalars a, const fgs_adam_state* st, int g)
+{
+    if (st) {
+        a.step_size = st->step_size[g];
+        a.inv_bc2_sqrt = st->inv_bc2_sqrt;
+        a.b1 = st->beta1_f;
+        a.b2 = st->beta2_f;
+        a.omb1 = st->one_minus_beta1_f;
+        a.omb2 = st->one_minus_beta2_f;
+        a.eps = st->eps_f;
+    }
+    return a;
+}
+
+// One thread: advance the step and derive the step sizes (double precision)
+// with the exponential decay of the means learning rate of Suppl. A.
+__global__ void adam_prepare_kernel(fgs_adam_state* st)
+{
+    const int t = st->step + 1;
+    st->step = t;
+    const double bc1 = 1.0 - pow(st->beta1, (double)t);
+    const double bc2 = 1.0 - pow(st->beta2, (double)t);
+    for (int g = 0; g < 6; ++g) {
+        double lr = st->lr[g];
+        if (g == 0 && st->lr_means_final > 0.0f && st->decay_steps > 0) {
+            const double f = fmin((double)(t - 1) / (double)st->decay_steps, 1.0);
+            lr = exp((1.0 - f) * log((double)st->lr[0]) + f * log((double)st->lr_means_final));
+        }
+        st->step_size[g] = (float)(lr / bc1);
+    }
+    st->inv_bc2_sqrt = (float)(1.0 / sqrt(bc2));
+    st->beta1_f = (float)st->beta1;
+    st->beta2_f = (float)st->beta2;
+    st->one_minus_beta1_f = (float)(1.0 - st->beta1);
+    st->one_minus_beta2_f = (float)(1.0 - st->beta2);
+    st->eps_f = (float)st->eps;
+}
+
+__device__ __forceinline__ float adam_update(float p, float g, float& m, float& v, const AdamScalars& a)
+{
+    m = m + a.omb1 * (g - m);
+    v = v * a.b2 + a.omb2 * g * g;
+    const float denom = sqrtf(v) * a.inv_bc2_sqrt + a.eps;
+    return p - a.step_size * (m / denom);
+}
+
+template <typename PT, typename MT>
+__global__ void __launch_bounds__(256)
+adam_kernel(int64_t count, PT* __restrict__ p, const float* __restrict__ g, MT* __restrict__ m,
+            MT* __restrict__ v, AdamScalars a0, const fgs_adam_state* __restrict__ st, int grp)
+{
+    const AdamScalars a = resolve(a0, st, grp);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        float mm = to_f32(m[i]);
+        float vv = VStore<MT>::load(v[i]);
+        const float pn = adam_update(to_f32(p[i]), g[i], mm, vv, a);
+        p[i] = from_f32<PT>(pn);
+        m[i] = from_f32<MT>(mm);
+        v[i] = VStore<MT>::store(vv);
+    }
+}
+
+// float32 everything, 16-byte aligned: four elements per thread and step.
+__global__ void __launch_bounds__(256)
+adam_f32x4_kernel(int64_t count4, float4* __restrict__ p, const float4* __restrict__ g,
+                  float4* __restrict__ m, float4* __restrict__ v, AdamScalars a0,
+                  const fgs_adam_state* __restrict__ st, int grp)
+{
+    const AdamScalars a = resolve(a0, st, grp);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count4; i += stride) {
+        float4 pp = p[i], gg = __ldcs(&g[i]), mm = m[i], vv = v[i];
+        pp.x = adam_update(pp.x, gg.x, mm.x, vv.x, a);
+        pp.y = adam_update(pp.y, gg.y, mm.y, vv.y, a);
+        pp.z = adam_update(pp.z, gg.z, mm.z, vv.z, a);
+        pp.w = adam_update(pp.w, gg.w, mm.w, vv.w, a);
+        p[i] = pp;
+        m[i] = mm;
+        v[i] = vv;
+    }
+}
+
+static int grid_for(int64_t work)
+{
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (work + 255) / 256;
+    const int64_t cap = (int64_t)sms * 8;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+template <typename PT, typename MT>
+static cudaError_t launch_typed(int64_t count, void* p, const float* g, void* m, void* v,
+                                const AdamScalars& a, const fgs_adam_state* ds, int grp,
+                                cudaStream_t st)
+{
+    adam_kernel<PT, MT><<<grid_for(count), 256, 0, st>>>(count, (PT*)p, g, (MT*)m, (MT*)v, a, ds, grp);
+    profile_mark(st, "adam");
+    return cudaGetLastError();
+}
+
+template <typename PT>
+static cudaError_t launch_m(int mdt, int64_t count, void* p, const float* g, void* m, void* v,
+                            const AdamScalars& a, const fgs_adam_state* ds, int grp, cudaStream_t st)
+{
+    switch (mdt) {
+    case FGS_BF16: return launch_typed<PT, __nv_bfloat16>(count, p, g, m, v, a, ds, grp, st);
+    case FGS_F16: return launch_typed<PT, __half>(count, p, g, m, v, a, ds, grp, st);
+    default: return launch_typed<PT, float>(count, p, g, m, v, a, ds, grp, st);
+    }
+}
+
+cudaError_t launch_adam_prepare(fgs_adam_state* ds, cudaStream_t st)
+{
+    adam_prepare_kernel<<<1, 1, 0, st>>>(ds);
+    profile_mark(st, "adam_prepare");
+    return cudaGetLastError();
+}
+
+// One parameter group.  pdt / mdt: storage of the parameter and of both
+// moments (the two moments share a type).  ds (nullable): device state whose
+// scalars replace the host ones.
+cudaError_t launch_adam_group(int64_t count, int pdt, int mdt, void* p, const float* g, void* m,
+                              void* v, float step_size, float inv_bc2_sqrt, double b1, double b2,
+                              double eps, const fgs_adam_state* ds, int grp, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    const AdamScalars a{step_size, inv_bc2_sqrt, (float)b1, (float)b2, (float)(1.0 - b1),
+                        (float)(1.0 - b2), (float)eps};
+    const bool aligned = ((uintptr_t)p | (uintptr_t)g | (uintptr_t)m | (uintptr_t)v) % 16 == 0;
+    if (pdt == FGS_F32 && mdt == FGS_F32 && aligned) {
+        const int64_t c4 = count / 4;
+        if (c4 > 0) {
+            adam_f32x4_kernel<<<grid_for(c4), 256, 0, st>>>(c4, (float4*)p, (const float4*)g, (float4*)m,
+                                                            (float4*)v, a, ds, grp);
+            profile_mark(st, "adam");
+        }
+        const int64_t rest = count - 4 * c4;
+        if (rest > 0) {
+            adam_kernel<float, float><<<1, 32, 0, st>>>(rest, (float*)p + 4 * c4, g + 4 * c4,
+                                                        (float*)m + 4 * c4, (float*)v + 4 * c4, a, ds, grp);
+            profile_mark(st, "adam_tail");
+        }
+        return cudaGetLastError();
+    }
+    switch (pdt) {
+    case FGS_BF16: return launch_m<__nv_bfloat16>(mdt, count, p, g, m, v, a, ds, grp, st);
+    case FGS_F16: return launch_m<__half>(mdt, count, p, g, m, v, a, ds, grp, st);
+    default: return launch_m<float>(mdt, count, p, g, m, v, a, ds, grp, st);
+    }
+}
+
+}  // namespace fgs

@@ -1,0 +1,272 @@
+// fgs_common.cuh -- definitions shared by the sm_103a kernels of libfastergs.
+//
+// Threshold constants of Faster-GS (arXiv 2602.09999):
+//   tau_alpha = 1/255 (Sec. 3.2 "Splat Bounding"), alpha clamp 0.99 and
+//   early-stop transmittance 1e-4 (Suppl. B.1), degenerate quaternion norm
+//   1e-4 and 2D-covariance determinant 1e-6 (Suppl. B.1), 2D dilation 0.3
+//   (Suppl. C, Eq. original_2dfilter), 16x16 tiles (Sec. 3.1).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fastergs.h"
+
+namespace fgs {
+
+constexpr int kTile = FGS_TILE;
+constexpr int kTilePixels = kTile * kTile;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kQNormMin = 1e-4f;
+constexpr float kDetMin = 1e-6f;
+constexpr float kDilation = 0.3f;
+constexpr int kPreBlock = 256;  // Gaussians per preprocess CTA (scan granularity)
+
+// Per-view sizes and prefix offsets, passed to kernels by value.  Sizes are
+// fixed for the lifetime of a captured graph; poses come from device memory.
+struct ViewTable {
+    int32_t n_views;
+    int32_t total_tiles;
+    int64_t total_pixels;
+    int32_t width[FGS_MAX_VIEWS];
+    int32_t height[FGS_MAX_VIEWS];
+    int32_t tiles_x[FGS_MAX_VIEWS];
+    int32_t tile_off[FGS_MAX_VIEWS + 1];
+    int64_t pix_off[FGS_MAX_VIEWS + 1];
+};
+
+// Screen-space state of one (view, Gaussian): 48 bytes, read by the blend
+// kernels as three 16-byte loads.
+struct alignas(16) Screen {
+    float4 q0;  // mu2D.x, mu2D.y, conic a, conic b
+    float4 q1;  // conic c, opacity, k = 2 ln(255 o), depth
+    float4 q2;  // rgb, bits: clamp mask (bits 0..2) | visible (bit 3)
+};
+
+// dL/d(mu2D, conic, opacity, rgb) accumulators of one (view, Gaussian).
+struct alignas(16) ScreenGrad {
+    float4 g0;  // d mu.x, d mu.y, d a, d b
+    float4 g1;  // d c, d o, d r, d g
+    float4 g2;  // d b(lue), unused x3
+};
+
+struct WsHeader {
+    uint32_t flags;
+    uint32_t reserved;
+    unsigned long long instances;  // total (Gaussian, tile) instances of the last forward
+    uint32_t counters[4];
+};
+
+__host__ __device__ inline int view_of_tile(const ViewTable& vt, int tile)
+{
+    int v = 0;
+    while (v + 1 < vt.n_views && tile >= vt.tile_off[v + 1]) ++v;
+    return v;
+}
+
+struct Cam {
+    float R[9], t[3], fx, fy, cx, cy, near_plane, pos[3];
+    int width, height;
+};
+
+__device__ inline Cam load_cam(const fgs_camera* cams, int v)
+{
+    const fgs_camera* c = cams + v;
+    Cam k;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) k.R[i] = __ldg(&c->R[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        k.t[i] = __ldg(&c->t[i]);
+        k.pos[i] = __ldg(&c->cam_pos[i]);
+    }
+    k.fx = __ldg(&c->fx);
+    k.fy = __ldg(&c->fy);
+    k.cx = __ldg(&c->cx);
+    k.cy = __ldg(&c->cy);
+    k.near_plane = __ldg(&c->near_plane);
+    k.width = __ldg(&c->width);
+    k.height = __ldg(&c->height);
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// Storage-type helpers (SH and Adam moments may be bf16 / fp16)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float to_f32(__half x) { return __half2float(x); }
+template <typename T> __device__ __forceinline__ T from_f32(float x);
+template <> __device__ __forceinline__ float from_f32<float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ __half from_f32<__half>(float x) { return __float2half_rn(x); }
+
+// ---------------------------------------------------------------------------
+// Decisions that two kernels must take bit-identically are written with
+// explicit round-to-nearest intrinsics, so no FMA contraction choice of the
+// compiler can make them differ between call sites.
+// ---------------------------------------------------------------------------
+
+// q(d) = a dx^2 + 2 b dx dy + c dy^2
+__device__ __forceinline__ float quad_form(float a, float b, float c, float dx, float dy)
+{
+    const float t0 = __fmul_rn(__fmul_rn(a, dx), dx);
+    const float t1 = __fmul_rn(__fmul_rn(__fmul_rn(2.0f, b), dx), dy);
+    const float t2 = __fmul_rn(__fmul_rn(c, dy), dy);
+    return __fadd_rn(__fadd_rn(t0, t1), t2);
+}
+
+// Tile culling of Sec. 3.2 (the per-tile maximum of the Gaussian): minimum
+// of the quadratic form over the box of the tile's pixel centres (offsets
+// from the mean); keep the tile iff it is <= k.
+__device__ __forceinline__ bool tile_keep(float mx, float my, float a, float b, float c, float k,
+                                          int tx, int ty, int width, int height)
+{
+    const float x_lo = __fadd_rn((float)(tx * kTile), 0.5f);
+    const float x_hi = fminf(__fadd_rn((float)(tx * kTile + kTile - 1), 0.5f), __fadd_rn((float)width, -0.5f));
+    const float y_lo = __fadd_rn((float)(ty * kTile), 0.5f);
+    const float y_hi = fminf(__fadd_rn((float)(ty * kTile + kTile - 1), 0.5f), __fadd_rn((float)height, -0.5f));
+    const float x0 = __fsub_rn(x_lo, mx), x1 = __fsub_rn(x_hi, mx);
+    const float y0 = __fsub_rn(y_lo, my), y1 = __fsub_rn(y_hi, my);
+    if (x0 <= 0.0f && 0.0f <= x1 && y0 <= 0.0f && 0.0f <= y1) return true;
+    float best = INFINITY;
+    // edges x = x0, x1: minimise over y in [y0, y1]
+    {
+        float X = x0;
+        float Y = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, X), c), y0), y1);
+        best = fminf(best, quad_form(a, b, c, X, Y));
+        X = x1;
+        Y = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, X), c), y0), y1);
+        best = fminf(best, quad_form(a, b, c, X, Y));
+    }
+    // edges y = y0, y1: minimise over x in [x0, x1]
+    {
+        float Y = y0;
+        float X = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, Y), a), x0), x1);
+        best = fminf(best, quad_form(a, b, c, X, Y));
+        Y = y1;
+        X = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, Y), a), x0), x1);
+        best = fminf(best, quad_form(a, b, c, X, Y));
+    }
+    return best <= k;
+}
+
+// Alpha of one fragment (Eq. 3 with the 3DGS rules): returns false when
+// the fragment is skipped (power > 0 or alpha < 1/255); otherwise alpha =
+// min(0.99, o G), and G and the clamp state for the backward.
+struct Frag {
+    float alpha, G, dx, dy;
+    bool clamped;
+};
+
+__device__ __forceinline__ bool eval_fragment(float px, float py, float4 q0, float c, float o,
+                                              Frag& f)
+{
+    f.dx = __fsub_rn(px, q0.x);
+    f.dy = __fsub_rn(py, q0.y);
+    const float power = __fmul_rn(-0.5f, quad_form(q0.z, q0.w, c, f.dx, f.dy));
+    if (power > 0.0f) return false;
+    f.G = __expf(power);
+    const float oG = __fmul_rn(o, f.G);
+    f.clamped = oG >= kAlphaMax;
+    f.alpha = f.clamped ? kAlphaMax : oG;
+    return f.alpha >= kAlphaMin;
+}
+
+// ---------------------------------------------------------------------------
+// Real SH basis (Condon-Shortley phase, orthonormal), degree <= 3, at a unit
+// direction; coefficient k = l*l + l + m.
+// ---------------------------------------------------------------------------
+struct SHC {
+    static constexpr float c0 = 0.28209479177387814f;   // 1/(2 sqrt(pi))
+    static constexpr float c1 = 0.4886025119029199f;    // sqrt(3/(4 pi))
+    static constexpr float c2a = 1.0925484305920792f;   // sqrt(15/pi)/2
+    static constexpr float c2b = 0.31539156525252005f;  // sqrt(5/pi)/4
+    static constexpr float c2c = 0.5462742152960396f;   // sqrt(15/pi)/4
+    static constexpr float c3a = 0.5900435899266435f;   // sqrt(35/(2 pi))/4
+    static constexpr float c3b = 2.890611442640554f;    // sqrt(105/pi)/2
+    static constexpr float c3c = 0.4570457994644658f;   // sqrt(21/(2 pi))/4
+    static constexpr float c3d = 0.3731763325901154f;   // sqrt(7/pi)/4
+    static constexpr float c3e = 1.445305721320277f;    // sqrt(105/pi)/4
+};
+
+__device__ __forceinline__ void sh_basis(float x, float y, float z, int degree, float Y[16])
+{
+    Y[0] = SHC::c0;
+#pragma unroll
+    for (int k = 1; k < 16; ++k) Y[k] = 0.0f;
+    if (degree < 1) return;
+    Y[1] = -SHC::c1 * y;
+    Y[2] = SHC::c1 * z;
+    Y[3] = -SHC::c1 * x;
+    if (degree < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = SHC::c2a * x * y;
+    Y[5] = -SHC::c2a * y * z;
+    Y[6] = SHC::c2b * (2.0f * zz - xx - yy);
+    Y[7] = -SHC::c2a * x * z;
+    Y[8] = SHC::c2c * (xx - yy);
+    if (degree < 3) return;
+    Y[9] = -SHC::c3a * y * (3.0f * xx - yy);
+    Y[10] = SHC::c3b * x * y * z;
+    Y[11] = -SHC::c3c * y * (4.0f * zz - xx - yy);
+    Y[12] = SHC::c3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -SHC::c3c * x * (4.0f * zz - xx - yy);
+    Y[14] = SHC::c3e * z * (xx - yy);
+    Y[15] = -SHC::c3a * x * (xx - 3.0f * yy);
+}
+
+// d/d(x, y, z) of sum_k coef[k] Y_k for the polynomial forms above.
+__device__ __forceinline__ void sh_dir_grad(float x, float y, float z, int degree,
+                                            const float coef[16], float g[3])
+{
+    g[0] = g[1] = g[2] = 0.0f;
+    if (degree < 1) return;
+    g[0] += -SHC::c1 * coef[3];
+    g[1] += -SHC::c1 * coef[1];
+    g[2] += SHC::c1 * coef[2];
+    if (degree < 2) return;
+    g[0] += SHC::c2a * y * coef[4] - SHC::c2a * z * coef[7] - 2.0f * SHC::c2b * x * coef[6] +
+            2.0f * SHC::c2c * x * coef[8];
+    g[1] += SHC::c2a * x * coef[4] - SHC::c2a * z * coef[5] - 2.0f * SHC::c2b * y * coef[6] -
+            2.0f * SHC::c2c * y * coef[8];
+    g[2] += -SHC::c2a * y * coef[5] + 4.0f * SHC::c2b * z * coef[6] - SHC::c2a * x * coef[7];
+    if (degree < 3) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    g[0] += -SHC::c3a * 6.0f * x * y * coef[9] + SHC::c3b * y * z * coef[10] +
+            SHC::c3c * 2.0f * x * y * coef[11] - SHC::c3d * 6.0f * x * z * coef[12] -
+            SHC::c3c * (4.0f * zz - 3.0f * xx - yy) * coef[13] + SHC::c3e * 2.0f * x * z * coef[14] -
+            SHC::c3a * (3.0f * xx - 3.0f * yy) * coef[15];
+    g[1] += -SHC::c3a * (3.0f * xx - 3.0f * yy) * coef[9] + SHC::c3b * x * z * coef[10] -
+            SHC::c3c * (4.0f * zz - xx - 3.0f * yy) * coef[11] - SHC::c3d * 6.0f * y * z * coef[12] +
+            SHC::c3c * 2.0f * x * y * coef[13] - SHC::c3e * 2.0f * y * z * coef[14] +
+            SHC::c3a * 6.0f * x * y * coef[15];
+    g[2] += SHC::c3b * x * y * coef[10] - SHC::c3c * 8.0f * y * z * coef[11] +
+            SHC::c3d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * coef[12] -
+            SHC::c3c * 8.0f * x * z * coef[13] + SHC::c3e * (xx - yy) * coef[14];
+}
+
+// Rotation matrix of a unit quaternion (w, x, y, z), Hamilton convention.
+__device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, float R[9])
+{
+    R[0] = 1.0f - 2.0f * (y * y + z * z);
+    R[1] = 2.0f * (x * y - w * z);
+    R[2] = 2.0f * (x * z + w * y);
+    R[3] = 2.0f * (x * y + w * z);
+    R[4] = 1.0f - 2.0f * (x * x + z * z);
+    R[5] = 2.0f * (y * z - w * x);
+    R[6] = 2.0f * (x * z - w * y);
+    R[7] = 2.0f * (y * z + w * x);
+    R[8] = 1.0f - 2.0f * (x * x + y * y);
+}
+
+__device__ __forceinline__ void set_flag(WsHeader* h, uint32_t bit) { atomicOr(&h->flags, bit); }
+
+// Records the next attached profiling event (no-op unless attached).
+void profile_mark(cudaStream_t st, const char* label);
+
+}  // namespace fgs

@@ -1,0 +1,293 @@
+// sort.cu -- stable LSD radix sort of (uint64 key, uint32 value) pairs and
+// the per-tile range extraction (Sec. 3.2 "Sorting": one radix sort of the
+// combined (tile << 32 | depth) keys; Suppl. B.2 complexity model O(k n)).
+//
+// Each pass orders 8 key bits (the last pass only the remaining ones) with
+// three kernels:
+//   upsweep   : per-CTA digit histogram of 4096 keys -> hist[digit][cta]
+//   scan      : one CTA per digit, exclusive prefix over the CTAs
+//   downsweep : stable rank of each key inside its CTA (warp ballots give
+//               the peers with the same digit; per-warp digit counters keep
+//               the input order), scatter to shared memory in digit order,
+//               then coalesced writes of each digit run to its global slot.
+// The number of valid keys is read from device memory, so the grid is sized
+// for the capacity and the sort can be captured in a CUDA graph.
+#include "fgs_common.cuh"
+
+namespace fgs {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per CTA
+constexpr int kRadix = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+
+__global__ void __launch_bounds__(kSortThreads)
+radix_upsweep_kernel(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ n_dev,
+                     int shift, uint32_t dmask, int nb_max, uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t h[kSortWarps][kRadix];
+    const uint32_t n = *n_dev;
+    const int nb = (int)((n + kSortTile - 1) / kSortTile);
+    const int warp = threadIdx.x >> 5;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int64_t base = (int64_t)b * kSortTile;
+        for (int d = threadIdx.x; d < kSortWarps * kRadix; d += kSortThreads) (&h[0][0])[d] = 0;
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < kSortItems; ++r) {
+            const int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
+            if (idx < n) {
+                const uint32_t d = (uint32_t)(keys[idx] >> shift) & dmask;
+                atomicAdd(&h[warp][d], 1u);
+            }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) s += h[w][d];
+            hist[(int64_t)d * nb_max + b] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA per digit: exclusive prefix of hist[d][0..nb) in place; the digit
+// total goes to dtot[d].
+__global__ void __launch_bounds__(256)
+radix_scan_kernel(uint32_t* __restrict__ hist, const uint32_t* __restrict__ n_dev, int nb_max,
+                  uint32_t* __restrict__ dtot)
+{
+    __shared__ uint32_t part[256];
+    const uint32_t n = *n_dev;
+    const int nb = (int)((n + kSortTile - 1) / kSortTile);
+    uint32_t* row = hist + (int64_t)blockIdx.x * nb_max;
+    const int t = threadIdx.x;
+    const int chunk = (nb + 255) / 256;
+    const int b0 = t * chunk, b1 = min(nb, b0 + chunk);
+    uint32_t s = 0;
+    for (int j = b0; j < b1; ++j) s += row[j];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        const uint32_t y = t >= o ? part[t - o] : 0u;
+        __syncthreads();
+        part[t] += y;
+        __syncthreads();
+    }
+    uint32_t run = part[t] - s;
+    for (int j = b0; j < b1; ++j) {
+        const uint32_t x = row[j];
+        row[j] = run;
+        run += x;
+    }
+    if (t == 255) dtot[blockIdx.x] = part[255];
+}
+
+struct DownSmem {
+    unsigned long long keys[kSortTile];
+    uint32_t vals[kSortTile];
+    uint32_t cnt[kSortWarps][kRadix];
+    uint32_t local_start[kRadix];
+    uint32_t glob_off[kRadix];
+    uint32_t scan_a[kRadix];
+    uint32_t scan_b[kRadix];
+};
+
+__device__ __forceinline__ void radix_downsweep_tile(DownSmem& S, const unsigned long long* __restrict__ keys_in,
+                                                     const uint32_t* __restrict__ vals_in,
+                                                     unsigned long long* __restrict__ keys_out,
+                                                     uint32_t* __restrict__ vals_out,
+                                                     const uint32_t* __restrict__ hist,
+                                                     const uint32_t* __restrict__ dtot, uint32_t n,
+                                                     int shift, uint32_t dmask, int nb_max, int b)
+{
+    const int64_t base = (int64_t)b * kSortTile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int d = tid; d < kSortWarps * kRadix; d += kSortThreads) (&S.cnt[0][0])[d] = 0;
+    __syncthreads();
+
+    unsigned long long k[kSortItems];
+    uint32_t val[kSortItems];
+    uint32_t dr[kSortItems];  // digit (bits 24..31) | rank within the warp (bits 0..23)
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t idx = base + (int64_t)warp * (kSortItems * 32) + r * 32 + lane;
+        const bool valid = idx < n;
+        k[r] = valid ? keys_in[idx] : 0ull;
+        val[r] = valid ? vals_in[idx] : 0u;
+        const uint32_t d = (uint32_t)(k[r] >> shift) & dmask;
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {
+            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? bb : ~bb;
+        }
+        const uint32_t before = __popc(peers & lt_mask);
+        const uint32_t prior = valid ? S.cnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid && before == (uint32_t)__popc(peers) - 1u) S.cnt[warp][d] = prior + __popc(peers);
+        __syncwarp();
+        dr[r] = valid ? ((d << 24) | (prior + before)) : 0xffffffffu;
+    }
+    __syncthreads();
+    // per digit: prefix over warps (in place) and the CTA total
+    const int d = tid;  // kSortThreads == kRadix
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = S.cnt[w][d];
+        S.cnt[w][d] = run;
+        run += c;
+    }
+    // exclusive scans over digits: CTA-local starts and global digit bases
+    const uint32_t gt = dtot[d];
+    S.scan_a[d] = run;
+    S.scan_b[d] = gt;
+    __syncthreads();
+    for (int o = 1; o < kRadix; o <<= 1) {
+        const uint32_t ya = d >= o ? S.scan_a[d - o] : 0u;
+        const uint32_t yb = d >= o ? S.scan_b[d - o] : 0u;
+        __syncthreads();
+        S.scan_a[d] += ya;
+        S.scan_b[d] += yb;
+        __syncthreads();
+    }
+    const uint32_t local_start = S.scan_a[d] - run;
+    const uint32_t digit_base = S.scan_b[d] - gt;
+    S.local_start[d] = local_start;
+    S.glob_off[d] = digit_base + hist[(int64_t)d * nb_max + b] - local_start;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        if (dr[r] == 0xffffffffu) continue;
+        const uint32_t dd = dr[r] >> 24;
+        const uint32_t pos = S.local_start[dd] + S.cnt[warp][dd] + (dr[r] & 0xffffffu);
+        S.keys[pos] = k[r];
+        S.vals[pos] = val[r];
+    }
+    __syncthreads();
+    const int count = (int)min((int64_t)kSortTile, (int64_t)n - base);
+    for (int j = tid; j < count; j += kSortThreads) {
+        const unsigned long long key = S.keys[j];
+        const uint32_t dd = (uint32_t)(key >> shift) & dmask;
+        const uint32_t g = S.glob_off[dd] + j;
+        keys_out[g] = key;
+        vals_out[g] = S.vals[j];
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+radix_downsweep_kernel(const unsigned long long* __restrict__ keys_in,
+                       const uint32_t* __restrict__ vals_in, unsigned long long* __restrict__ keys_out,
+                       uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ hist,
+                       const uint32_t* __restrict__ dtot, const uint32_t* __restrict__ n_dev,
+                       int shift, uint32_t dmask, int nb_max)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DownSmem& S = *reinterpret_cast<DownSmem*>(smem_raw);
+    const uint32_t n = *n_dev;
+    const int nb = (int)((n + kSortTile - 1) / kSortTile);
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        radix_downsweep_tile(S, keys_in, vals_in, keys_out, vals_out, hist, dtot, n, shift, dmask, nb_max, b);
+        __syncthreads();
+    }
+}
+
+// [start, end) of each tile's run in the sorted keys; ranges must be zeroed.
+__global__ void __launch_bounds__(256)
+tile_ranges_kernel(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ n_dev,
+                   uint2* __restrict__ ranges)
+{
+    const uint32_t n = *n_dev;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t tile = (uint32_t)(keys[j] >> 32);
+        if (j == 0) {
+            ranges[tile].x = 0;
+        } else {
+            const uint32_t prev = (uint32_t)(keys[j - 1] >> 32);
+            if (prev != tile) {
+                ranges[prev].y = (uint32_t)j;
+                ranges[tile].x = (uint32_t)j;
+            }
+        }
+        if (j == (int64_t)n - 1) ranges[tile].y = (uint32_t)n;
+    }
+}
+
+// CTAs per SM times the SM count of the current device.
+static int resident_grid(int per_sm)
+{
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * per_sm;
+}
+
+__global__ void set_count_kernel(uint32_t* dst, uint32_t value) { *dst = value; }
+
+cudaError_t launch_set_count(uint32_t* dst, uint32_t value, cudaStream_t st)
+{
+    set_count_kernel<<<1, 1, 0, st>>>(dst, value);
+    return cudaGetLastError();
+}
+
+size_t sort_hist_bytes(int64_t n_max)
+{
+    const int64_t nb = (n_max + kSortTile - 1) / kSortTile;
+    return (size_t)(kRadix * (nb > 0 ? nb : 1) + kRadix + 64) * sizeof(uint32_t);
+}
+
+// Sorts n_dev[0] pairs on bits [0, bits).  Returns 1 when the result is in
+// the *_alt buffers.  hist: sort_hist_bytes(n_max) bytes.
+int radix_sort(unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
+               uint32_t* vals_alt, int64_t n_max, const uint32_t* n_dev, int bits,
+               uint32_t* hist, cudaStream_t st, cudaError_t* err)
+{
+    const int smem = (int)sizeof(DownSmem);
+    cudaFuncSetAttribute(radix_downsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int nb_max = (int)((n_max + kSortTile - 1) / kSortTile);
+    const int grid = nb_max < resident_grid(2) ? nb_max : resident_grid(2);
+    uint32_t* dtot = hist + (int64_t)kRadix * (nb_max > 0 ? nb_max : 1);
+    int passes = (bits + 7) / 8;
+    unsigned long long *ki = keys, *ko = keys_alt;
+    uint32_t *vi = vals, *vo = vals_alt;
+    *err = cudaSuccess;
+    if (nb_max == 0) return 0;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        const int dbits = bits - shift < 8 ? bits - shift : 8;  // the last pass may be narrower
+        const uint32_t dmask = (1u << dbits) - 1u;
+        radix_upsweep_kernel<<<grid, kSortThreads, 0, st>>>(ki, n_dev, shift, dmask, nb_max, hist);
+        profile_mark(st, "sort_upsweep");
+        radix_scan_kernel<<<kRadix, 256, 0, st>>>(hist, n_dev, nb_max, dtot);
+        profile_mark(st, "sort_scan");
+        radix_downsweep_kernel<<<grid, kSortThreads, smem, st>>>(ki, vi, ko, vo, hist, dtot, n_dev,
+                                                                 shift, dmask, nb_max);
+        profile_mark(st, "sort_downsweep");
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            *err = e;
+            return 0;
+        }
+        unsigned long long* tk = ki; ki = ko; ko = tk;
+        uint32_t* tv = vi; vi = vo; vo = tv;
+    }
+    return passes & 1;
+}
+
+cudaError_t launch_tile_ranges(const unsigned long long* keys, const uint32_t* n_dev, int64_t n_max,
+                               uint2* ranges, int total_tiles, cudaStream_t st)
+{
+    cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)total_tiles, st);
+    profile_mark(st, "zero_ranges");
+    const int grid = (int)min((n_max + 255) / 256, (int64_t)resident_grid(8));
+    if (grid > 0) tile_ranges_kernel<<<grid, 256, 0, st>>>(keys, n_dev, ranges);
+    profile_mark(st, "tile_ranges");
+    return cudaGetLastError();
+}
+
+}  // namespace fgs

@@ -1,0 +1,113 @@
+"""CPU-side checks of the C ABI: the library loads, exports every function
+include/fastergs.h declares, its structs match the ctypes mirrors, and the
+host-only logic (workspace layout, argument checks, status strings) behaves.
+No call here launches a kernel."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2602_09999_gb300 import binding as B
+from paper_2602_09999_gb300 import build_lib, scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fastergs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return B.lib()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fgs_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_function(lib):
+    names = _declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(B.EXPORTED)
+
+
+def test_struct_sizes_match_c(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "fastergs.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(fgs_camera),'
+                   ' sizeof(fgs_params), sizeof(fgs_workspace_layout), sizeof(fgs_adam_state),'
+                   ' offsetof(fgs_adam_state, step_size));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert [int(x) for x in out] == [ctypes.sizeof(B.fgs_camera), ctypes.sizeof(B.fgs_params),
+                                     ctypes.sizeof(B.fgs_workspace_layout),
+                                     ctypes.sizeof(B.fgs_adam_state),
+                                     B.fgs_adam_state.step_size.offset]
+
+
+def test_workspace_layout(lib):
+    cams = [scenes.look_at((0, 0, 4), (0, 0, 0), w, h) for w, h in [(1237, 822), (640, 426)]]
+    ca = B.camera_array(cams)
+    L = B.fgs_workspace_size(3_000_000, ca, 2, 10_000_000)
+    tiles = 78 * 52 + 40 * 27
+    assert L.total_tiles == tiles
+    assert L.total_pixels == 1237 * 822 + 640 * 426
+    assert L.sort_bits == 32 + int(np.ceil(np.log2(tiles)))
+    assert L.sorted_in_alt == ((L.sort_bits + 7) // 8) % 2
+    offs = list(L.offset)
+    sizes = list(L.bytes)
+    for i in range(B.FGS_WS_NUM_SLOTS):
+        assert offs[i] % 256 == 0
+        if i + 1 < B.FGS_WS_NUM_SLOTS:
+            assert offs[i] + sizes[i] <= offs[i + 1]
+    assert offs[-1] + sizes[-1] <= L.total_bytes
+    assert sizes[B.FGS_WS_SCREEN] == 48 * 2 * 3_000_000
+    assert sizes[B.FGS_WS_KEYS] == 8 * 10_000_000
+
+
+@pytest.mark.parametrize("n,nv,k,code", [(0, 1, 10, -2), (2 ** 31, 1, 10, -2), (10, 0, 10, -7),
+                                         (10, 17, 10, -7), (10, 1, -1, -9)])
+def test_workspace_argument_errors(lib, n, nv, k, code):
+    cams = [scenes.look_at((0, 0, 4), (0, 0, 0), 64, 64)] * max(nv, 1)
+    ca = B.camera_array(cams)
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_workspace_size(n, ca, nv, k)
+    assert e.value.code == code
+
+
+def test_bad_camera_size_rejected(lib):
+    cam = scenes.look_at((0, 0, 4), (0, 0, 0), 64, 64)
+    cam.width = 0
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_workspace_size(10, B.camera_array([cam]), 1, 10)
+    assert e.value.code == -2
+
+
+def test_strerror(lib):
+    for code in range(-9, 1):
+        assert B.fgs_strerror(code)
+    assert B.fgs_strerror(-100) == "unknown status"
+
+
+def test_null_pointer_checks_before_any_launch(lib):
+    """Argument checks run on the host before any CUDA call."""
+    cam = B.camera_array([scenes.look_at((0, 0, 4), (0, 0, 0), 64, 64)])
+    L = B.fgs_workspace_size(10, cam, 1, 100)
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_render_forward(None, L, B.fgs_params(), 3, cam, None, (0, 0, 0), None, None)
+    assert e.value.code == -1
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_adam_step(B.fgs_params(), B.fgs_params(), B.fgs_params(), B.fgs_params(),
+                        [1e-3] * 6, 0.9, 0.999, 1e-15, 1, None)
+    assert e.value.code in (-1, -2)
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_sort_pairs(None, None, None, None, 10, 32, None, 0, None)
+    assert e.value.code == -1

@@ -1,0 +1,335 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+same seeded inputs: per-Gaussian screen state, tile lists (bit-exact after
+removing decisions float32 may take either way), images (max abs 2e-4
+outside ambiguous pixels), loss, gradients (relative L2 1e-3 per tensor),
+Adam and the full step, single and batched uneven views."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from gpu_util import (GRAD_REL_L2, IMAGE_TOL, compare_lists, gpu_forward,  # noqa: E402
+                      oracle_forward, rel_l2)
+from paper_2602_09999_gb300 import binding as B  # noqa: E402
+from paper_2602_09999_gb300 import scenes  # noqa: E402
+from paper_2602_09999_gb300 import train as T  # noqa: E402
+
+GROUPS = T.GROUPS
+
+
+def _scene_cases():
+    return [
+        ("tiny256", scenes.tiny_scene(10_000, seed=0), [scenes.tiny_camera(256, 256)]),
+        ("ragged", scenes.tiny_scene(6_000, seed=1), [scenes.tiny_camera(250, 183)]),
+        ("orbit_small", scenes.outdoor_scene(40_000, seed=2),
+         scenes.orbit_cameras(1, 203, 131, radius=6.0, seed=5)),
+    ]
+
+
+@pytest.fixture(scope="module", params=_scene_cases(), ids=lambda c: c[0])
+def case(request, oracle_mod):
+    name, params, cams = request.param
+    rast, views, t, images = gpu_forward(params, cams)
+    pres, lists, outs = oracle_forward(params, cams)
+    return dict(name=name, params=params, cams=cams, rast=rast, views=views, t=t, images=images,
+                pres=pres, lists=lists, outs=outs)
+
+
+def test_screen_state_matches_oracle(case):
+    scr = case["rast"].screen().cpu().numpy()
+    for v, pre in enumerate(case["pres"]):
+        s = scr[v]
+        bits = s[:, 11].view(np.uint32)
+        gvis = (bits & 8) != 0
+        keep_any = np.zeros(pre["xy"].shape[0], bool)
+        li = case["lists"][v]
+        keep_any[li["gid"][(li["flags"] & oracle.KEEP) != 0]] = True
+        sure = ~pre["marginal"]
+        marg_g = np.zeros_like(keep_any)
+        marg_g[li["gid"][(li["flags"] & oracle.IMARGINAL) != 0]] = True
+        sure &= ~marg_g
+        np.testing.assert_array_equal(gvis[sure], keep_any[sure])
+        m = gvis & keep_any
+        assert m.sum() > 100
+        np.testing.assert_allclose(s[m, 0:2], pre["xy"][m], atol=2e-3, rtol=0)
+        cmax = np.maximum(np.abs(pre["conic"][m, 0]), np.abs(pre["conic"][m, 2]))[:, None]
+        conic_g = np.stack([s[m, 2], s[m, 3], s[m, 4]], 1)
+        assert np.all(np.abs(conic_g - pre["conic"][m]) <= 1e-4 * cmax + 1e-7)
+        np.testing.assert_allclose(s[m, 5], pre["opacity"][m], rtol=2e-6)
+        np.testing.assert_allclose(s[m, 7], pre["depth"][m], rtol=2e-6)
+        np.testing.assert_allclose(s[m, 8:11], pre["rgb"][m], atol=2e-5)
+        clamp_g = np.stack([(bits[m] >> c) & 1 for c in range(3)], 1)
+        np.testing.assert_array_equal(clamp_g, pre["clamped"][m])
+
+
+def test_tile_lists_bit_exact(case):
+    compared, excluded = compare_lists(case["rast"], case["views"], case["pres"], case["lists"])
+    assert compared == case["rast"].layout.total_tiles
+    total = sum(li["gid"].size for li in case["lists"])
+    assert excluded <= 0.01 * total
+
+
+def test_images_within_tolerance(case):
+    imgs = case["views"].split(case["images"])
+    Tg, ncg = case["rast"].per_pixel()
+    Tg, ncg = Tg.cpu().numpy(), ncg.cpu().numpy()
+    _, vals, ranges = [x.cpu().numpy() if hasattr(x, "cpu") else x
+                       for x in case["rast"].sorted_lists()]
+    pix_off = case["views"].pix_off
+    total_amb = 0
+    tile_off = 0
+    for v, out in enumerate(case["outs"]):
+        img = imgs[v].cpu().numpy()
+        amb = out["ambiguous"].astype(bool)
+        total_amb += int(amb.sum())
+        err = np.abs(img - out["image"]).max(axis=0)
+        assert err[~amb].max() <= IMAGE_TOL, (case["name"], float(err[~amb].max()))
+        H, W = amb.shape
+        Tv = Tg[pix_off[v]:pix_off[v + 1]].reshape(H, W)
+        assert np.abs(Tv - out["T_final"])[~amb].max() <= 5e-5
+        # last contributor: unique Gaussian id
+        nc = ncg[pix_off[v]:pix_off[v + 1]].reshape(H, W).astype(np.int64)
+        tx = case["cams"][v].tiles[0]
+        uu, vv = np.meshgrid(np.arange(W), np.arange(H))
+        tiles = tile_off + (vv // 16) * tx + (uu // 16)
+        start = ranges.reshape(-1, 2)[tiles, 0].astype(np.int64)
+        last = np.where(nc > 0, vals[np.maximum(start + nc - 1, 0)], -1)
+        np.testing.assert_array_equal(last[~amb], out["last_gid"][~amb])
+        tile_off += case["lists"][v]["ranges"].shape[0]
+    npx = sum(o["image"].shape[1] * o["image"].shape[2] for o in case["outs"])
+    print(f"{case['name']}: ambiguous pixels {total_amb} / {npx}")
+    assert total_amb <= 0.01 * npx
+
+
+def test_forward_is_deterministic(case):
+    images2 = torch.zeros_like(case["images"])
+    case["rast"].forward(T.params_struct(case["t"]), 3, (0.0, 0.0, 0.0), images2)
+    torch.cuda.synchronize()
+    assert torch.equal(images2, case["images"])
+
+
+# --------------------------------------------------------------------------
+# loss (synthetic images: inputs never come from either side's output)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("sizes,lam", [([(64, 64)], 0.2), ([(37, 53)], 0.2),
+                                       ([(40, 30), (17, 33), (64, 48)], 0.2),
+                                       ([(100, 60)], 0.0), ([(33, 20)], 1.0)])
+def test_loss_matches_oracle(sizes, lam):
+    rng = np.random.default_rng(len(sizes) * 100 + sizes[0][0])
+    cams = [scenes.look_at((0, 0, 4), (0, 0, 0), w, h) for w, h in sizes]
+    imgs = [rng.uniform(0, 1.2, (3, h, w)).astype(np.float32) for w, h in sizes]
+    tgts = [rng.uniform(0, 1, (3, h, w)).astype(np.float32) for w, h in sizes]
+    views = T.Views(cams)
+    rast = T.Rasterizer(10, views, 16)
+    im = views.concat([torch.from_numpy(i) for i in imgs]).cuda()
+    tg = views.concat([torch.from_numpy(i) for i in tgts]).cuda()
+    loss = torch.zeros(1, device="cuda")
+    dl = torch.zeros_like(im)
+    rast.loss(im, tg, lam, loss, dl)
+    torch.cuda.synchronize()
+    B_ = len(sizes)
+    Lo, grads = 0.0, []
+    for i, t in zip(imgs, tgts):
+        L, g = oracle.loss(i.astype(np.float64), t.astype(np.float64), lam, grad_scale=1.0 / B_)
+        Lo += L / B_
+        grads.append(g)
+    assert float(loss.item()) == pytest.approx(Lo, rel=2e-6, abs=1e-7)
+    for v, g in enumerate(views.split(dl)):
+        gg = g.cpu().numpy()
+        scale = np.abs(grads[v]).max()
+        assert np.abs(gg - grads[v]).max() <= 2e-5 * scale + 1e-12
+
+
+# --------------------------------------------------------------------------
+# backward: gradients through the C ABI vs the oracle's exact adjoint
+# --------------------------------------------------------------------------
+def _gpu_grads(params, cams, targets, lam=0.2, bg=(0.0, 0.0, 0.0), sh_degree=3):
+    rast, views, t, images = gpu_forward(params, cams, bg=bg, sh_degree=sh_degree)
+    tg = views.concat([torch.from_numpy(x) for x in targets]).cuda()
+    loss = torch.zeros(1, device="cuda")
+    dl = torch.zeros_like(images)
+    rast.loss(images, tg, lam, loss, dl)
+    grads = {k: torch.zeros(t[k].shape, device="cuda") for k in GROUPS}
+    rast.backward(T.params_struct(t), sh_degree, bg, dl, T.params_struct(grads))
+    torch.cuda.synchronize()
+    return float(loss.item()), {k: v.cpu().numpy() for k, v in grads.items()}, rast
+
+
+@pytest.mark.parametrize("name,n,size,bg,deg", [("tiny", 4000, (128, 96), (0, 0, 0), 3),
+                                                ("bg", 3000, (96, 96), (0.2, 0.5, 0.9), 3),
+                                                ("deg1", 3000, (80, 64), (0, 0, 0), 1)])
+def test_gradients_match_oracle(oracle_mod, name, n, size, bg, deg):
+    params = scenes.tiny_scene(n, seed=20 + n)
+    cams = [scenes.tiny_camera(*size)]
+    targets = [scenes.target_image(*size, view=3)]
+    Lg, gg, _ = _gpu_grads(params, cams, targets, bg=bg, sh_degree=deg)
+    Lo, _, go, _, _ = oracle.train_step(cams, params, targets, sh_degree=deg, bg=bg)
+    assert Lg == pytest.approx(Lo, rel=1e-5)
+    for k in GROUPS:
+        if not np.any(go[k]):
+            assert not np.any(gg[k]), k
+            continue
+        assert rel_l2(gg[k], go[k]) <= GRAD_REL_L2, (k, rel_l2(gg[k], go[k]))
+
+
+def test_batched_uneven_views_match_oracle(oracle_mod):
+    params = scenes.tiny_scene(5000, seed=31)
+    sizes = [(120, 90), (77, 101), (64, 64)]
+    cams = [scenes.look_at((0.5 * i, 0.3, 4.0), (0, 0, 0), w, h) for i, (w, h) in enumerate(sizes)]
+    targets = [scenes.target_image(w, h, view=i) for i, (w, h) in enumerate(sizes)]
+    Lg, gg, rast = _gpu_grads(params, cams, targets)
+    Lo, imgs, go, _, _ = oracle.train_step(cams, params, targets)
+    assert Lg == pytest.approx(Lo, rel=1e-5)
+    for k in GROUPS:
+        assert rel_l2(gg[k], go[k]) <= GRAD_REL_L2, (k, rel_l2(gg[k], go[k]))
+
+
+# --------------------------------------------------------------------------
+# Adam
+# --------------------------------------------------------------------------
+def _adam_inputs(n, seed):
+    rng = np.random.default_rng(seed)
+    shapes = {"means": (n, 3), "log_scales": (n, 3), "quats": (n, 4), "opacity": (n,),
+              "sh_dc": (n, 3), "sh_rest": (n, 15, 3)}
+    p = {k: rng.standard_normal(s).astype(np.float32) for k, s in shapes.items()}
+    g = {k: (rng.standard_normal(s) * 10.0 ** rng.uniform(-7, 0, s)).astype(np.float32)
+         for k, s in shapes.items()}
+    for k in g:
+        g[k].reshape(-1)[::13] = 0.0
+    m = {k: (0.1 * rng.standard_normal(s)).astype(np.float32) for k, s in shapes.items()}
+    v = {k: (0.01 * rng.random(s)).astype(np.float32) for k, s in shapes.items()}
+    return p, g, m, v
+
+
+@pytest.mark.parametrize("n,step,device_state", [(1001, 1, False), (4096, 7, False),
+                                                 (777, 3, True)])
+def test_adam_matches_oracle(oracle_mod, n, step, device_state):
+    p, g, m, v = _adam_inputs(n, n + step)
+    lr = T.DEFAULT_LR
+    tp = {k: torch.from_numpy(p[k].copy()).cuda() for k in GROUPS}
+    tg = {k: torch.from_numpy(g[k].copy()).cuda() for k in GROUPS}
+    tm = {k: torch.from_numpy(m[k].copy()).cuda() for k in GROUPS}
+    tv = {k: torch.from_numpy(v[k].copy()).cuda() for k in GROUPS}
+    s = torch.cuda.current_stream().cuda_stream
+    ps, gs, ms, vs = (T.params_struct(x) for x in (tp, tg, tm, tv))
+    if device_state:
+        st = B.fgs_adam_state()
+        for i in range(6):
+            st.lr[i] = lr[i]
+        st.beta1, st.beta2, st.eps, st.step = 0.9, 0.999, 1e-15, step - 1
+        import ctypes
+        buf = torch.frombuffer(bytearray(ctypes.string_at(ctypes.addressof(st), ctypes.sizeof(st))),
+                               dtype=torch.uint8).cuda()
+        B.fgs_adam_step_device(ps, gs, ms, vs, buf.data_ptr(), s)
+    else:
+        B.fgs_adam_step(ps, gs, ms, vs, lr, 0.9, 0.999, 1e-15, step, s)
+    torch.cuda.synchronize()
+    for i, k in enumerate(GROUPS):
+        po = p[k].astype(np.float64).copy()
+        mo = m[k].astype(np.float64).copy()
+        vo = v[k].astype(np.float64).copy()
+        oracle.adam(po.reshape(-1), g[k].astype(np.float64).reshape(-1), mo.reshape(-1),
+                    vo.reshape(-1), lr[i], step)
+        du_g = tp[k].cpu().numpy().astype(np.float64) - p[k]
+        du_o = po - p[k]
+        # update error relative to the learning rate, plus float32 rounding of p
+        assert np.abs(du_g - du_o).max() <= 1e-5 * lr[i] + 2.4e-7 * np.abs(p[k]).max(), k
+        # moments: float32 rounding of the inputs' magnitudes (m may cancel)
+        ulp = 2.0 ** -24
+        m_tol = 4 * ulp * (np.abs(m[k]) + np.abs(g[k])) + 1e-6 * np.abs(mo)
+        assert np.all(np.abs(tm[k].cpu().numpy() - mo) <= m_tol), k
+        v_tol = 4 * ulp * (np.abs(v[k]) + g[k].astype(np.float64) ** 2) + 1e-6 * np.abs(vo)
+        assert np.all(np.abs(tv[k].cpu().numpy() - vo) <= v_tol), k
+
+
+# --------------------------------------------------------------------------
+# full step and graph capture
+# --------------------------------------------------------------------------
+def test_full_step_matches_oracle(oracle_mod):
+    params = scenes.tiny_scene(3000, seed=41)
+    cams = [scenes.tiny_camera(96, 80)]
+    targets = [scenes.target_image(96, 80, view=9)]
+    tr = T.Trainer(params, cams, k_max=200_000)
+    tr.set_targets(targets)
+    tr.step()
+    torch.cuda.synchronize()
+    Lo, _, go, newp, _ = oracle.train_step(cams, params, targets)
+    assert float(tr.loss.item()) == pytest.approx(Lo, rel=1e-5)
+    assert tr.adam_step_count() == 1
+    for i, k in enumerate(GROUPS):
+        got = tr.params[k].cpu().numpy().astype(np.float64)
+        g = go[k]
+        rms = np.sqrt(np.mean(g * g)) if np.any(g) else 0.0
+        robust = np.abs(g) > 1e-2 * rms
+        # first Adam step moves each element by ~lr * sign(g)
+        err = np.abs(got - newp[k])
+        assert err[robust].max() <= 1e-3 * T.DEFAULT_LR[i] + 2.4e-7 * np.abs(newp[k]).max(), k
+        still = g == 0
+        np.testing.assert_array_equal(got[still], np.asarray(params[k], np.float64)[still])
+
+
+def test_graph_replay_matches_eager():
+    params = scenes.tiny_scene(4000, seed=51)
+    cams = [scenes.tiny_camera(128, 128)]
+    targets = [scenes.target_image(128, 128, view=1)]
+    a = T.Trainer(params, cams, k_max=300_000)
+    b = T.Trainer(params, cams, k_max=300_000)
+    a.set_targets(targets)
+    b.set_targets(targets)
+    b.capture(warmup=1)           # one eager warm-up step inside capture()
+    a.step()                      # keep the two trainers in step
+    for _ in range(3):
+        a.step()
+        b.replay()
+    torch.cuda.synchronize()
+    assert a.adam_step_count() == b.adam_step_count() == 4
+    assert float(a.loss.item()) == pytest.approx(float(b.loss.item()), rel=1e-4)
+    for k in GROUPS:
+        assert rel_l2(b.params[k].cpu().numpy(), a.params[k].cpu().numpy()) < 1e-4, k
+    # forward alone is deterministic: replaying the same state gives the same image
+    a.forward_only()
+    img1 = a.images.clone()
+    a.forward_only()
+    assert torch.equal(img1, a.images)
+
+
+# --------------------------------------------------------------------------
+# host-detected errors and the capacity flag
+# --------------------------------------------------------------------------
+def test_capacity_overflow_sets_flag_without_fault():
+    params = scenes.tiny_scene(5000, seed=61)
+    cams = [scenes.tiny_camera(128, 128)]
+    rast, views, t, images = gpu_forward(params, cams, k_max=1000)
+    flags, inst = rast.error(clear=True)
+    assert flags & B.FGS_FLAG_CAPACITY and inst > 1000
+    flags2, _ = rast.error()
+    assert flags2 == 0
+
+
+def test_host_errors_are_reported():
+    params = scenes.tiny_scene(100, seed=62)
+    cams = [scenes.tiny_camera(32, 32)]
+    rast, views, t, images = gpu_forward(params, cams)
+    ps = T.params_struct(t)
+    s = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_render_forward(rast.ws.data_ptr(), rast.layout, ps, 4, views.host,
+                             views.device.data_ptr(), (0, 0, 0), images.data_ptr(), s)
+    assert e.value.code == -3
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_render_forward(rast.ws.data_ptr() + 16, rast.layout, ps, 3, views.host,
+                             views.device.data_ptr(), (0, 0, 0), images.data_ptr(), s)
+    assert e.value.code == -8
+    other = B.fgs_workspace_size(101, views.host, 1, rast.k_max)
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_render_forward(rast.ws.data_ptr(), other, ps, 3, views.host,
+                             views.device.data_ptr(), (0, 0, 0), images.data_ptr(), s)
+    assert e.value.code == -2
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_render_forward(rast.ws.data_ptr(), rast.layout, ps, 3, views.host, None, (0, 0, 0),
+                             images.data_ptr(), s)
+    assert e.value.code == -1
