@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--small", action="store_true",
                     help="small case for profiler captures (300k Gaussians)")
     ap.add_argument("--phase-report", default="", help="write per-kernel timings to this file")
+    ap.add_argument("--kmax", type=int, default=0,
+                    help="instance capacity; 0 = probe every camera and add 25%%")
     return ap.parse_args()
 
 
@@ -222,16 +224,19 @@ def run_ours(args, dist):
     cam_bytes = ctypes.sizeof(B.fgs_camera)
 
     # instance capacity: largest count over the cameras, with margin
-    probe = T.Trainer(params, [cams[0]], k_max=max(1_000_000, 40 * n // 10))
-    kmax_seen = 0
-    for i in range(len(cams)):
-        probe.views.device.copy_(cam_table[i * cam_bytes:(i + 1) * cam_bytes])
-        probe.forward_only()
-        flags, inst = probe.rast.error(clear=True)
-        kmax_seen = max(kmax_seen, inst)
-    del probe
-    torch.cuda.empty_cache()
-    k_max = int(kmax_seen * 1.25) + 4096
+    if args.kmax > 0:
+        k_max = args.kmax
+    else:
+        probe = T.Trainer(params, [cams[0]], k_max=max(1_000_000, 40 * n // 10))
+        kmax_seen = 0
+        for i in range(len(cams)):
+            probe.views.device.copy_(cam_table[i * cam_bytes:(i + 1) * cam_bytes])
+            probe.forward_only()
+            flags, inst = probe.rast.error(clear=True)
+            kmax_seen = max(kmax_seen, inst)
+        del probe
+        torch.cuda.empty_cache()
+        k_max = int(kmax_seen * 1.25) + 4096
 
     tr = T.Trainer(params, [cams[0]], k_max=k_max, lam=0.2)
     stream = torch.cuda.current_stream()

@@ -107,6 +107,33 @@ __device__ __forceinline__ float warp_sum(float x)
     return x;
 }
 
+// Sums eight per-lane values over the warp with 9 shuffles (reduce-scatter:
+// each butterfly step sends half of the remaining values).  Afterwards lane
+// l holds the total of value ((l >> 2) & 7) -- lanes 0, 4, ..., 28 hold
+// values 0..7.
+__device__ __forceinline__ float warp_sum8_scatter(const float v[8], int lane)
+{
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    float a[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float send = h16 ? v[j] : v[j + 4];
+        const float keep = h16 ? v[j + 4] : v[j];
+        a[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float b[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float send = h8 ? a[j] : a[j + 2];
+        const float keep = h8 ? a[j + 2] : a[j];
+        b[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float c = (h4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h4 ? b[0] : b[1], 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
 __global__ void __launch_bounds__(kBlendThreads)
 blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
                  const uint32_t* __restrict__ gids, const Screen* __restrict__ screen, float bg0,
@@ -195,12 +222,11 @@ blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int k = 0; k < 9; ++k) d[k] = warp_sum(d[k]);
-                if (lane == 0) {
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) atomicAdd(&s_acc[k][jj], d[k]);
-                }
+                // value index of lane l after the scatter: (l >> 2) & 7
+                const float part = warp_sum8_scatter(d, lane);
+                const float last_v = warp_sum(d[8]);
+                if ((lane & 3) == 0) atomicAdd(&s_acc[(lane >> 2) & 7][jj], part);
+                if (lane == 1) atomicAdd(&s_acc[8][jj], last_v);
             }
         }
         __syncthreads();

@@ -46,22 +46,104 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     return base + x - v;
 }
 
-template <typename SHT>
-__device__ __forceinline__ void load_sh(const SHT* __restrict__ sh_dc, const SHT* __restrict__ sh_rest,
-                                        int64_t i, int degree, float sh[16][3])
+constexpr int kBigRect = 32;  // rectangles with more tiles are culled by the whole warp
+
+// Per-view screen geometry of one Gaussian (Eq. 1-2, Suppl. B.1 tests,
+// Suppl. C dilation, Sec. 3.2 opacity-aware rectangle).
+struct Geo {
+    float mx, my, ca, cb, cc, k, depth;
+    int tx0, ty0, tw, ntiles;  // tile rectangle (ntiles = 0: not rendered)
+};
+
+__device__ __forceinline__ void project(const Cam& cam, const float mu[3], const float M[9], float o,
+                                        Geo& g)
 {
+    g.ntiles = 0;
+    float t[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) sh[0][c] = to_f32(sh_dc[3 * i + c]);
-    const int ncoef = (degree + 1) * (degree + 1);
+    for (int r = 0; r < 3; ++r)
+        t[r] = cam.R[3 * r] * mu[0] + cam.R[3 * r + 1] * mu[1] + cam.R[3 * r + 2] * mu[2] + cam.t[r];
+    if (!(t[2] > cam.near_plane)) return;
+    const float iz = 1.0f / t[2];
+    // Eq. 2: J (2x3) and T2 = J Rcam; M2 = T2 M, Sigma2D = M2 M2^T
+    const float j00 = cam.fx * iz, j02 = -cam.fx * t[0] * iz * iz;
+    const float j11 = cam.fy * iz, j12 = -cam.fy * t[1] * iz * iz;
+    float T2[6];
 #pragma unroll
-    for (int k = 1; k < 16; ++k)
+    for (int c = 0; c < 3; ++c) {
+        T2[c] = j00 * cam.R[c] + j02 * cam.R[6 + c];
+        T2[3 + c] = j11 * cam.R[3 + c] + j12 * cam.R[6 + c];
+    }
+    float M2[6];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            sh[k][c] = k < ncoef ? to_f32(sh_rest[45 * i + 3 * (k - 1) + c]) : 0.0f;
+            M2[3 * r + c] = T2[3 * r] * M[c] + T2[3 * r + 1] * M[3 + c] + T2[3 * r + 2] * M[6 + c];
+    const float ca = M2[0] * M2[0] + M2[1] * M2[1] + M2[2] * M2[2];
+    const float cb = M2[0] * M2[3] + M2[1] * M2[4] + M2[2] * M2[5];
+    const float cc = M2[3] * M2[3] + M2[4] * M2[4] + M2[5] * M2[5];
+    // Cauchy-Binet: det(M2 M2^T) = sum of squared 2x2 minors (no cancellation)
+    const float m01 = M2[0] * M2[4] - M2[1] * M2[3];
+    const float m02 = M2[0] * M2[5] - M2[2] * M2[3];
+    const float m12 = M2[1] * M2[5] - M2[2] * M2[4];
+    const float det2 = m01 * m01 + m02 * m02 + m12 * m12;
+    if (!(det2 >= kDetMin)) return;
+    const float da = ca + kDilation, dc = cc + kDilation;
+    const float detd = det2 + kDilation * (ca + cc) + kDilation * kDilation;
+    const float idet = 1.0f / detd;
+    g.ca = dc * idet;
+    g.cb = -cb * idet;
+    g.cc = da * idet;
+    g.mx = cam.fx * t[0] * iz + cam.cx;
+    g.my = cam.fy * t[1] * iz + cam.cy;
+    g.depth = t[2];
+    g.k = fmaxf(2.0f * __logf(255.0f * o), 0.0f);
+    const float ex = sqrtf(g.k * da), ey = sqrtf(g.k * dc);
+    const float u0 = fmaxf(ceilf(g.mx - ex - 0.5f), 0.0f);
+    const float u1 = fminf(floorf(g.mx + ex - 0.5f), (float)(cam.width - 1));
+    const float v0 = fmaxf(ceilf(g.my - ey - 0.5f), 0.0f);
+    const float v1 = fminf(floorf(g.my + ey - 0.5f), (float)(cam.height - 1));
+    if (!(u0 <= u1 && v0 <= v1)) return;
+    g.tx0 = (int)u0 / kTile;
+    g.ty0 = (int)v0 / kTile;
+    g.tw = (int)u1 / kTile - g.tx0 + 1;
+    g.ntiles = g.tw * ((int)v1 / kTile - g.ty0 + 1);
+}
+
+// Kept tiles of one Gaussian: the thread alone for small rectangles; for
+// large ones every lane of the warp takes a stride of the rectangle and the
+// counts are reduced (the warp must be converged; `g` is per lane).
+__device__ __forceinline__ uint32_t count_tiles(const Geo& g, bool has, int width, int height)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t count = 0;
+    const bool big = has && g.ntiles > kBigRect;
+    if (has && !big) {
+        for (int t = 0; t < g.ntiles; ++t)
+            count += tile_keep(g.mx, g.my, g.ca, g.cb, g.cc, g.k, g.tx0 + t % g.tw, g.ty0 + t / g.tw,
+                               width, height);
+    }
+    unsigned bigmask = __ballot_sync(0xffffffffu, big);
+    while (bigmask) {
+        const int src = __ffs(bigmask) - 1;
+        bigmask &= bigmask - 1;
+        const float mx = __shfl_sync(0xffffffffu, g.mx, src), my = __shfl_sync(0xffffffffu, g.my, src);
+        const float a = __shfl_sync(0xffffffffu, g.ca, src), b = __shfl_sync(0xffffffffu, g.cb, src);
+        const float c = __shfl_sync(0xffffffffu, g.cc, src), k = __shfl_sync(0xffffffffu, g.k, src);
+        const int tx0 = __shfl_sync(0xffffffffu, g.tx0, src), ty0 = __shfl_sync(0xffffffffu, g.ty0, src);
+        const int tw = __shfl_sync(0xffffffffu, g.tw, src), nt = __shfl_sync(0xffffffffu, g.ntiles, src);
+        uint32_t part = 0;
+        for (int t = lane; t < nt; t += 32)
+            part += tile_keep(mx, my, a, b, c, k, tx0 + t % tw, ty0 + t / tw, width, height);
+        part = __reduce_add_sync(0xffffffffu, part);
+        if (lane == src) count = part;
+    }
+    return count;
 }
 
 template <typename SHT>
-__global__ void __launch_bounds__(kPreBlock)
+__global__ void __launch_bounds__(kPreBlock, 3)
 preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
                       const float* __restrict__ log_scales, const float* __restrict__ quats,
                       const float* __restrict__ opac, const SHT* __restrict__ sh_dc,
@@ -95,98 +177,48 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
         o = 1.0f / (1.0f + __expf(-opac[i]));
         ok = qn >= kQNormMin && o >= kAlphaMin;
     }
-    float sh[16][3];
-    bool sh_loaded = false;
+    const int ncoef = (sh_degree + 1) * (sh_degree + 1);
     for (int v = 0; v < vt.n_views; ++v) {
-        uint32_t count = 0;
+        const Cam cam = load_cam(cams, v);
+        Geo g;
+        g.ntiles = 0;
+        if (ok) project(cam, mu, M, o, g);
+        const bool has = g.ntiles > 0;
+        const uint32_t count = count_tiles(g, has, cam.width, cam.height);
         Screen rec;
         rec.q0 = make_float4(0.f, 0.f, 0.f, 0.f);
         rec.q1 = make_float4(0.f, 0.f, 0.f, 0.f);
         rec.q2 = make_float4(0.f, 0.f, 0.f, 0.f);
         ushort4 rect = make_ushort4(1, 1, 0, 0);
-        if (ok) {
-            const Cam cam = load_cam(cams, v);
-            float t[3];
+        if (count > 0) {
+            rect = make_ushort4((unsigned short)g.tx0, (unsigned short)g.ty0,
+                                (unsigned short)(g.tx0 + g.tw - 1),
+                                (unsigned short)(g.ty0 + g.ntiles / g.tw - 1));
+            // SH colour from the view direction, streamed from memory
+            float d0 = mu[0] - cam.pos[0], d1 = mu[1] - cam.pos[1], d2 = mu[2] - cam.pos[2];
+            const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            d0 *= il; d1 *= il; d2 *= il;
+            float Y[16];
+            sh_basis(d0, d1, d2, sh_degree, Y);
+            float r0 = 0.5f + Y[0] * to_f32(sh_dc[3 * i]);
+            float r1 = 0.5f + Y[0] * to_f32(sh_dc[3 * i + 1]);
+            float r2 = 0.5f + Y[0] * to_f32(sh_dc[3 * i + 2]);
+            const SHT* rest = sh_rest + 45 * i;
 #pragma unroll
-            for (int r = 0; r < 3; ++r)
-                t[r] = cam.R[3 * r] * mu[0] + cam.R[3 * r + 1] * mu[1] + cam.R[3 * r + 2] * mu[2] + cam.t[r];
-            if (t[2] > cam.near_plane) {
-                const float iz = 1.0f / t[2];
-                // Eq. 2: J (2x3) and T2 = J Rcam; M2 = T2 M, Sigma2D = M2 M2^T
-                const float j00 = cam.fx * iz, j02 = -cam.fx * t[0] * iz * iz;
-                const float j11 = cam.fy * iz, j12 = -cam.fy * t[1] * iz * iz;
-                float T2[6];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    T2[c] = j00 * cam.R[c] + j02 * cam.R[6 + c];
-                    T2[3 + c] = j11 * cam.R[3 + c] + j12 * cam.R[6 + c];
-                }
-                float M2[6];
-#pragma unroll
-                for (int r = 0; r < 2; ++r)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        M2[3 * r + c] = T2[3 * r] * M[c] + T2[3 * r + 1] * M[3 + c] + T2[3 * r + 2] * M[6 + c];
-                const float ca = M2[0] * M2[0] + M2[1] * M2[1] + M2[2] * M2[2];
-                const float cb = M2[0] * M2[3] + M2[1] * M2[4] + M2[2] * M2[5];
-                const float cc = M2[3] * M2[3] + M2[4] * M2[4] + M2[5] * M2[5];
-                // Cauchy-Binet: det(M2 M2^T) = sum of squared 2x2 minors
-                const float m01 = M2[0] * M2[4] - M2[1] * M2[3];
-                const float m02 = M2[0] * M2[5] - M2[2] * M2[3];
-                const float m12 = M2[1] * M2[5] - M2[2] * M2[4];
-                const float det2 = m01 * m01 + m02 * m02 + m12 * m12;
-                if (det2 >= kDetMin) {
-                    const float da = ca + kDilation, dc = cc + kDilation;
-                    const float detd = det2 + kDilation * (ca + cc) + kDilation * kDilation;
-                    const float idet = 1.0f / detd;
-                    const float conic_a = dc * idet, conic_b = -cb * idet, conic_c = da * idet;
-                    const float mx = cam.fx * t[0] * iz + cam.cx;
-                    const float my = cam.fy * t[1] * iz + cam.cy;
-                    const float k = fmaxf(2.0f * __logf(255.0f * o), 0.0f);
-                    const float ex = sqrtf(k * da), ey = sqrtf(k * dc);
-                    const float u0 = fmaxf(ceilf(mx - ex - 0.5f), 0.0f);
-                    const float u1 = fminf(floorf(mx + ex - 0.5f), (float)(cam.width - 1));
-                    const float v0 = fmaxf(ceilf(my - ey - 0.5f), 0.0f);
-                    const float v1 = fminf(floorf(my + ey - 0.5f), (float)(cam.height - 1));
-                    if (u0 <= u1 && v0 <= v1) {
-                        const int tx0 = (int)u0 / kTile, tx1 = (int)u1 / kTile;
-                        const int ty0 = (int)v0 / kTile, ty1 = (int)v1 / kTile;
-                        for (int ty = ty0; ty <= ty1; ++ty)
-                            for (int tx = tx0; tx <= tx1; ++tx)
-                                count += tile_keep(mx, my, conic_a, conic_b, conic_c, k, tx, ty,
-                                                   cam.width, cam.height);
-                        if (count > 0) {
-                            rect = make_ushort4((unsigned short)tx0, (unsigned short)ty0,
-                                                (unsigned short)tx1, (unsigned short)ty1);
-                            if (!sh_loaded) {
-                                load_sh(sh_dc, sh_rest, i, sh_degree, sh);
-                                sh_loaded = true;
-                            }
-                            float d0 = mu[0] - cam.pos[0], d1 = mu[1] - cam.pos[1], d2 = mu[2] - cam.pos[2];
-                            const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-                            d0 *= il; d1 *= il; d2 *= il;
-                            float Y[16];
-                            sh_basis(d0, d1, d2, sh_degree, Y);
-                            float rgb[3];
-                            uint32_t bits = 8u;  // visible
-#pragma unroll
-                            for (int ch = 0; ch < 3; ++ch) {
-                                float acc = 0.5f;
-#pragma unroll
-                                for (int kk = 0; kk < 16; ++kk) acc += Y[kk] * sh[kk][ch];
-                                if (acc < 0.0f) {
-                                    bits |= 1u << ch;
-                                    acc = 0.0f;
-                                }
-                                rgb[ch] = acc;
-                            }
-                            rec.q0 = make_float4(mx, my, conic_a, conic_b);
-                            rec.q1 = make_float4(conic_c, o, k, t[2]);
-                            rec.q2 = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float(bits));
-                        }
-                    }
+            for (int kk = 1; kk < 16; ++kk) {
+                if (kk < ncoef) {
+                    r0 += Y[kk] * to_f32(rest[3 * (kk - 1)]);
+                    r1 += Y[kk] * to_f32(rest[3 * (kk - 1) + 1]);
+                    r2 += Y[kk] * to_f32(rest[3 * (kk - 1) + 2]);
                 }
             }
+            uint32_t bits = 8u;  // visible
+            if (r0 < 0.f) { bits |= 1u; r0 = 0.f; }
+            if (r1 < 0.f) { bits |= 2u; r1 = 0.f; }
+            if (r2 < 0.f) { bits |= 4u; r2 = 0.f; }
+            rec.q0 = make_float4(g.mx, g.my, g.ca, g.cb);
+            rec.q1 = make_float4(g.cc, o, g.k, g.depth);
+            rec.q2 = make_float4(r0, r1, r2, __uint_as_float(bits));
         }
         const int64_t vi = (int64_t)v * n + i;
         if (valid) {
@@ -234,6 +266,10 @@ scan_block_sums_kernel(uint32_t* __restrict__ block_sum, int64_t count, WsHeader
     }
 }
 
+// Emits (global tile << 32 | depth bits, Gaussian id) for every kept tile
+// of every (view, Gaussian), in row-major tile order at the scanned offset.
+// Large rectangles are emitted by the whole warp, 32 tiles per step, with a
+// ballot prefix keeping the row-major order.
 __global__ void __launch_bounds__(256)
 duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
                  const ushort4* __restrict__ rects, const uint32_t* __restrict__ local_off,
@@ -241,34 +277,95 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
                  unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals)
 {
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= (int64_t)vt.n_views * n) return;
-    const int v = (int)(gi / n);
-    const int64_t i = gi - (int64_t)v * n;
-    const float4 q2 = screen[gi].q2;
-    if (!(__float_as_uint(q2.w) & 8u)) return;
-    const float4 q0 = screen[gi].q0;
-    const float4 q1 = screen[gi].q1;
-    const ushort4 r = rects[gi];
-    uint64_t off = (uint64_t)local_off[gi] + block_sum[(int64_t)v * nblk + i / kPreBlock];
-    const unsigned long long depth_bits = __float_as_uint(q1.w);
-    const int width = vt.width[v], height = vt.height[v], tx_n = vt.tiles_x[v], toff = vt.tile_off[v];
-    for (int ty = r.y; ty <= r.w; ++ty)
-        for (int tx = r.x; tx <= r.z; ++tx) {
+    const int lane = threadIdx.x & 31;
+    const bool valid = gi < (int64_t)vt.n_views * n;
+    int v = 0;
+    int64_t i = 0;
+    bool vis = false;
+    float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
+    ushort4 r = make_ushort4(1, 1, 0, 0);
+    uint64_t off = 0;
+    if (valid) {
+        v = (int)(gi / n);
+        i = gi - (int64_t)v * n;
+        vis = (__float_as_uint(screen[gi].q2.w) & 8u) != 0;
+        if (vis) {
+            q0 = screen[gi].q0;
+            q1 = screen[gi].q1;
+            r = rects[gi];
+            off = (uint64_t)local_off[gi] + block_sum[(int64_t)v * nblk + i / kPreBlock];
+        }
+    }
+    const int tw = (int)r.z - (int)r.x + 1;
+    const int nt = vis ? tw * ((int)r.w - (int)r.y + 1) : 0;
+    const bool big = vis && nt > kBigRect;
+    if (vis && !big) {
+        const int width = vt.width[v], height = vt.height[v];
+        const unsigned long long depth_bits = __float_as_uint(q1.w);
+        const unsigned long long toff = (unsigned long long)vt.tile_off[v];
+        const int tx_n = vt.tiles_x[v];
+        for (int t = 0; t < nt; ++t) {
+            const int tx = r.x + t % tw, ty = r.y + t / tw;
             if (!tile_keep(q0.x, q0.y, q0.z, q0.w, q1.x, q1.z, tx, ty, width, height)) continue;
             if (off < (uint64_t)k_max) {
-                const unsigned long long tile = (unsigned long long)(toff + ty * tx_n + tx);
-                keys[off] = (tile << 32) | depth_bits;
+                keys[off] = ((toff + ty * tx_n + tx) << 32) | depth_bits;
                 vals[off] = (uint32_t)i;
             }
             ++off;
         }
+    }
+    unsigned bigmask = __ballot_sync(0xffffffffu, big);
+    while (bigmask) {
+        const int src = __ffs(bigmask) - 1;
+        bigmask &= bigmask - 1;
+        const float mx = __shfl_sync(0xffffffffu, q0.x, src), my = __shfl_sync(0xffffffffu, q0.y, src);
+        const float a = __shfl_sync(0xffffffffu, q0.z, src), b = __shfl_sync(0xffffffffu, q0.w, src);
+        const float c = __shfl_sync(0xffffffffu, q1.x, src), k = __shfl_sync(0xffffffffu, q1.z, src);
+        const unsigned long long depth_bits = __float_as_uint(__shfl_sync(0xffffffffu, q1.w, src));
+        const int sv = __shfl_sync(0xffffffffu, v, src);
+        const uint32_t sid = (uint32_t)__shfl_sync(0xffffffffu, (unsigned long long)i, src);
+        const int tx0 = __shfl_sync(0xffffffffu, (int)r.x, src), ty0 = __shfl_sync(0xffffffffu, (int)r.y, src);
+        const int stw = __shfl_sync(0xffffffffu, tw, src), snt = __shfl_sync(0xffffffffu, nt, src);
+        uint64_t soff = __shfl_sync(0xffffffffu, (unsigned long long)off, src);
+        const int width = vt.width[sv], height = vt.height[sv], tx_n = vt.tiles_x[sv];
+        const unsigned long long toff = (unsigned long long)vt.tile_off[sv];
+        for (int base = 0; base < snt; base += 32) {
+            const int t = base + lane;
+            const int tx = tx0 + t % stw, ty = ty0 + t / stw;
+            const bool keep = t < snt && tile_keep(mx, my, a, b, c, k, tx, ty, width, height);
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            const uint64_t pos = soff + __popc(m & ((1u << lane) - 1u));
+            if (keep && pos < (uint64_t)k_max) {
+                keys[pos] = ((toff + ty * tx_n + tx) << 32) | depth_bits;
+                vals[pos] = sid;
+            }
+            soff += __popc(m);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Backward of the preprocessing (chain rule, summed over views)
 // ---------------------------------------------------------------------------
+constexpr int kBwdBlock = 128;
+
+// dir, colour gradient (clamped channels masked) of one visible view.
+__device__ __forceinline__ void view_colour_grad(const Cam& cam, const float mu[3], uint32_t bits,
+                                                 const ScreenGrad& g, float d[3], float& il,
+                                                 float grgb[3])
+{
+    d[0] = mu[0] - cam.pos[0];
+    d[1] = mu[1] - cam.pos[1];
+    d[2] = mu[2] - cam.pos[2];
+    il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    d[0] *= il; d[1] *= il; d[2] *= il;
+    grgb[0] = (bits & 1u) ? 0.f : g.g1.z;
+    grgb[1] = (bits & 2u) ? 0.f : g.g1.w;
+    grgb[2] = (bits & 4u) ? 0.f : g.g2.x;
+}
+
 template <typename SHT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kBwdBlock)
 preprocess_bwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
                       const float* __restrict__ log_scales, const float* __restrict__ quats,
                       const float* __restrict__ opac, const SHT* __restrict__ sh_dc,
@@ -279,161 +376,150 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
                       float* __restrict__ g_opac, float* __restrict__ g_dc,
                       float* __restrict__ g_rest)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    __shared__ float s_rest[kBwdBlock * 45];
+    const int64_t i0 = (int64_t)blockIdx.x * kBwdBlock;
+    const int64_t i = i0 + threadIdx.x;
+    const bool valid = i < n;
     float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
     float gw = 0.f;
-    float gsh[16][3];
+    float gdc[3] = {0.f, 0.f, 0.f};
+    uint32_t vis_mask = 0;
+    if (valid)
+        for (int v = 0; v < vt.n_views; ++v)
+            if (__float_as_uint(screen[(int64_t)v * n + i].q2.w) & 8u) vis_mask |= 1u << v;
+    float mu[3] = {0.f, 0.f, 0.f};
+    const int ncoef = (sh_degree + 1) * (sh_degree + 1);
+    if (vis_mask) {
+        mu[0] = means[3 * i]; mu[1] = means[3 * i + 1]; mu[2] = means[3 * i + 2];
+        const float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+        const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        const float inv = 1.0f / qn;
+        const float qh[4] = {qw * inv, qx * inv, qy * inv, qz * inv};
+        float Rq[9], s[3], M[9];
+        quat_to_rot(qh[0], qh[1], qh[2], qh[3], Rq);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
-    bool any = false;
-    float mu[3], qh[4], qn = 0.f, s[3], Rq[9], M[9], o = 0.f;
-    float sh[16][3];
-    for (int v = 0; v < vt.n_views; ++v) {
-        const int64_t vi = (int64_t)v * n + i;
-        const Screen rec = screen[vi];
-        const uint32_t bits = __float_as_uint(rec.q2.w);
-        if (!(bits & 8u)) continue;
-        const ScreenGrad g = sgrad[vi];
-        if (!any) {
-            any = true;
-            mu[0] = means[3 * i]; mu[1] = means[3 * i + 1]; mu[2] = means[3 * i + 2];
-            const float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
-            qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-            const float inv = 1.0f / qn;
-            qh[0] = qw * inv; qh[1] = qx * inv; qh[2] = qy * inv; qh[3] = qz * inv;
-            quat_to_rot(qh[0], qh[1], qh[2], qh[3], Rq);
+        for (int a = 0; a < 3; ++a) s[a] = __expf(log_scales[3 * i + a]);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) s[a] = __expf(log_scales[3 * i + a]);
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) M[3 * r + c] = Rq[3 * r + c] * s[c];
+        float dM_acc[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) dM_acc[a] = 0.f;
+        for (int v = 0; v < vt.n_views; ++v) {
+            if (!(vis_mask >> v & 1u)) continue;
+            const int64_t vi = (int64_t)v * n + i;
+            const Screen rec = screen[vi];
+            const uint32_t bits = __float_as_uint(rec.q2.w);
+            const ScreenGrad g = sgrad[vi];
+            const Cam cam = load_cam(cams, v);
+            const float o = rec.q1.y;
+            float t[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                t[r] = cam.R[3 * r] * mu[0] + cam.R[3 * r + 1] * mu[1] + cam.R[3 * r + 2] * mu[2] + cam.t[r];
+            const float iz = 1.0f / t[2], iz2 = iz * iz;
+            float dmu[3] = {0.f, 0.f, 0.f}, dt[3] = {0.f, 0.f, 0.f};
+
+            // opacity: o = sigmoid(w)
+            gw += g.g1.y * o * (1.0f - o);
+
+            // colour -> view direction -> mean
+            {
+                float d[3], il, grgb[3];
+                view_colour_grad(cam, mu, bits, g, d, il, grgb);
+                float coef[16];
+#pragma unroll
+                for (int kk = 0; kk < 16; ++kk) coef[kk] = 0.f;
+#pragma unroll
+                for (int kk = 1; kk < 16; ++kk) {
+                    if (kk < ncoef) {
+                        const SHT* r3 = sh_rest + 45 * i + 3 * (kk - 1);
+                        coef[kk] = to_f32(r3[0]) * grgb[0] + to_f32(r3[1]) * grgb[1] + to_f32(r3[2]) * grgb[2];
+                    }
+                }
+                float gd[3];
+                sh_dir_grad(d[0], d[1], d[2], sh_degree, coef, gd);
+                const float dd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) dmu[a] += (gd[a] - d[a] * dd) * il;
+                // band 0 (Y_0 is constant)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) gdc[c] += SHC::c0 * grgb[c];
+            }
+
+            // Eq. 1: mu2D = (fx tx/tz + cx, fy ty/tz + cy)
+            const float gx = g.g0.x, gy = g.g0.y;
+            dt[0] += gx * cam.fx * iz;
+            dt[1] += gy * cam.fy * iz;
+            dt[2] += -(gx * cam.fx * t[0] + gy * cam.fy * t[1]) * iz2;
+
+            // conic = (Sigma2D + 0.3 I)^-1 : dSigma = -conic G conic, with G
+            // the full symmetric gradient [[ga, gb/2], [gb/2, gc]]
+            const float ca = rec.q0.z, cb = rec.q0.w, cc = rec.q1.x;
+            const float ga = g.g0.z, gb = 0.5f * g.g0.w, gc = g.g1.x;
+            const float P00 = ca * ga + cb * gb, P01 = ca * gb + cb * gc;
+            const float P10 = cb * ga + cc * gb, P11 = cb * gb + cc * gc;
+            const float S00 = -(P00 * ca + P01 * cb);
+            const float S01 = -(P00 * cb + P01 * cc);
+            const float S11 = -(P10 * cb + P11 * cc);
+
+            // Sigma2D = T2 Sigma T2^T = (T2 M)(T2 M)^T with T2 = J Rcam
+            const float j00 = cam.fx * iz, j02 = -cam.fx * t[0] * iz2;
+            const float j11 = cam.fy * iz, j12 = -cam.fy * t[1] * iz2;
+            float T2[6];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                T2[c] = j00 * cam.R[c] + j02 * cam.R[6 + c];
+                T2[3 + c] = j11 * cam.R[3 + c] + j12 * cam.R[6 + c];
+            }
+            float M2[6];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    M2[3 * r + c] = T2[3 * r] * M[c] + T2[3 * r + 1] * M[3 + c] + T2[3 * r + 2] * M[6 + c];
+            // dL/dM2 = 2 GS M2; dL/dT2 = dM2 M^T; dL/dM = T2^T dM2
+            float dM2[6];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dM2[c] = 2.0f * (S00 * M2[c] + S01 * M2[3 + c]);
+                dM2[3 + c] = 2.0f * (S01 * M2[c] + S11 * M2[3 + c]);
+            }
+            float dT2[6];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    dT2[3 * r + c] = dM2[3 * r] * M[3 * c] + dM2[3 * r + 1] * M[3 * c + 1] +
+                                     dM2[3 * r + 2] * M[3 * c + 2];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) M[3 * r + c] = Rq[3 * r + c] * s[c];
-            o = rec.q1.y;
-            load_sh(sh_dc, sh_rest, i, sh_degree, sh);
+                for (int c = 0; c < 3; ++c) dM_acc[3 * r + c] += T2[r] * dM2[c] + T2[3 + r] * dM2[3 + c];
+            // dJ = dT2 Rcam^T ; J entries used: j00, j02, j11, j12
+            const float dj00 = dT2[0] * cam.R[0] + dT2[1] * cam.R[1] + dT2[2] * cam.R[2];
+            const float dj02 = dT2[0] * cam.R[6] + dT2[1] * cam.R[7] + dT2[2] * cam.R[8];
+            const float dj11 = dT2[3] * cam.R[3] + dT2[4] * cam.R[4] + dT2[5] * cam.R[5];
+            const float dj12 = dT2[3] * cam.R[6] + dT2[4] * cam.R[7] + dT2[5] * cam.R[8];
+            dt[0] += -dj02 * cam.fx * iz2;
+            dt[1] += -dj12 * cam.fy * iz2;
+            dt[2] += -dj00 * cam.fx * iz2 + 2.0f * dj02 * cam.fx * t[0] * iz2 * iz -
+                     dj11 * cam.fy * iz2 + 2.0f * dj12 * cam.fy * t[1] * iz2 * iz;
+            // t = Rcam mu + tcam
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                gmu[a] += dmu[a] + cam.R[a] * dt[0] + cam.R[3 + a] * dt[1] + cam.R[6 + a] * dt[2];
         }
-        const Cam cam = load_cam(cams, v);
-        float t[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-            t[r] = cam.R[3 * r] * mu[0] + cam.R[3 * r + 1] * mu[1] + cam.R[3 * r + 2] * mu[2] + cam.t[r];
-        const float iz = 1.0f / t[2], iz2 = iz * iz;
-        float dmu[3] = {0.f, 0.f, 0.f}, dt[3] = {0.f, 0.f, 0.f};
-
-        // opacity: o = sigmoid(w)
-        gw += g.g1.y * o * (1.0f - o);
-
-        // colour: rgb_c = max(0, sum_k Y_k sh_kc + 0.5)
-        {
-            float d0 = mu[0] - cam.pos[0], d1 = mu[1] - cam.pos[1], d2 = mu[2] - cam.pos[2];
-            const float len = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-            const float il = 1.0f / len;
-            d0 *= il; d1 *= il; d2 *= il;
-            float Y[16];
-            sh_basis(d0, d1, d2, sh_degree, Y);
-            const float grgb[3] = {(bits & 1u) ? 0.f : g.g1.z, (bits & 2u) ? 0.f : g.g1.w,
-                                   (bits & 4u) ? 0.f : g.g2.x};
-            float coef[16];
-#pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-                coef[kk] = 0.f;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    gsh[kk][ch] += Y[kk] * grgb[ch];
-                    coef[kk] += sh[kk][ch] * grgb[ch];
-                }
-            }
-            float gd[3];
-            sh_dir_grad(d0, d1, d2, sh_degree, coef, gd);
-            const float dd = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
-            dmu[0] += (gd[0] - d0 * dd) * il;
-            dmu[1] += (gd[1] - d1 * dd) * il;
-            dmu[2] += (gd[2] - d2 * dd) * il;
-        }
-
-        // Eq. 1: mu2D = (fx tx/tz + cx, fy ty/tz + cy)
-        const float gx = g.g0.x, gy = g.g0.y;
-        dt[0] += gx * cam.fx * iz;
-        dt[1] += gy * cam.fy * iz;
-        dt[2] += -(gx * cam.fx * t[0] + gy * cam.fy * t[1]) * iz2;
-
-        // conic = (Sigma2D + 0.3 I)^-1 : dSigma = -conic G conic, with G the
-        // full symmetric gradient [[ga, gb/2], [gb/2, gc]]
-        const float ca = rec.q0.z, cb = rec.q0.w, cc = rec.q1.x;
-        const float ga = g.g0.z, gb = 0.5f * g.g0.w, gc = g.g1.x;
-        const float P00 = ca * ga + cb * gb, P01 = ca * gb + cb * gc;
-        const float P10 = cb * ga + cc * gb, P11 = cb * gb + cc * gc;
-        const float S00 = -(P00 * ca + P01 * cb);
-        const float S01 = -(P00 * cb + P01 * cc);
-        const float S11 = -(P10 * cb + P11 * cc);
-
-        // Sigma2D = T2 Sigma T2^T with T2 = J Rcam, Sigma = M M^T
-        const float j00 = cam.fx * iz, j02 = -cam.fx * t[0] * iz2;
-        const float j11 = cam.fy * iz, j12 = -cam.fy * t[1] * iz2;
-        float T2[6];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            T2[c] = j00 * cam.R[c] + j02 * cam.R[6 + c];
-            T2[3 + c] = j11 * cam.R[3 + c] + j12 * cam.R[6 + c];
-        }
-        float Sig[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                Sig[3 * r + c] = M[3 * r] * M[3 * c] + M[3 * r + 1] * M[3 * c + 1] + M[3 * r + 2] * M[3 * c + 2];
-        // U = T2 Sigma (2x3); dT2 = 2 GS U
-        float U[6];
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                U[3 * r + c] = T2[3 * r] * Sig[c] + T2[3 * r + 1] * Sig[3 + c] + T2[3 * r + 2] * Sig[6 + c];
-        float dT2[6];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            dT2[c] = 2.0f * (S00 * U[c] + S01 * U[3 + c]);
-            dT2[3 + c] = 2.0f * (S01 * U[c] + S11 * U[3 + c]);
-        }
-        // dSigma = T2^T GS T2
-        float dSig[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const float a0 = S00 * T2[r] + S01 * T2[3 + r];
-            const float a1 = S01 * T2[r] + S11 * T2[3 + r];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) dSig[3 * r + c] = a0 * T2[c] + a1 * T2[3 + c];
-        }
-        // dJ = dT2 Rcam^T ; J entries used: j00, j02, j11, j12
-        const float dj00 = dT2[0] * cam.R[0] + dT2[1] * cam.R[1] + dT2[2] * cam.R[2];
-        const float dj02 = dT2[0] * cam.R[6] + dT2[1] * cam.R[7] + dT2[2] * cam.R[8];
-        const float dj11 = dT2[3] * cam.R[3] + dT2[4] * cam.R[4] + dT2[5] * cam.R[5];
-        const float dj12 = dT2[3] * cam.R[6] + dT2[4] * cam.R[7] + dT2[5] * cam.R[8];
-        dt[0] += -dj02 * cam.fx * iz2;
-        dt[1] += -dj12 * cam.fy * iz2;
-        dt[2] += -dj00 * cam.fx * iz2 + 2.0f * dj02 * cam.fx * t[0] * iz2 * iz -
-                 dj11 * cam.fy * iz2 + 2.0f * dj12 * cam.fy * t[1] * iz2 * iz;
-        // t = Rcam mu + tcam
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            dmu[a] += cam.R[a] * dt[0] + cam.R[3 + a] * dt[1] + cam.R[6 + a] * dt[2];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) gmu[a] += dmu[a];
-        // Sigma = M M^T: dM = 2 dSigma M (dSigma symmetric); M = Rq S
-        float dM[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                dM[3 * r + c] = 2.0f * (dSig[3 * r] * M[c] + dSig[3 * r + 1] * M[3 + c] + dSig[3 * r + 2] * M[6 + c]);
+        // M = Rq S: dS, dRq -> log-scales and the quaternion
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            gls[c] += (dM[c] * Rq[c] + dM[3 + c] * Rq[3 + c] + dM[6 + c] * Rq[6 + c]) * s[c];
+            gls[c] = (dM_acc[c] * Rq[c] + dM_acc[3 + c] * Rq[3 + c] + dM_acc[6 + c] * Rq[6 + c]) * s[c];
         float G[9];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) G[3 * r + c] = dM[3 * r + c] * s[c];
+            for (int c = 0; c < 3; ++c) G[3 * r + c] = dM_acc[3 * r + c] * s[c];
         const float w = qh[0], x = qh[1], y = qh[2], z = qh[3];
         float dq[4];
         dq[0] = 2.0f * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
@@ -445,22 +531,64 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
                         y * G[5] + x * G[6] + y * G[7]);
         const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) gq[a] += (dq[a] - qh[a] * qd) / qn;
+        for (int a = 0; a < 4; ++a) gq[a] = (dq[a] - qh[a] * qd) / qn;
     }
+    // SH bands 1..3: d/dsh_kc = sum_v Y_k(dir_v) grgb_vc, four coefficients at a
+    // time, staged in shared memory for coalesced stores
+    float* my = s_rest + 45 * threadIdx.x;
+    for (int kb = 1; kb < 16; kb += 5) {
+        float acc[5][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        g_means[3 * i + a] = gmu[a];
-        g_scales[3 * i + a] = gls[a];
+        for (int q = 0; q < 5; ++q) acc[q][0] = acc[q][1] = acc[q][2] = 0.f;
+        if (vis_mask && kb < ncoef) {
+            for (int v = 0; v < vt.n_views; ++v) {
+                if (!(vis_mask >> v & 1u)) continue;
+                const int64_t vi = (int64_t)v * n + i;
+                const uint32_t bits = __float_as_uint(screen[vi].q2.w);
+                const ScreenGrad g = sgrad[vi];
+                const Cam cam = load_cam(cams, v);
+                float d[3], il, grgb[3];
+                view_colour_grad(cam, mu, bits, g, d, il, grgb);
+                float Y[16];
+                sh_basis(d[0], d[1], d[2], sh_degree, Y);
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[q][c] += Y[kb + q] * grgb[c];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) my[3 * (kb - 1 + q) + c] = acc[q][c];
     }
+    if (valid) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) g_quats[4 * i + a] = gq[a];
-    g_opac[i] = gw;
+        for (int a = 0; a < 3; ++a) {
+            g_means[3 * i + a] = gmu[a];
+            g_scales[3 * i + a] = gls[a];
+            g_dc[3 * i + a] = gdc[a];
+        }
+        if (((uintptr_t)g_quats & 15) == 0) {
+            *reinterpret_cast<float4*>(g_quats + 4 * i) = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        } else {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) g_dc[3 * i + c] = gsh[0][c];
-#pragma unroll
-    for (int k = 1; k < 16; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) g_rest[45 * i + 3 * (k - 1) + c] = gsh[k][c];
+            for (int a = 0; a < 4; ++a) g_quats[4 * i + a] = gq[a];
+        }
+        g_opac[i] = gw;
+    }
+    __syncthreads();
+    // coalesced copy of the block's sh_rest gradients (128 * 45 floats)
+    const int64_t cnt = min((int64_t)kBwdBlock, n - i0) * 45;
+    float* dst = g_rest + i0 * 45;
+    if (((uintptr_t)dst & 15) == 0) {
+        const int64_t c4 = cnt / 4;
+        for (int64_t e = threadIdx.x; e < c4; e += kBwdBlock)
+            reinterpret_cast<float4*>(dst)[e] = reinterpret_cast<const float4*>(s_rest)[e];
+        for (int64_t e = 4 * c4 + threadIdx.x; e < cnt; e += kBwdBlock) dst[e] = s_rest[e];
+    } else {
+        for (int64_t e = threadIdx.x; e < cnt; e += kBwdBlock) dst[e] = s_rest[e];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -517,8 +645,8 @@ static cudaError_t launch_pre_bwd_t(int64_t n, int deg, const fgs_params* p, con
                                     const ViewTable& vt, const Screen* screen,
                                     const ScreenGrad* sgrad, const fgs_params* g, cudaStream_t st)
 {
-    const int grid = (int)((n + 127) / 128);
-    preprocess_bwd_kernel<SHT><<<grid, 128, 0, st>>>(
+    const int grid = (int)((n + kBwdBlock - 1) / kBwdBlock);
+    preprocess_bwd_kernel<SHT><<<grid, kBwdBlock, 0, st>>>(
         n, deg, (const float*)p->data[0], (const float*)p->data[1], (const float*)p->data[2],
         (const float*)p->data[3], (const SHT*)p->data[4], (const SHT*)p->data[5], cams, vt, screen,
         sgrad, (float*)g->data[0], (float*)g->data[1], (float*)g->data[2], (float*)g->data[3],
