@@ -54,7 +54,8 @@ enum fgs_status {
     FGS_ERR_CUDA = -6,       /* a kernel launch failed */
     FGS_ERR_VIEWS = -7,      /* n_views outside 1..FGS_MAX_VIEWS */
     FGS_ERR_ALIGN = -8,      /* a pointer is not 16-byte aligned */
-    FGS_ERR_ARG = -9         /* another argument is out of range */
+    FGS_ERR_ARG = -9,        /* another argument is out of range */
+    FGS_ERR_TOO_LARGE = -10  /* more pairs than fgs_sort_pairs_static can hold */
 };
 
 /* Sticky bits set on the device, read by fgs_get_error. */
@@ -223,6 +224,27 @@ size_t fgs_sort_scratch_bytes(int64_t n);
 int fgs_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                    int64_t n, int32_t bits, void *scratch, size_t scratch_bytes,
                    int32_t *result_in_alt, void *stream);
+
+/* The same stable radix sort for callers that cannot allocate device
+ * memory on the path where they sort -- for instance a host framework that
+ * owns every device allocation through its own pool and forbids raw
+ * cudaMalloc from plug-ins, or latency-critical code that cannot afford the
+ * device-wide synchronisation cudaMalloc and cudaFree imply.  The paper has
+ * no counterpart; this is a deployment variant of fgs_sort_pairs.
+ *
+ * keys[n] / vals[n] (device) are sorted in place on their low `bits` bits.
+ * All scratch is one library-owned array of FGS_STATIC_SORT_MAX_PAIRS pairs
+ * (about 12.3 MB: keys and values ping-pong buffers plus histograms), held
+ * by every GPU that loads the library until the process exits; the call
+ * allocates nothing.  n > FGS_STATIC_SORT_MAX_PAIRS returns
+ * FGS_ERR_TOO_LARGE before any launch; n == 0 returns FGS_OK.
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make it before any stream capture on that device.
+ * Every call uses the same array: calls whose kernels overlap on the GPU
+ * (different streams, or different host threads, without ordering between
+ * them) race on it and corrupt each other's results. */
+#define FGS_STATIC_SORT_MAX_PAIRS (1 << 20)
+int fgs_sort_pairs_static(uint64_t *keys, uint32_t *vals, int64_t n, int32_t bits, void *stream);
 
 /* Synchronises `stream`, then reads the workspace header: sticky device
  * flags (FGS_FLAG_*) and the instance count of the last forward.  Either

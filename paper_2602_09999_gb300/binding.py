@@ -29,11 +29,13 @@ FGS_FLAG_CAPACITY = 1
 
 STATUS = {0: "FGS_OK", -1: "FGS_ERR_NULL", -2: "FGS_ERR_SHAPE", -3: "FGS_ERR_SH_DEGREE",
           -4: "FGS_ERR_WORKSPACE", -5: "FGS_ERR_DTYPE", -6: "FGS_ERR_CUDA", -7: "FGS_ERR_VIEWS",
-          -8: "FGS_ERR_ALIGN", -9: "FGS_ERR_ARG"}
+          -8: "FGS_ERR_ALIGN", -9: "FGS_ERR_ARG", -10: "FGS_ERR_TOO_LARGE"}
+FGS_STATIC_SORT_MAX_PAIRS = 1 << 20
 
 EXPORTED = ("fgs_workspace_size", "fgs_render_forward", "fgs_loss_l1_dssim",
             "fgs_render_backward", "fgs_adam_step", "fgs_adam_step_device",
-            "fgs_sort_scratch_bytes", "fgs_sort_pairs", "fgs_get_error", "fgs_profile_attach",
+            "fgs_sort_scratch_bytes", "fgs_sort_pairs", "fgs_sort_pairs_static", "fgs_get_error",
+            "fgs_profile_attach",
             "fgs_profile_count", "fgs_strerror")
 
 
@@ -106,6 +108,7 @@ def lib():
             L.fgs_sort_scratch_bytes.argtypes = [I64]
             L.fgs_sort_scratch_bytes.restype = SZ
             L.fgs_sort_pairs.argtypes = [P, P, P, P, I64, I32, P, SZ, P, P]
+            L.fgs_sort_pairs_static.argtypes = [P, P, I64, I32, P]
             L.fgs_get_error.argtypes = [P, P, P, I32, P]
             L.fgs_profile_attach.argtypes = [P, P, I32]
             L.fgs_profile_count.argtypes = []
@@ -198,6 +201,12 @@ def fgs_sort_pairs(keys, vals, keys_alt, vals_alt, n, bits, scratch, scratch_byt
            lib().fgs_sort_pairs(keys, vals, keys_alt, vals_alt, int(n), int(bits), scratch,
                                 int(scratch_bytes), ctypes.byref(alt), stream))
     return int(alt.value)
+
+
+def fgs_sort_pairs_static(keys, vals, n, bits, stream):
+    """In-place sort with the library's own scratch (no allocation)."""
+    _check("fgs_sort_pairs_static",
+           lib().fgs_sort_pairs_static(keys, vals, int(n), int(bits), stream))
 
 
 def fgs_get_error(ws, clear=False, stream=None):

@@ -400,6 +400,7 @@ const char* fgs_strerror(int code)
     case FGS_ERR_VIEWS: return "view count outside 1..16";
     case FGS_ERR_ALIGN: return "pointer not aligned";
     case FGS_ERR_ARG: return "argument out of range";
+    case FGS_ERR_TOO_LARGE: return "more pairs than the static sort scratch holds";
     default: return "unknown status";
     }
 }
