@@ -51,7 +51,7 @@ typedef struct {
  * decide the other way (all zero = pure FP64 decisions, nothing flagged). */
 typedef struct {
     double rel;        /* relative margin for scalar threshold tests */
-    double q_rel;      /* rounding of a quadratic form, relative to the sum of |terms| */
+    double q_rel;      /* rounding of a quadratic form, relative to its error scale */
     double pos_rel;    /* error of mu2D relative to max(1, |mu2D|) (pixels) */
     double px;         /* absolute margin (pixels) for rectangle edges */
     double t_rel;      /* relative margin for the transmittance stop test */
@@ -347,11 +347,38 @@ static void gauss_forward(const orc_camera *cam, int sh_degree, int64_t i,
     g->marginal = marginal;
 }
 
+/* Size of the float32 rounding error of q(d) = d^T C d, C = [[a, b], [b, c]]
+ * positive definite, when C is held as its eigenvalues lb >= ls and the
+ * angle of its eigenvectors: with u, w the offsets along the eigenvectors of
+ * ls and lb, each eigenvalue carries a relative error of a few ulps, which
+ * moves the form by that fraction of ls u^2 + lb w^2 = q, and the angle an
+ * absolute error of a few ulps (radians), which moves it by that amount times
+ * |dq/dangle| = 2 (lb - ls) |u w|.  (Held as the entries a, b, c instead, the
+ * error would be a fraction of |a dx^2| + |2 b dx dy| + |c dy^2|, far larger
+ * along a needle-like splat, where a c - b^2 cancels.) */
+static double form_error_scale(double a, double b, double c, double dx, double dy)
+{
+    const double half = sqrt(0.25 * (a - c) * (a - c) + b * b);
+    const double lb = 0.5 * (a + c) + half;
+    const double ls = (a * c - b * b) / lb;
+    /* unit eigenvector of lb: (b, lb - a) or (lb - c, b), whichever is longer */
+    double ex = b, ey = lb - a;
+    if (fabs(lb - c) + fabs(b) > fabs(ex) + fabs(ey)) { ex = lb - c; ey = b; }
+    const double nrm = sqrt(ex * ex + ey * ey);
+    double w = dx, u = dy;
+    if (nrm > 0.0) {
+        w = (ex * dx + ey * dy) / nrm;
+        u = (ex * dy - ey * dx) / nrm;
+    }
+    return ls * u * u + lb * w * w + 2.0 * (lb - ls) * fabs(u * w);
+}
+
 /* Minimum of q(d) = d^T C d over the box [x0,x1] x [y0,y1] of offsets d,
  * for a positive definite C = [[a, b], [b, c]].  Zero if the origin is
  * inside; otherwise the minimum over the four edges, each a clamped 1D
- * quadratic.  Also returns, at the minimiser, the sum of |terms| and
- * |C d| (1-norm), which size the float32 error of the value. */
+ * quadratic.  Also returns, at the minimiser, the float32 error scale of the
+ * form (form_error_scale) and |C d| (1-norm), its sensitivity to the
+ * position of the mean. */
 static double box_qmin(double a, double b, double c, double x0, double x1, double y0, double y1,
                        double *mag, double *grad)
 {
@@ -367,7 +394,7 @@ static double box_qmin(double a, double b, double c, double x0, double x1, doubl
         double q = a * X * X + 2.0 * b * X * Yv + c * Yv * Yv;
         if (q < best) {
             best = q;
-            bmag = fabs(a * X * X) + fabs(2.0 * b * X * Yv) + fabs(c * Yv * Yv);
+            bmag = form_error_scale(a, b, c, X, Yv);
             bgrad = fabs(a * X + b * Yv) + fabs(b * X + c * Yv);
         }
         /* edge y = ys[e]: minimise over x */
@@ -378,7 +405,7 @@ static double box_qmin(double a, double b, double c, double x0, double x1, doubl
         q = a * Xv * Xv + 2.0 * b * Xv * Yf + c * Yf * Yf;
         if (q < best) {
             best = q;
-            bmag = fabs(a * Xv * Xv) + fabs(2.0 * b * Xv * Yf) + fabs(c * Yf * Yf);
+            bmag = form_error_scale(a, b, c, Xv, Yf);
             bgrad = fabs(a * Xv + b * Yf) + fabs(b * Xv + c * Yf);
         }
     }
@@ -548,14 +575,17 @@ static void pixel_walk(double px, double py, int64_t start, int64_t end, const i
         const double qa = conic[3 * g] * dx * dx;
         const double qb = 2.0 * conic[3 * g + 1] * dx * dy;
         const double qc = conic[3 * g + 2] * dy * dy;
-        const double mag = fabs(qa) + fabs(qb) + fabs(qc);
         const double power = -0.5 * (qa + qb + qc);
         const double oG = opac[g] * exp(power);
         /* relative float32 error of o G: opacity and exp rounding, the
-         * rounding of the quadratic form and the position error of mu2D */
+         * rounding of the form (form_error_scale) and the position error of
+         * mu2D */
         const double pos_err = mg->pos_rel * fmax(1.0, fmax(fabs(xy[2 * g]), fabs(xy[2 * g + 1])));
         const double grad = fabs(conic[3 * g] * dx + conic[3 * g + 1] * dy) +
                             fabs(conic[3 * g + 1] * dx + conic[3 * g + 2] * dy);
+        const double mag = mg->q_rel > 0.0
+                               ? form_error_scale(conic[3 * g], conic[3 * g + 1], conic[3 * g + 2], dx, dy)
+                               : 0.0;
         const double slack = mg->rel + 0.5 * mg->q_rel * mag + pos_err * grad;
         if (!keep || (f & ORC_IMARGINAL)) {
             /* a candidate float32 may decide differently: flag the pixel
