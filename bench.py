@@ -48,7 +48,9 @@ def parse_args():
     ap.add_argument("--gaussians", type=int, default=3_000_000)
     ap.add_argument("--width", type=int, default=1237)
     ap.add_argument("--height", type=int, default=822)
-    ap.add_argument("--batch", type=int, default=4, help="views per step of the batched variant")
+    ap.add_argument("--batch", type=int, nargs="+", default=[4, 8],
+                    help="views per step of the batched variants")
+    ap.add_argument("--no-tune", action="store_true", help="default launch configuration")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -193,6 +195,19 @@ def algorithmic_bytes(label, n, views, instances, pixels, sh_bytes, moment_bytes
     return None
 
 
+# FP32 operations per unit of the blend kernels (an FMA counts 2): one alpha
+# evaluation per list position up to a pixel's last contributor (offset,
+# quadratic form, exp2 argument, o G: 12), and per blended fragment the
+# forward's accumulation (9) or the backward's adjoint (T recovery, dalpha,
+# colour behind, nine gradient terms: 50).
+BLEND_FLOPS = {"blend_fwd": (12, 9), "blend_bwd": (12, 50)}
+
+
+def fp32_peak_tflops(sm_count, sm_mhz):
+    """128 FP32 lanes per SM, one FMA (2 ops) per lane per clock."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def adam_bytes_per_group(n, widths=(3, 3, 4, 1, 3, 45), p_bytes=(4, 4, 4, 4, 4, 4), m_bytes=4):
     """p read+write, g read, m and v read+write."""
     return [n * w * (2 * pb + 4 + 4 * m_bytes) for w, pb in zip(widths, p_bytes)]
@@ -240,6 +255,11 @@ def run_ours(args, dist):
 
     tr = T.Trainer(params, [cams[0]], k_max=k_max, lam=0.2)
     stream = torch.cuda.current_stream()
+    tuned = None
+    if not args.no_tune:
+        from paper_2602_09999_gb300 import tune
+        tr.targets.copy_(targets[0])
+        tuned = tune.autotune(tr, reps=3)
 
     def one_step(i):
         tr.views.device.copy_(cam_table[(i % len(cams)) * cam_bytes:((i % len(cams)) + 1) * cam_bytes])
@@ -320,13 +340,43 @@ def run_ours(args, dist):
         scr = tr.rast.screen()[0]
         bits = scr[:, 11].contiguous().view(torch.int32)
         visible_est = int(((bits & 8) != 0).sum().item())
-        if dom == "adam":
+        if dom in BLEND_FLOPS:
+            # fragment counts of every camera the timed region visited
+            visits = {}
+            for i in range(args.steps):
+                c = (args.warmup + i) % len(cams)
+                visits[c] = visits.get(c, 0) + 1
+            ev = bl = 0.0
+            for c, cnt in visits.items():
+                tr.views.device.copy_(cam_table[c * cam_bytes:(c + 1) * cam_bytes])
+                tr.forward_only()
+                a, b = tr.rast.fragment_counts()
+                ev += a * cnt
+                bl += b * cnt
+            ev /= args.steps
+            bl /= args.steps
+            f_eval, f_blend = BLEND_FLOPS[dom]
+            flops = f_eval * ev + f_blend * bl
+            props = torch.cuda.get_device_properties(dev)
+            sm_mhz = float(clocks.get("sm_max_mhz") or 2070.0)
+            peak = fp32_peak_tflops(props.multi_processor_count, sm_mhz)
+            achieved = flops / (avg_ms / 1000.0) / 1e12
+            roofline = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3),
+                        "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                        "traffic": None, "peak_source": "derived: SMs x 128 FP32 lanes x 2 x "
+                                                        f"{sm_mhz:.0f} MHz",
+                        "avg_launch_ms": round(avg_ms, 5),
+                        "algorithmic_flops_per_launch": int(flops),
+                        "evaluations_per_launch": int(ev), "blended_per_launch": int(bl)}
+        elif dom == "adam":
             # six launches per step, one per group; average over all of them
             tot_bytes = sum(adam_bytes_per_group(n))
             alg = tot_bytes / 6.0
         else:
             alg = algorithmic_bytes(dom, n, 1, inst_last, pixels, 4, 4, visible_est)
-        if alg is not None:
+        if dom in BLEND_FLOPS:
+            pass
+        elif alg is not None:
             achieved = alg / (avg_ms / 1000.0) / 1e9
             roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
                         "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
@@ -372,15 +422,20 @@ def run_ours(args, dist):
                "h2d_bytes_per_step": 3 * W * H * 4 + cam_bytes, "d2h_bytes_per_step": 4,
                "steps": steps_e2e}
 
-    # batched variant: B views per step, CUDA graph, bf16 SH and moments
-    batched = None
+    # batched variants: B views per step, CUDA graph, bf16 SH and moments
+    batched = []
     if not args.no_batched:
         del tr
         torch.cuda.empty_cache()
-        Bv = args.batch
+    for Bv in ([] if args.no_batched else args.batch):
+        torch.cuda.empty_cache()
         tb = T.Trainer(params, cams[:Bv], k_max=int(k_max * Bv), lam=0.2,
                        sh_dtype=torch.bfloat16, moment_dtype=torch.bfloat16)
         tb.targets.copy_(targets[:Bv].reshape(-1)[:tb.targets.numel()])
+        tb_tuned = None
+        if not args.no_tune:
+            from paper_2602_09999_gb300 import tune
+            tb_tuned = tune.autotune(tb, reps=2)
         ncam = len(cams) // Bv
 
         def load_batch(i):
@@ -410,12 +465,15 @@ def run_ours(args, dist):
         if tb.rast.error()[0]:
             raise RuntimeError("capacity exceeded in the batched variant")
         bvps = dist.world * steps_b * Bv / (bms / 1000.0)
-        batched = {"views_per_s": round(bvps, 3), "ms_per_step": round(bms / steps_b, 4),
-                   "views_per_step": Bv, "resolution": f"{W}x{H}", "graph": True,
-                   "storage": "bf16 SH parameters, bf16 Adam moments", "steps": steps_b,
-                   "ratio_vs_plain": round(bvps / views_per_s, 4)}
+        batched.append({"views_per_s": round(bvps, 3), "ms_per_step": round(bms / steps_b, 4),
+                        "views_per_step": Bv, "resolution": f"{W}x{H}", "graph": True,
+                        "storage": "bf16 SH parameters, bf16 Adam moments", "steps": steps_b,
+                        "blend_config": list(tb_tuned[0]) if tb_tuned else None,
+                        "ratio_vs_plain": round(bvps / views_per_s, 4)})
+        del tb
 
-    return dict(ms_per_step=ms_per_step, views_per_s=views_per_s, elapsed_ms=max_ms,
+    return dict(tuned=list(tuned[0]) if tuned else None, tuning_ms=tuned[1] if tuned else None,
+                ms_per_step=ms_per_step, views_per_s=views_per_s, elapsed_ms=max_ms,
                 phase_ms=phase_ms, launches_per_step=launches / max(args.steps, 1),
                 launches=launches, roofline=roofline, clocks=clocks, e2e=e2e, batched=batched,
                 k_max=k_max, instances_last=inst_last, visible_last=visible_est, n=n)
@@ -522,7 +580,8 @@ def main():
                 "data": "synthetic (seeded outdoor-shaped scene, orbit cameras, uniform targets)",
                 "config": config_dict(args, n), "clocks": r["clocks"], "e2e": r["e2e"],
                 "gpu_launches": r["launches"], "roofline": r["roofline"], "cpu_baseline": cpu,
-                "batched": r["batched"], "kernel_ms_per_step": r["phase_ms"],
+                "batched": r["batched"], "blend_config": r["tuned"],
+                "blend_config_ms": r["tuning_ms"], "kernel_ms_per_step": r["phase_ms"],
                 "instances_last_step": r["instances_last"], "k_max": r["k_max"]}
         print(json.dumps(line), flush=True)
         if args.phase_report:

@@ -96,8 +96,8 @@ typedef struct fgs_params {
  * forward (may exceed k_max), uint32 counters. */
 enum fgs_ws_slot {
     FGS_WS_HEADER = 0,
-    FGS_WS_SCREEN,      /* 48-byte records [n_views*n]: float4 (mu2D, conic a, b),
-                           float4 (conic c, o, k = 2 ln(255 o), depth),
+    FGS_WS_SCREEN,      /* 48-byte records [n_views*n]: float4 (mu2D, conic eigenvalues lb >= ls),
+                           float4 (major-axis angle, o, k = 2 ln(255 o), depth),
                            float4 (rgb, bits: clamp mask 0..2, visible 3) */
     FGS_WS_RECT,        /* ushort4 [n_views*n]: tile rectangle x0, y0, x1, y1 (inclusive) */
     FGS_WS_LOCAL_OFF,   /* uint32 [n_views*n]: CTA-local exclusive prefix of tile counts */
@@ -110,12 +110,26 @@ enum fgs_ws_slot {
     FGS_WS_RANGES,      /* uint2 [total_tiles]: [start, end) of each tile's list */
     FGS_WS_T_FINAL,     /* float [total_pixels]: final transmittance */
     FGS_WS_N_CONTRIB,   /* uint32 [total_pixels]: list position of the last blended entry */
-    FGS_WS_SCREEN_GRAD, /* 48-byte records [n_views*n]: float4 dL/d(mu2D, conic a, b),
-                           float4 dL/d(conic c, o, r, g), float4 (dL/db, 0, 0, 0) */
+    FGS_WS_SCREEN_GRAD, /* 48-byte records [n_views*n]: float4 (dL/dmu2D, dL/dSigma2D 00, 01),
+                           float4 (dL/dSigma2D 11, dL/do, dL/dr, dL/dg), float4 (dL/db, 0, 0, 0);
+                           dL/dSigma2D is the full symmetric gradient */
     FGS_WS_LOSS_MAPS,   /* float [9*total_pixels]: SSIM partial-derivative maps */
     FGS_WS_LOSS_PART,   /* double [loss blocks*2]: per-CTA L1 / SSIM sums */
+    FGS_WS_N_BLENDED,   /* uint32 [total_pixels]: fragments blended into each pixel */
     FGS_WS_NUM_SLOTS
 };
+
+/* Launch choices that change speed, never results: pixels each blend thread
+ * owns (1, 2 or 4; the CTA of a 16x16 tile has 256 / that many threads) and
+ * list entries staged per shared-memory batch (64, 128 or 256).  Supported
+ * pairs: (1,256) (2,128) (2,256) (4,64) (4,128) (4,256).  fgs_workspace_size
+ * fills the defaults; an autotuner may overwrite them in the layout before
+ * the calls that use it. */
+typedef struct fgs_tuning {
+    int32_t blend_pixels_per_thread;
+    int32_t blend_batch;
+    int32_t reserved[6];
+} fgs_tuning;
 
 typedef struct fgs_workspace_layout {
     size_t total_bytes;
@@ -128,6 +142,7 @@ typedef struct fgs_workspace_layout {
     int64_t total_pixels;
     int32_t sort_bits;       /* key bits the radix sort orders */
     int32_t sorted_in_alt;   /* 1: sorted keys/values end in the *_ALT slots */
+    fgs_tuning tuning;       /* launch choices (defaults filled in) */
 } fgs_workspace_layout;
 
 /* Workspace size and layout for n Gaussians, n_views host cameras and an

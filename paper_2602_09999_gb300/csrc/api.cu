@@ -27,11 +27,15 @@ cudaError_t launch_tile_ranges(const unsigned long long* keys, const uint32_t* n
                                uint2* ranges, int total_tiles, cudaStream_t st);
 cudaError_t launch_blend_fwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                              const Screen* screen, const float bg[3], float* images, float* T_final,
-                             uint32_t* n_contrib, cudaStream_t st);
+                             uint32_t* n_contrib, uint32_t* n_blended, int ppt, int batch,
+                             cudaStream_t st);
 cudaError_t launch_blend_bwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                              const Screen* screen, const float bg[3], const float* dL_dimg,
                              const float* T_final, const uint32_t* n_contrib, ScreenGrad* sgrad,
-                             cudaStream_t st);
+                             int ppt, int batch, cudaStream_t st);
+bool blend_config_supported(int ppt, int batch);
+
+static const int kDefaultPPT = 2, kDefaultBatch = 128;
 cudaError_t launch_loss(const ViewTable& vt, const float* images, const float* targets, float lambda,
                         float* maps, double* partials, float* loss_out, float* dL, cudaStream_t st);
 cudaError_t launch_adam_group(int64_t count, int pdt, int mdt, void* p, const float* g, void* m,
@@ -135,6 +139,7 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     sz[FGS_WS_SCREEN_GRAD] = sizeof(ScreenGrad) * (size_t)vn;
     sz[FGS_WS_LOSS_MAPS] = sizeof(float) * 9 * (size_t)vt->total_pixels;
     sz[FGS_WS_LOSS_PART] = sizeof(double) * 2 * (size_t)vt->total_tiles;
+    sz[FGS_WS_N_BLENDED] = sizeof(uint32_t) * (size_t)vt->total_pixels;
     size_t off = 0;
     for (int s = 0; s < FGS_WS_NUM_SLOTS; ++s) {
         L->offset[s] = off;
@@ -149,6 +154,8 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     L->total_pixels = vt->total_pixels;
     L->sort_bits = sort_bits_for(vt->total_tiles);
     L->sorted_in_alt = ((L->sort_bits + 7) / 8) & 1;
+    L->tuning.blend_pixels_per_thread = kDefaultPPT;
+    L->tuning.blend_batch = kDefaultBatch;
     return FGS_OK;
 }
 
@@ -162,6 +169,8 @@ static int check_layout(void* ws, const fgs_workspace_layout* L, const fgs_camer
     if (rc != FGS_OK) return rc;
     if (memcmp(mine.offset, L->offset, sizeof(mine.offset)) != 0 || mine.total_bytes != L->total_bytes)
         return FGS_ERR_WORKSPACE;
+    if (!blend_config_supported(L->tuning.blend_pixels_per_thread, L->tuning.blend_batch))
+        return FGS_ERR_ARG;
     return FGS_OK;
 }
 
@@ -239,7 +248,9 @@ int fgs_render_forward(void* ws, const fgs_workspace_layout* L, const fgs_params
         return rc;
     return cuda_rc(launch_blend_fwd(vt, n, ranges, svals, screen, bg, images,
                                     slot<float>(ws, L, FGS_WS_T_FINAL),
-                                    slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB), st));
+                                    slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB),
+                                    slot<uint32_t>(ws, L, FGS_WS_N_BLENDED),
+                                    L->tuning.blend_pixels_per_thread, L->tuning.blend_batch, st));
 }
 
 int fgs_loss_l1_dssim(void* ws, const fgs_workspace_layout* L, const fgs_camera* cams_host,
@@ -280,7 +291,9 @@ int fgs_render_backward(void* ws, const fgs_workspace_layout* L, const fgs_param
     profile_mark(st, "zero_screen_grads");
     if ((rc = cuda_rc(launch_blend_bwd(vt, n, slot<uint2>(ws, L, FGS_WS_RANGES), svals, screen, bg,
                                        dl_dimages, slot<float>(ws, L, FGS_WS_T_FINAL),
-                                       slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB), sgrad, st))) != FGS_OK)
+                                       slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB), sgrad,
+                                       L->tuning.blend_pixels_per_thread, L->tuning.blend_batch,
+                                       st))) != FGS_OK)
         return rc;
     return cuda_rc(launch_preprocess_bwd(n, sh_degree, params, cams_device, vt, screen, sgrad, grads, st));
 }

@@ -9,7 +9,11 @@
 // the blend instead of storing per-fragment state.
 //
 // Backward (Sec. 3.2 "Per-Gaussian Backward" discusses the cost of the
-// atomics this design reduces): the CTA walks the same list back to front
+// atomics this design reduces).  The per-Gaussian screen gradient it
+// accumulates is dL/dSigma2D directly, dpow (C d)(C d)^T / 2 per fragment,
+// instead of dL/dconic followed by -C G C: for needle-like splats the conic
+// gradient is large and C G C cancels by orders of magnitude in float32,
+// while C d is well conditioned.  The CTA walks the same list back to front
 // from the largest last-contributor position of its pixels; each pixel
 // recovers T_i = T_{i+1} / (1 - alpha_i) and the colour behind it,
 // A_i = alpha_{i+1} c_{i+1} + (1 - alpha_{i+1}) A_{i+1} (A = bg behind the
@@ -22,81 +26,175 @@
 namespace fgs {
 
 constexpr int kBlendThreads = kTilePixels;  // 256
+constexpr float kLog2e = 1.4426950408889634f;
 
-struct TilePix {
-    int v, tile_local, px, py, W, H;
-    bool inside;
+// One list entry staged in shared memory: mean, the conic's eigen form
+// pre-scaled for exp2 (A = -ls log2(e) / 2, B = -lb log2(e) / 2), the
+// major-axis direction (cos, sin), colour and opacity.
+struct Entry {
+    float2 xy;
+    float4 coef;  // A, B, cos, sin
+    float4 rgbo;  // r, g, b, o
 };
 
-__device__ __forceinline__ TilePix tile_pixel(const ViewTable& vt, int tile)
+template <int PPT> struct TileMap {
+    static constexpr int NT = kTilePixels / PPT;
+    static constexpr int NW = NT / 32;
+    static constexpr int R = 2 * PPT;
+    int v, W, H, x0, y0, px;
+    int py[PPT];
+    bool inside[PPT];
+    // Thread -> pixel map with PPT pixels per thread: the CTA covers one
+    // 16x16 tile; warp w covers rows [R w, R w + R) with R = 2 PPT, lane l
+    // the column l & 15 and the rows (l >> 4) + 2 k, k < PPT.
+    __device__ __forceinline__ TileMap(const ViewTable& vt, int tile)
+    {
+        v = view_of_tile(vt, tile);
+        const int lt = tile - vt.tile_off[v];
+        x0 = (lt % vt.tiles_x[v]) * kTile;
+        y0 = (lt / vt.tiles_x[v]) * kTile;
+        W = vt.width[v];
+        H = vt.height[v];
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        px = x0 + (lane & 15);
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            py[k] = y0 + R * w + (lane >> 4) + 2 * k;
+            inside[k] = px < W && py[k] < H;
+        }
+    }
+};
+
+// Bit w set when the bounding box of the ellipse d^T conic d <= k (where
+// alpha can reach 1/255), widened by 1% and 0.01 px against float32
+// rounding of the alpha test, meets the pixel rows of warp w.  The vertical
+// half-extent is sqrt(k Sigma_yy) with Sigma_yy = s^2 / ls + c^2 / lb.
+__device__ __forceinline__ uint32_t warp_row_mask(const Screen& rec, int y0, int R, int nw)
 {
-    TilePix t;
-    t.v = view_of_tile(vt, tile);
-    t.tile_local = tile - vt.tile_off[t.v];
-    const int tx = t.tile_local % vt.tiles_x[t.v], ty = t.tile_local / vt.tiles_x[t.v];
-    t.px = tx * kTile + (threadIdx.x % kTile);
-    t.py = ty * kTile + (threadIdx.x / kTile);
-    t.W = vt.width[t.v];
-    t.H = vt.height[t.v];
-    t.inside = t.px < t.W && t.py < t.H;
-    return t;
+    float sn, cs;
+    sincosf(rec.q1.x, &sn, &cs);
+    const float syy = sn * sn / rec.q0.w + cs * cs / rec.q0.z;
+    const float ey = sqrtf(rec.q1.z * syy) * 1.01f + 0.01f;
+    const float my = rec.q0.y;
+    if (!(ey == ey)) return 0xffu;
+    uint32_t m = 0;
+    for (int w = 0; w < nw; ++w) {
+        const float r0 = (float)(y0 + R * w) + 0.5f, r1 = r0 + (float)(R - 1);
+        if (my + ey >= r0 && my - ey <= r1) m |= 1u << w;
+    }
+    return m;
 }
 
-__global__ void __launch_bounds__(kBlendThreads)
+__device__ __forceinline__ void stage_entry(const Screen& rec, Entry& e)
+{
+    float sn, cs;
+    sincosf(rec.q1.x, &sn, &cs);
+    e.xy = make_float2(rec.q0.x, rec.q0.y);
+    e.coef = make_float4(-0.5f * kLog2e * rec.q0.w, -0.5f * kLog2e * rec.q0.z, cs, sn);
+    e.rgbo = make_float4(rec.q2.x, rec.q2.y, rec.q2.z, rec.q1.y);
+}
+
+// Alpha of one fragment (Eq. 3 with the 3DGS rules), shared by the forward
+// and the backward so both take the same decisions: skip when the exponent
+// is positive or alpha < 1/255; alpha = min(0.99, o G).  Also returns the
+// offset along (u) and across (w) the major axis for the backward.
+__device__ __forceinline__ bool eval_frag(float px, float py, const Entry& e, Frag& f, float& u,
+                                          float& w)
+{
+    f.dx = __fsub_rn(px, e.xy.x);
+    f.dy = __fsub_rn(py, e.xy.y);
+    u = __fmaf_rn(e.coef.z, f.dx, __fmul_rn(e.coef.w, f.dy));
+    w = __fmaf_rn(e.coef.z, f.dy, -__fmul_rn(e.coef.w, f.dx));
+    const float l2 = __fmaf_rn(__fmul_rn(e.coef.x, u), u, __fmul_rn(__fmul_rn(e.coef.y, w), w));
+    if (l2 > 0.0f) return false;
+    f.G = exp2f(l2);
+    const float oG = __fmul_rn(e.rgbo.w, f.G);
+    f.clamped = oG >= kAlphaMax;
+    f.alpha = f.clamped ? kAlphaMax : oG;
+    return f.alpha >= kAlphaMin;
+}
+
+template <int PPT, int BATCH>
+__global__ void __launch_bounds__(kTilePixels / PPT)
 blend_fwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
                  const uint32_t* __restrict__ gids, const Screen* __restrict__ screen, float bg0,
                  float bg1, float bg2, float* __restrict__ images, float* __restrict__ T_final,
-                 uint32_t* __restrict__ n_contrib)
+                 uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ n_blended)
 {
-    __shared__ float4 s_q0[kBlendThreads];
-    __shared__ float2 s_co[kBlendThreads];
-    __shared__ float4 s_rgb[kBlendThreads];
+    using Map = TileMap<PPT>;
+    __shared__ Entry s_e[BATCH];
+    __shared__ uint8_t s_mask[BATCH];
     const int tile = blockIdx.x;
-    const TilePix tp = tile_pixel(vt, tile);
+    const Map tm(vt, tile);
+    const int warp = threadIdx.x >> 5;
     const uint2 range = ranges[tile];
-    const float fx = (float)tp.px + 0.5f, fy = (float)tp.py + 0.5f;
-    const Screen* scr = screen + (int64_t)tp.v * n;
-    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0;
-    bool done = !tp.inside;
-    for (uint32_t start = range.x; start < range.y; start += kBlendThreads) {
-        if (__syncthreads_count(done) == kBlendThreads) break;
-        const uint32_t j = start + threadIdx.x;
-        if (j < range.y) {
-            const Screen rec = scr[gids[j]];
-            s_q0[threadIdx.x] = rec.q0;
-            s_co[threadIdx.x] = make_float2(rec.q1.x, rec.q1.y);
-            s_rgb[threadIdx.x] = rec.q2;
+    const Screen* scr = screen + (int64_t)tm.v * n;
+    const float fx = (float)tm.px + 0.5f;
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    uint32_t last[PPT], blended[PPT];
+    bool done[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        T[k] = 1.0f;
+        C0[k] = C1[k] = C2[k] = 0.f;
+        last[k] = 0;
+        blended[k] = 0;
+        done[k] = !tm.inside[k];
+    }
+    for (uint32_t start = range.x; start < range.y; start += BATCH) {
+        bool all_done = true;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) all_done &= done[k];
+        if (__syncthreads_count(all_done) == Map::NT) break;
+        for (int e = threadIdx.x; e < BATCH; e += Map::NT) {
+            const uint32_t j = start + e;
+            if (j < range.y) {
+                const Screen rec = scr[gids[j]];
+                stage_entry(rec, s_e[e]);
+                s_mask[e] = (uint8_t)warp_row_mask(rec, tm.y0, Map::R, Map::NW);
+            }
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)kBlendThreads, range.y - start);
-        for (int jj = 0; !done && jj < cnt; ++jj) {
-            Frag f;
-            const float2 co = s_co[jj];
-            if (!eval_fragment(fx, fy, s_q0[jj], co.x, co.y, f)) continue;
-            const float test = T * (1.0f - f.alpha);
-            if (test < kTMin) {
-                done = true;
-                break;
+        const int cnt = (int)min((uint32_t)BATCH, range.y - start);
+        for (int jj = 0; jj < cnt && !all_done; ++jj) {
+            if (!((s_mask[jj] >> warp) & 1u)) continue;
+            const Entry e = s_e[jj];
+            all_done = true;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (done[k]) continue;
+                Frag f;
+                float u, w;
+                if (eval_frag(fx, (float)tm.py[k] + 0.5f, e, f, u, w)) {
+                    const float test = T[k] * (1.0f - f.alpha);
+                    if (test < kTMin) {
+                        done[k] = true;
+                        continue;
+                    }
+                    const float wt = f.alpha * T[k];
+                    C0[k] += wt * e.rgbo.x;
+                    C1[k] += wt * e.rgbo.y;
+                    C2[k] += wt * e.rgbo.z;
+                    T[k] = test;
+                    last[k] = start + jj - range.x + 1;
+                    ++blended[k];
+                }
+                all_done = false;
             }
-            const float w = f.alpha * T;
-            const float4 c = s_rgb[jj];
-            C0 += w * c.x;
-            C1 += w * c.y;
-            C2 += w * c.z;
-            T = test;
-            last = start + jj - range.x + 1;
         }
     }
-    if (tp.inside) {
-        const int64_t P = (int64_t)tp.W * tp.H;
-        const int64_t pix = (int64_t)tp.py * tp.W + tp.px;
-        float* img = images + 3 * vt.pix_off[tp.v];
-        img[pix] = C0 + T * bg0;
-        img[P + pix] = C1 + T * bg1;
-        img[2 * P + pix] = C2 + T * bg2;
-        T_final[vt.pix_off[tp.v] + pix] = T;
-        n_contrib[vt.pix_off[tp.v] + pix] = last;
+    const int64_t P = (int64_t)tm.W * tm.H;
+    float* img = images + 3 * vt.pix_off[tm.v];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (!tm.inside[k]) continue;
+        const int64_t pix = (int64_t)tm.py[k] * tm.W + tm.px;
+        img[pix] = C0[k] + T[k] * bg0;
+        img[P + pix] = C1[k] + T[k] * bg1;
+        img[2 * P + pix] = C2[k] + T[k] * bg2;
+        T_final[vt.pix_off[tm.v] + pix] = T[k];
+        n_contrib[vt.pix_off[tm.v] + pix] = last[k];
+        n_blended[vt.pix_off[tm.v] + pix] = blended[k];
     }
 }
 
@@ -134,126 +232,185 @@ __device__ __forceinline__ float warp_sum8_scatter(const float v[8], int lane)
     return c;
 }
 
-__global__ void __launch_bounds__(kBlendThreads)
+template <int PPT, int BATCH>
+__global__ void __launch_bounds__(kTilePixels / PPT)
 blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
                  const uint32_t* __restrict__ gids, const Screen* __restrict__ screen, float bg0,
                  float bg1, float bg2, const float* __restrict__ dL_dimg,
                  const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
                  ScreenGrad* __restrict__ sgrad)
 {
-    __shared__ float4 s_q0[kBlendThreads];
-    __shared__ float2 s_co[kBlendThreads];
-    __shared__ float4 s_rgb[kBlendThreads];
-    __shared__ uint32_t s_gid[kBlendThreads];
-    __shared__ float s_acc[9][kBlendThreads];
+    using Map = TileMap<PPT>;
+    __shared__ Entry s_e[BATCH];
+    __shared__ uint8_t s_mask[BATCH];
+    __shared__ uint32_t s_gid[BATCH];
+    __shared__ float s_acc[9][BATCH];
     __shared__ uint32_t s_max;
     const int tile = blockIdx.x;
-    const TilePix tp = tile_pixel(vt, tile);
+    const Map tm(vt, tile);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint2 range = ranges[tile];
-    const float fx = (float)tp.px + 0.5f, fy = (float)tp.py + 0.5f;
-    const Screen* scr = screen + (int64_t)tp.v * n;
-    ScreenGrad* sg = sgrad + (int64_t)tp.v * n;
-    const int lane = threadIdx.x & 31;
+    const Screen* scr = screen + (int64_t)tm.v * n;
+    ScreenGrad* sg = sgrad + (int64_t)tm.v * n;
+    const float fx = (float)tm.px + 0.5f;
+    const int64_t P = (int64_t)tm.W * tm.H;
+    const float* dl = dL_dimg + 3 * vt.pix_off[tm.v];
 
-    float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    uint32_t last = 0;
-    if (tp.inside) {
-        const int64_t P = (int64_t)tp.W * tp.H;
-        const int64_t pix = (int64_t)tp.py * tp.W + tp.px;
-        const float* dl = dL_dimg + 3 * vt.pix_off[tp.v];
-        g0 = dl[pix];
-        g1 = dl[P + pix];
-        g2 = dl[2 * P + pix];
-        T = T_final[vt.pix_off[tp.v] + pix];
-        last = n_contrib[vt.pix_off[tp.v] + pix];
+    float T[PPT], g0[PPT], g1[PPT], g2[PPT], A0[PPT], A1[PPT], A2[PPT];
+    uint32_t last[PPT];
+    uint32_t my_max = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        T[k] = 1.0f;
+        g0[k] = g1[k] = g2[k] = 0.f;
+        last[k] = 0;
+        A0[k] = bg0;  // colour behind, normalised by T after the entry
+        A1[k] = bg1;
+        A2[k] = bg2;
+        if (tm.inside[k]) {
+            const int64_t pix = (int64_t)tm.py[k] * tm.W + tm.px;
+            g0[k] = dl[pix];
+            g1[k] = dl[P + pix];
+            g2[k] = dl[2 * P + pix];
+            T[k] = T_final[vt.pix_off[tm.v] + pix];
+            last[k] = n_contrib[vt.pix_off[tm.v] + pix];
+            my_max = max(my_max, last[k]);
+        }
     }
+    const uint32_t warp_max = __reduce_max_sync(0xffffffffu, my_max);
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    if (last) atomicMax(&s_max, last);
+    if (lane == 0 && warp_max) atomicMax(&s_max, warp_max);
     __syncthreads();
     const uint32_t end = range.x + s_max;
-    float A0 = bg0, A1 = bg1, A2 = bg2;  // colour behind, normalised by T after the entry
 
     for (uint32_t bend = end; bend > range.x;) {
-        const uint32_t bstart = bend > range.x + kBlendThreads ? bend - kBlendThreads : range.x;
+        const uint32_t bstart = bend > range.x + BATCH ? bend - BATCH : range.x;
         const int cnt = (int)(bend - bstart);
         __syncthreads();
-        if (threadIdx.x < cnt) {
-            const uint32_t j = bend - 1 - threadIdx.x;  // slot 0 is the back-most entry
-            const uint32_t g = gids[j];
-            const Screen rec = scr[g];
-            s_gid[threadIdx.x] = g;
-            s_q0[threadIdx.x] = rec.q0;
-            s_co[threadIdx.x] = make_float2(rec.q1.x, rec.q1.y);
-            s_rgb[threadIdx.x] = rec.q2;
-        }
+        for (int e = threadIdx.x; e < BATCH; e += Map::NT) {
+            if (e < cnt) {
+                const uint32_t j = bend - 1 - e;  // slot 0 is the back-most entry
+                const uint32_t g = gids[j];
+                const Screen rec = scr[g];
+                s_gid[e] = g;
+                stage_entry(rec, s_e[e]);
+                s_mask[e] = (uint8_t)warp_row_mask(rec, tm.y0, Map::R, Map::NW);
+            }
 #pragma unroll
-        for (int k = 0; k < 9; ++k) s_acc[k][threadIdx.x] = 0.f;
+            for (int k = 0; k < 9; ++k) s_acc[k][e] = 0.f;
+        }
         __syncthreads();
         for (int jj = 0; jj < cnt; ++jj) {
             const uint32_t pos = bend - jj - range.x;  // 1-based list position
-            Frag f;
-            const float4 q0 = s_q0[jj];
-            const float2 co = s_co[jj];
-            bool contrib = pos <= last && eval_fragment(fx, fy, q0, co.x, co.y, f);
+            if (pos > warp_max || !((s_mask[jj] >> warp) & 1u)) continue;  // uniform over the warp
+            const Entry e = s_e[jj];
+            // eigenvalues back from the pre-scaled form
+            const float ls = -2.0f / kLog2e * e.coef.x, lb = -2.0f / kLog2e * e.coef.y;
             float d[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) d[k] = 0.f;
-            if (contrib) {
-                const float4 c = s_rgb[jj];
-                const float Ti = T / (1.0f - f.alpha);
-                const float dalpha = Ti * (g0 * (c.x - A0) + g1 * (c.y - A1) + g2 * (c.z - A2));
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                Frag f;
+                float u, w;
+                if (!(pos <= last[k] && eval_frag(fx, (float)tm.py[k] + 0.5f, e, f, u, w))) continue;
+                any = true;
+                const float Ti = T[k] / (1.0f - f.alpha);
+                const float dalpha = Ti * (g0[k] * (e.rgbo.x - A0[k]) + g1[k] * (e.rgbo.y - A1[k]) +
+                                           g2[k] * (e.rgbo.z - A2[k]));
                 const float wT = f.alpha * Ti;
-                d[6] = wT * g0;
-                d[7] = wT * g1;
-                d[8] = wT * g2;
-                A0 = f.alpha * c.x + (1.0f - f.alpha) * A0;
-                A1 = f.alpha * c.y + (1.0f - f.alpha) * A1;
-                A2 = f.alpha * c.z + (1.0f - f.alpha) * A2;
-                T = Ti;
+                d[6] += wT * g0[k];
+                d[7] += wT * g1[k];
+                d[8] += wT * g2[k];
+                A0[k] = f.alpha * e.rgbo.x + (1.0f - f.alpha) * A0[k];
+                A1[k] = f.alpha * e.rgbo.y + (1.0f - f.alpha) * A1[k];
+                A2[k] = f.alpha * e.rgbo.z + (1.0f - f.alpha) * A2[k];
+                T[k] = Ti;
                 if (!f.clamped) {
+                    // power = -q/2 with q = d^T C d; v = C d = ls u e + lb w e_perp
+                    // from the eigen form (no cancellation)
                     const float dpow = dalpha * f.alpha;  // alpha = o G here
-                    d[5] = dalpha * f.G;
-                    d[2] = -0.5f * f.dx * f.dx * dpow;
-                    d[3] = -f.dx * f.dy * dpow;
-                    d[4] = -0.5f * f.dy * f.dy * dpow;
-                    d[0] = dpow * (q0.z * f.dx + q0.w * f.dy);
-                    d[1] = dpow * (q0.w * f.dx + co.x * f.dy);
+                    const float lu = ls * u, lw = lb * w;
+                    const float vx = e.coef.z * lu - e.coef.w * lw;
+                    const float vy = e.coef.w * lu + e.coef.z * lw;
+                    d[5] += dalpha * f.G;
+                    d[0] += dpow * vx;  // dL/dmu = dpow C d
+                    d[1] += dpow * vy;
+                    // dL/dSigma (full symmetric) = -C (dL/dC) C = dpow v v^T / 2
+                    const float hp = 0.5f * dpow;
+                    d[2] += hp * vx * vx;
+                    d[3] += hp * vx * vy;
+                    d[4] += hp * vy * vy;
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                // value index of lane l after the scatter: (l >> 2) & 7
-                const float part = warp_sum8_scatter(d, lane);
-                const float last_v = warp_sum(d[8]);
-                if ((lane & 3) == 0) atomicAdd(&s_acc[(lane >> 2) & 7][jj], part);
-                if (lane == 1) atomicAdd(&s_acc[8][jj], last_v);
-            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            // value index of lane l after the scatter: (l >> 2) & 7
+            const float part = warp_sum8_scatter(d, lane);
+            const float last_v = warp_sum(d[8]);
+            if ((lane & 3) == 0) atomicAdd(&s_acc[(lane >> 2) & 7][jj], part);
+            if (lane == 1) atomicAdd(&s_acc[8][jj], last_v);
         }
         __syncthreads();
-        if (threadIdx.x < cnt) {
-            const int s = threadIdx.x;
-            const float4 a = make_float4(s_acc[0][s], s_acc[1][s], s_acc[2][s], s_acc[3][s]);
-            const float4 b = make_float4(s_acc[4][s], s_acc[5][s], s_acc[6][s], s_acc[7][s]);
-            const float e = s_acc[8][s];
-            if (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f || b.x != 0.f || b.y != 0.f ||
-                b.z != 0.f || b.w != 0.f || e != 0.f) {
+        for (int s = threadIdx.x; s < cnt; s += Map::NT) {
+            // dL/dmu2D, dL/dSigma2D (H00, H01, H11 of the full symmetric
+            // gradient), dL/do and dL/drgb of this entry over the CTA
+            const float4 ga = make_float4(s_acc[0][s], s_acc[1][s], s_acc[2][s], s_acc[3][s]);
+            const float4 gb = make_float4(s_acc[4][s], s_acc[5][s], s_acc[6][s], s_acc[7][s]);
+            const float gblue = s_acc[8][s];
+            if (ga.x != 0.f || ga.y != 0.f || ga.z != 0.f || ga.w != 0.f || gb.x != 0.f || gb.y != 0.f ||
+                gb.z != 0.f || gb.w != 0.f || gblue != 0.f) {
                 ScreenGrad* dst = sg + s_gid[s];
-                atomicAdd(&dst->g0, a);
-                atomicAdd(&dst->g1, b);
-                atomicAdd(&dst->g2.x, e);
+                atomicAdd(&dst->g0, ga);
+                atomicAdd(&dst->g1, gb);
+                atomicAdd(&dst->g2.x, gblue);
             }
         }
         bend = bstart;
     }
 }
 
+// Launch configurations the tuner may pick: pixels per thread x batch.
+template <int PPT, int BATCH>
+static void launch_pair_fwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
+                            const Screen* screen, const float bg[3], float* images, float* T_final,
+                            uint32_t* n_contrib, uint32_t* n_blended, cudaStream_t st)
+{
+    blend_fwd_kernel<PPT, BATCH><<<vt.total_tiles, kTilePixels / PPT, 0, st>>>(
+        vt, n, ranges, gids, screen, bg[0], bg[1], bg[2], images, T_final, n_contrib, n_blended);
+}
+
+template <int PPT, int BATCH>
+static void launch_pair_bwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
+                            const Screen* screen, const float bg[3], const float* dL_dimg,
+                            const float* T_final, const uint32_t* n_contrib, ScreenGrad* sgrad,
+                            cudaStream_t st)
+{
+    blend_bwd_kernel<PPT, BATCH><<<vt.total_tiles, kTilePixels / PPT, 0, st>>>(
+        vt, n, ranges, gids, screen, bg[0], bg[1], bg[2], dL_dimg, T_final, n_contrib, sgrad);
+}
+
+#define FGS_BLEND_CONFIGS(X) X(1, 256) X(2, 128) X(2, 256) X(4, 64) X(4, 128) X(4, 256)
+
+bool blend_config_supported(int ppt, int batch)
+{
+#define FGS_CHECK(P, Bt) if (ppt == P && batch == Bt) return true;
+    FGS_BLEND_CONFIGS(FGS_CHECK)
+#undef FGS_CHECK
+    return false;
+}
+
 cudaError_t launch_blend_fwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                              const Screen* screen, const float bg[3], float* images, float* T_final,
-                             uint32_t* n_contrib, cudaStream_t st)
+                             uint32_t* n_contrib, uint32_t* n_blended, int ppt, int batch,
+                             cudaStream_t st)
 {
     if (vt.total_tiles <= 0) return cudaSuccess;
-    blend_fwd_kernel<<<vt.total_tiles, kBlendThreads, 0, st>>>(vt, n, ranges, gids, screen, bg[0], bg[1],
-                                                               bg[2], images, T_final, n_contrib);
+#define FGS_GO(P, Bt) \
+    if (ppt == P && batch == Bt) launch_pair_fwd<P, Bt>(vt, n, ranges, gids, screen, bg, images, T_final, n_contrib, n_blended, st);
+    FGS_BLEND_CONFIGS(FGS_GO)
+#undef FGS_GO
     profile_mark(st, "blend_fwd");
     return cudaGetLastError();
 }
@@ -261,11 +418,13 @@ cudaError_t launch_blend_fwd(const ViewTable& vt, int64_t n, const uint2* ranges
 cudaError_t launch_blend_bwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                              const Screen* screen, const float bg[3], const float* dL_dimg,
                              const float* T_final, const uint32_t* n_contrib, ScreenGrad* sgrad,
-                             cudaStream_t st)
+                             int ppt, int batch, cudaStream_t st)
 {
     if (vt.total_tiles <= 0) return cudaSuccess;
-    blend_bwd_kernel<<<vt.total_tiles, kBlendThreads, 0, st>>>(vt, n, ranges, gids, screen, bg[0], bg[1],
-                                                               bg[2], dL_dimg, T_final, n_contrib, sgrad);
+#define FGS_GO(P, Bt) \
+    if (ppt == P && batch == Bt) launch_pair_bwd<P, Bt>(vt, n, ranges, gids, screen, bg, dL_dimg, T_final, n_contrib, sgrad, st);
+    FGS_BLEND_CONFIGS(FGS_GO)
+#undef FGS_GO
     profile_mark(st, "blend_bwd");
     return cudaGetLastError();
 }

@@ -40,17 +40,21 @@ struct ViewTable {
 };
 
 // Screen-space state of one (view, Gaussian): 48 bytes, read by the blend
-// kernels as three 16-byte loads.
+// kernels as three 16-byte loads.  The conic is stored in eigen form (see
+// EigenConic below).
 struct alignas(16) Screen {
-    float4 q0;  // mu2D.x, mu2D.y, conic a, conic b
-    float4 q1;  // conic c, opacity, k = 2 ln(255 o), depth
+    float4 q0;  // mu2D.x, mu2D.y, conic eigenvalues lb >= ls
+    float4 q1;  // major-axis angle, opacity, k = 2 ln(255 o), depth
     float4 q2;  // rgb, bits: clamp mask (bits 0..2) | visible (bit 3)
 };
 
-// dL/d(mu2D, conic, opacity, rgb) accumulators of one (view, Gaussian).
+// Screen-space gradient accumulators of one (view, Gaussian): dL/dmu2D,
+// dL/dSigma2D as the full symmetric matrix [[H00, H01], [H01, H11]] (the
+// conic gradient mapped through d conic = -conic dSigma conic), dL/do and
+// dL/drgb.
 struct alignas(16) ScreenGrad {
-    float4 g0;  // d mu.x, d mu.y, d a, d b
-    float4 g1;  // d c, d o, d r, d g
+    float4 g0;  // d mu.x, d mu.y, H00, H01
+    float4 g1;  // H11, d o, d r, d g
     float4 g2;  // d b(lue), unused x3
 };
 
@@ -111,20 +115,42 @@ template <> __device__ __forceinline__ __half from_f32<__half>(float x) { return
 // compiler can make them differ between call sites.
 // ---------------------------------------------------------------------------
 
-// q(d) = a dx^2 + 2 b dx dy + c dy^2
-__device__ __forceinline__ float quad_form(float a, float b, float c, float dx, float dy)
+// The conic (inverse dilated 2D covariance) is kept in eigen form: the two
+// eigenvalues (lb >= ls) and the angle th of the eigenvector of the small
+// one, i.e. the major axis of the splat.  With e = (cos th, sin th),
+//   q(d) = d^T conic d = ls (e . d)^2 + lb (e_perp . d)^2,
+// a sum of two non-negative terms.  Storing (a, b, c) instead loses the small
+// eigenvalue of needle-like splats (a c - b^2 cancels), which moves q by
+// percents at pixels far along the needle; the eigen form is computed from
+// the covariance itself (lmax by a sum of non-negative terms, lmin = det /
+// lmax with the Cauchy-Binet determinant), so it stays accurate.
+struct EigenConic {
+    float lb, ls, c, s;  // eigenvalues and the major-axis direction
+};
+
+__device__ __forceinline__ EigenConic eigen_from_stored(float lb, float ls, float th)
 {
-    const float t0 = __fmul_rn(__fmul_rn(a, dx), dx);
-    const float t1 = __fmul_rn(__fmul_rn(__fmul_rn(2.0f, b), dx), dy);
-    const float t2 = __fmul_rn(__fmul_rn(c, dy), dy);
-    return __fadd_rn(__fadd_rn(t0, t1), t2);
+    EigenConic e;
+    e.lb = lb;
+    e.ls = ls;
+    sincosf(th, &e.s, &e.c);
+    return e;
+}
+
+__device__ __forceinline__ float eigen_q(const EigenConic& e, float dx, float dy)
+{
+    const float u = __fmaf_rn(e.c, dx, __fmul_rn(e.s, dy));    // along the major axis
+    const float w = __fmaf_rn(e.c, dy, -__fmul_rn(e.s, dx));   // across it
+    return __fmaf_rn(__fmul_rn(e.ls, u), u, __fmul_rn(__fmul_rn(e.lb, w), w));
 }
 
 // Tile culling of Sec. 3.2 (the per-tile maximum of the Gaussian): minimum
 // of the quadratic form over the box of the tile's pixel centres (offsets
-// from the mean); keep the tile iff it is <= k.
-__device__ __forceinline__ bool tile_keep(float mx, float my, float a, float b, float c, float k,
-                                          int tx, int ty, int width, int height)
+// from the mean); keep the tile iff it is <= k.  The minimum of a convex
+// quadratic over a box is 0 when the mean is inside, else it lies on an edge,
+// where the 1D minimiser (from the conic entries) is clamped to the edge.
+__device__ __forceinline__ bool tile_keep(float mx, float my, const EigenConic& e, float k, int tx,
+                                          int ty, int width, int height)
 {
     const float x_lo = __fadd_rn((float)(tx * kTile), 0.5f);
     const float x_hi = fminf(__fadd_rn((float)(tx * kTile + kTile - 1), 0.5f), __fadd_rn((float)width, -0.5f));
@@ -133,49 +159,36 @@ __device__ __forceinline__ bool tile_keep(float mx, float my, float a, float b, 
     const float x0 = __fsub_rn(x_lo, mx), x1 = __fsub_rn(x_hi, mx);
     const float y0 = __fsub_rn(y_lo, my), y1 = __fsub_rn(y_hi, my);
     if (x0 <= 0.0f && 0.0f <= x1 && y0 <= 0.0f && 0.0f <= y1) return true;
+    // conic entries for the 1D minimisers: a = ls c^2 + lb s^2, b = (ls - lb) s c, cc = ls s^2 + lb c^2
+    const float a = __fmaf_rn(e.ls, __fmul_rn(e.c, e.c), __fmul_rn(e.lb, __fmul_rn(e.s, e.s)));
+    const float b = __fmul_rn(__fsub_rn(e.ls, e.lb), __fmul_rn(e.s, e.c));
+    const float cc = __fmaf_rn(e.ls, __fmul_rn(e.s, e.s), __fmul_rn(e.lb, __fmul_rn(e.c, e.c)));
     float best = INFINITY;
-    // edges x = x0, x1: minimise over y in [y0, y1]
     {
         float X = x0;
-        float Y = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, X), c), y0), y1);
-        best = fminf(best, quad_form(a, b, c, X, Y));
+        float Y = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, X), cc), y0), y1);
+        best = fminf(best, eigen_q(e, X, Y));
         X = x1;
-        Y = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, X), c), y0), y1);
-        best = fminf(best, quad_form(a, b, c, X, Y));
+        Y = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, X), cc), y0), y1);
+        best = fminf(best, eigen_q(e, X, Y));
     }
-    // edges y = y0, y1: minimise over x in [x0, x1]
     {
         float Y = y0;
         float X = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, Y), a), x0), x1);
-        best = fminf(best, quad_form(a, b, c, X, Y));
+        best = fminf(best, eigen_q(e, X, Y));
         Y = y1;
         X = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, Y), a), x0), x1);
-        best = fminf(best, quad_form(a, b, c, X, Y));
+        best = fminf(best, eigen_q(e, X, Y));
     }
     return best <= k;
 }
 
-// Alpha of one fragment (Eq. 3 with the 3DGS rules): returns false when
-// the fragment is skipped (power > 0 or alpha < 1/255); otherwise alpha =
-// min(0.99, o G), and G and the clamp state for the backward.
+// One evaluated fragment: alpha = min(0.99, o G), G = exp(power), the
+// offset from the mean and whether the clamp is active.
 struct Frag {
     float alpha, G, dx, dy;
     bool clamped;
 };
-
-__device__ __forceinline__ bool eval_fragment(float px, float py, float4 q0, float c, float o,
-                                              Frag& f)
-{
-    f.dx = __fsub_rn(px, q0.x);
-    f.dy = __fsub_rn(py, q0.y);
-    const float power = __fmul_rn(-0.5f, quad_form(q0.z, q0.w, c, f.dx, f.dy));
-    if (power > 0.0f) return false;
-    f.G = __expf(power);
-    const float oG = __fmul_rn(o, f.G);
-    f.clamped = oG >= kAlphaMax;
-    f.alpha = f.clamped ? kAlphaMax : oG;
-    return f.alpha >= kAlphaMin;
-}
 
 // ---------------------------------------------------------------------------
 // Real SH basis (Condon-Shortley phase, orthonormal), degree <= 3, at a unit

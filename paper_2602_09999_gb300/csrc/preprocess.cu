@@ -51,7 +51,8 @@ constexpr int kBigRect = 32;  // rectangles with more tiles are culled by the wh
 // Per-view screen geometry of one Gaussian (Eq. 1-2, Suppl. B.1 tests,
 // Suppl. C dilation, Sec. 3.2 opacity-aware rectangle).
 struct Geo {
-    float mx, my, ca, cb, cc, k, depth;
+    float mx, my, k, depth, th;
+    EigenConic e;
     int tx0, ty0, tw, ntiles;  // tile rectangle (ntiles = 0: not rendered)
 };
 
@@ -91,10 +92,15 @@ __device__ __forceinline__ void project(const Cam& cam, const float mu[3], const
     if (!(det2 >= kDetMin)) return;
     const float da = ca + kDilation, dc = cc + kDilation;
     const float detd = det2 + kDilation * (ca + cc) + kDilation * kDilation;
-    const float idet = 1.0f / detd;
-    g.ca = dc * idet;
-    g.cb = -cb * idet;
-    g.cc = da * idet;
+    // conic = (Sigma2D + 0.3 I)^-1 in eigen form: the dilated covariance has
+    // eigenvalues lmax = (da + dc)/2 + sqrt(((da - dc)/2)^2 + cb^2) (no
+    // cancellation) and lmin = detd / lmax, major axis at th
+    const float hdiff = 0.5f * (da - dc);
+    const float lmax = 0.5f * (da + dc) + sqrtf(hdiff * hdiff + cb * cb);
+    g.th = 0.5f * atan2f(2.0f * cb, da - dc);
+    g.e.ls = 1.0f / lmax;
+    g.e.lb = lmax / detd;
+    sincosf(g.th, &g.e.s, &g.e.c);
     g.mx = cam.fx * t[0] * iz + cam.cx;
     g.my = cam.fy * t[1] * iz + cam.cy;
     g.depth = t[2];
@@ -121,21 +127,24 @@ __device__ __forceinline__ uint32_t count_tiles(const Geo& g, bool has, int widt
     const bool big = has && g.ntiles > kBigRect;
     if (has && !big) {
         for (int t = 0; t < g.ntiles; ++t)
-            count += tile_keep(g.mx, g.my, g.ca, g.cb, g.cc, g.k, g.tx0 + t % g.tw, g.ty0 + t / g.tw,
-                               width, height);
+            count += tile_keep(g.mx, g.my, g.e, g.k, g.tx0 + t % g.tw, g.ty0 + t / g.tw, width, height);
     }
     unsigned bigmask = __ballot_sync(0xffffffffu, big);
     while (bigmask) {
         const int src = __ffs(bigmask) - 1;
         bigmask &= bigmask - 1;
         const float mx = __shfl_sync(0xffffffffu, g.mx, src), my = __shfl_sync(0xffffffffu, g.my, src);
-        const float a = __shfl_sync(0xffffffffu, g.ca, src), b = __shfl_sync(0xffffffffu, g.cb, src);
-        const float c = __shfl_sync(0xffffffffu, g.cc, src), k = __shfl_sync(0xffffffffu, g.k, src);
+        EigenConic e;
+        e.lb = __shfl_sync(0xffffffffu, g.e.lb, src);
+        e.ls = __shfl_sync(0xffffffffu, g.e.ls, src);
+        e.c = __shfl_sync(0xffffffffu, g.e.c, src);
+        e.s = __shfl_sync(0xffffffffu, g.e.s, src);
+        const float k = __shfl_sync(0xffffffffu, g.k, src);
         const int tx0 = __shfl_sync(0xffffffffu, g.tx0, src), ty0 = __shfl_sync(0xffffffffu, g.ty0, src);
         const int tw = __shfl_sync(0xffffffffu, g.tw, src), nt = __shfl_sync(0xffffffffu, g.ntiles, src);
         uint32_t part = 0;
         for (int t = lane; t < nt; t += 32)
-            part += tile_keep(mx, my, a, b, c, k, tx0 + t % tw, ty0 + t / tw, width, height);
+            part += tile_keep(mx, my, e, k, tx0 + t % tw, ty0 + t / tw, width, height);
         part = __reduce_add_sync(0xffffffffu, part);
         if (lane == src) count = part;
     }
@@ -216,8 +225,8 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
             if (r0 < 0.f) { bits |= 1u; r0 = 0.f; }
             if (r1 < 0.f) { bits |= 2u; r1 = 0.f; }
             if (r2 < 0.f) { bits |= 4u; r2 = 0.f; }
-            rec.q0 = make_float4(g.mx, g.my, g.ca, g.cb);
-            rec.q1 = make_float4(g.cc, o, g.k, g.depth);
+            rec.q0 = make_float4(g.mx, g.my, g.e.lb, g.e.ls);
+            rec.q1 = make_float4(g.th, o, g.k, g.depth);
             rec.q2 = make_float4(r0, r1, r2, __uint_as_float(bits));
         }
         const int64_t vi = (int64_t)v * n + i;
@@ -304,9 +313,10 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
         const unsigned long long depth_bits = __float_as_uint(q1.w);
         const unsigned long long toff = (unsigned long long)vt.tile_off[v];
         const int tx_n = vt.tiles_x[v];
+        const EigenConic e = eigen_from_stored(q0.z, q0.w, q1.x);
         for (int t = 0; t < nt; ++t) {
             const int tx = r.x + t % tw, ty = r.y + t / tw;
-            if (!tile_keep(q0.x, q0.y, q0.z, q0.w, q1.x, q1.z, tx, ty, width, height)) continue;
+            if (!tile_keep(q0.x, q0.y, e, q1.z, tx, ty, width, height)) continue;
             if (off < (uint64_t)k_max) {
                 keys[off] = ((toff + ty * tx_n + tx) << 32) | depth_bits;
                 vals[off] = (uint32_t)i;
@@ -319,8 +329,10 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
         const int src = __ffs(bigmask) - 1;
         bigmask &= bigmask - 1;
         const float mx = __shfl_sync(0xffffffffu, q0.x, src), my = __shfl_sync(0xffffffffu, q0.y, src);
-        const float a = __shfl_sync(0xffffffffu, q0.z, src), b = __shfl_sync(0xffffffffu, q0.w, src);
-        const float c = __shfl_sync(0xffffffffu, q1.x, src), k = __shfl_sync(0xffffffffu, q1.z, src);
+        const EigenConic e = eigen_from_stored(__shfl_sync(0xffffffffu, q0.z, src),
+                                               __shfl_sync(0xffffffffu, q0.w, src),
+                                               __shfl_sync(0xffffffffu, q1.x, src));
+        const float k = __shfl_sync(0xffffffffu, q1.z, src);
         const unsigned long long depth_bits = __float_as_uint(__shfl_sync(0xffffffffu, q1.w, src));
         const int sv = __shfl_sync(0xffffffffu, v, src);
         const uint32_t sid = (uint32_t)__shfl_sync(0xffffffffu, (unsigned long long)i, src);
@@ -332,7 +344,7 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
         for (int base = 0; base < snt; base += 32) {
             const int t = base + lane;
             const int tx = tx0 + t % stw, ty = ty0 + t / stw;
-            const bool keep = t < snt && tile_keep(mx, my, a, b, c, k, tx, ty, width, height);
+            const bool keep = t < snt && tile_keep(mx, my, e, k, tx, ty, width, height);
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             const uint64_t pos = soff + __popc(m & ((1u << lane) - 1u));
             if (keep && pos < (uint64_t)k_max) {
@@ -454,15 +466,9 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
             dt[1] += gy * cam.fy * iz;
             dt[2] += -(gx * cam.fx * t[0] + gy * cam.fy * t[1]) * iz2;
 
-            // conic = (Sigma2D + 0.3 I)^-1 : dSigma = -conic G conic, with G
-            // the full symmetric gradient [[ga, gb/2], [gb/2, gc]]
-            const float ca = rec.q0.z, cb = rec.q0.w, cc = rec.q1.x;
-            const float ga = g.g0.z, gb = 0.5f * g.g0.w, gc = g.g1.x;
-            const float P00 = ca * ga + cb * gb, P01 = ca * gb + cb * gc;
-            const float P10 = cb * ga + cc * gb, P11 = cb * gb + cc * gc;
-            const float S00 = -(P00 * ca + P01 * cb);
-            const float S01 = -(P00 * cb + P01 * cc);
-            const float S11 = -(P10 * cb + P11 * cc);
+            // the blend backward accumulates dL/dSigma2D (full symmetric, the
+            // dilation has unit Jacobian): H = [[S00, S01], [S01, S11]]
+            const float S00 = g.g0.z, S01 = g.g0.w, S11 = g.g1.x;
 
             // Sigma2D = T2 Sigma T2^T = (T2 M)(T2 M)^T with T2 = J Rcam
             const float j00 = cam.fx * iz, j02 = -cam.fx * t[0] * iz2;

@@ -141,6 +141,13 @@ class Rasterizer:
         return (self.slot(B.FGS_WS_T_FINAL, torch.float32),
                 self.slot(B.FGS_WS_N_CONTRIB, torch.int32))
 
+    def fragment_counts(self):
+        """(list positions evaluated up to each pixel's last contributor,
+        fragments blended), summed over all pixels of the last forward."""
+        nc = self.slot(B.FGS_WS_N_CONTRIB, torch.int32).to(torch.int64).sum().item()
+        nb = self.slot(B.FGS_WS_N_BLENDED, torch.int32).to(torch.int64).sum().item()
+        return int(nc), int(nb)
+
 
 class RasterizeFn(torch.autograd.Function):
     """images = render(means, log_scales, quats, opacity, sh_dc, sh_rest)."""
@@ -232,6 +239,12 @@ class Trainer:
 
     def forward_only(self):
         self.rast.forward(self.p_s, self.sh_degree, self.bg, self.images)
+
+    def forward_backward(self):
+        """Forward, loss and backward without the optimiser step."""
+        self.rast.forward(self.p_s, self.sh_degree, self.bg, self.images)
+        self.rast.loss(self.images, self.targets, self.lam, self.loss, self.dl)
+        self.rast.backward(self.p_s, self.sh_degree, self.bg, self.dl, self.g_s)
 
     def adam_step_count(self) -> int:
         st = B.fgs_adam_state.from_buffer_copy(bytes(self.adam_state.cpu().numpy()))

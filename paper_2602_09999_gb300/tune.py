@@ -1,0 +1,78 @@
+"""Autotuner for the launch choices of the blend kernels.
+
+The choices (pixels per blend thread, list entries per shared-memory batch;
+see fgs_tuning in include/fastergs.h) change speed only: every choice gives
+bit-identical images and the same gradients up to atomic-add order.  The
+tuner times forward + loss + backward of the caller's own batch shape for
+each supported choice with CUDA events, keeps the fastest, and caches it in
+a JSON file keyed by GPU name, Gaussian count and pixel count (rounded to
+powers of two), so later runs of the same shape skip the search.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import torch
+
+from . import binding as B
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
+
+
+def _key(n: int, pixels: int) -> str:
+    name = torch.cuda.get_device_name().replace(" ", "_")
+    return f"{name}/n2^{round(math.log2(max(n, 1)))}/px2^{round(math.log2(max(pixels, 1)))}"
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(table):
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    tmp = CACHE + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, CACHE)
+
+
+def apply(layout, choice):
+    layout.tuning.blend_pixels_per_thread = int(choice[0])
+    layout.tuning.blend_batch = int(choice[1])
+
+
+def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=B.BLEND_CONFIGS):
+    """Picks the fastest blend configuration for `trainer`'s batch shape and
+    writes it into its workspace layout.  Runs forward, loss and backward
+    only (the parameters are not updated).  Returns (choice, timings_ms)."""
+    key = _key(trainer.n, trainer.views.total_pixels)
+    table = _load() if use_cache else {}
+    if key in table:
+        choice = tuple(table[key]["choice"])
+        apply(trainer.rast.layout, choice)
+        return choice, table[key].get("ms", {})
+    timings = {}
+    stream = torch.cuda.current_stream()
+    for cfg in configs:
+        apply(trainer.rast.layout, cfg)
+        trainer.forward_backward()        # warm-up of this configuration
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            trainer.forward_backward()
+        t1.record(stream)
+        t1.synchronize()
+        timings[f"{cfg[0]}x{cfg[1]}"] = t0.elapsed_time(t1) / reps
+    best = min(configs, key=lambda c: timings[f"{c[0]}x{c[1]}"])
+    apply(trainer.rast.layout, best)
+    if use_cache:
+        table[key] = {"choice": list(best), "ms": timings}
+        _store(table)
+    return best, timings

@@ -13,12 +13,15 @@ IMAGE_TOL = 2e-4          # max abs image error (fixed by the hot-path target)
 GRAD_REL_L2 = 1e-3        # relative L2 error per gradient tensor (same source)
 
 
-def gpu_forward(params, cams, k_max=None, sh_degree=3, bg=(0.0, 0.0, 0.0), sh_dtype=torch.float32):
+def gpu_forward(params, cams, k_max=None, sh_degree=3, bg=(0.0, 0.0, 0.0), sh_dtype=torch.float32,
+                tuning=None):
     n = params["means"].shape[0]
     views = T.Views(cams)
     if k_max is None:
         k_max = max(4096, 64 * n * len(cams))
     rast = T.Rasterizer(n, views, k_max)
+    if tuning is not None:
+        rast.layout.tuning.blend_pixels_per_thread, rast.layout.tuning.blend_batch = tuning
     t = T.to_device_params(params, sh_dtype=sh_dtype)
     images = torch.zeros(3 * views.total_pixels, device="cuda")
     rast.forward(T.params_struct(t), sh_degree, bg, images)
@@ -84,6 +87,87 @@ def oracle_forward(params, cams, sh_degree=3, bg=(0.0, 0.0, 0.0), margins=oracle
         lists.append(li)
         outs.append(out)
     return pres, lists, outs
+
+
+def ambiguity_masks(cams, params, sh_degree=3, bg=(0.0, 0.0, 0.0), dilate=5):
+    """Per view: pixels touched by a decision float32 may take either way
+    (oracle flags), dilated by the SSIM window radius so that no loss
+    gradient outside the mask depends on a flagged pixel."""
+    masks = []
+    for cam in cams:
+        _, _, out = oracle.render(cam, params, sh_degree, bg, oracle.FP32_MARGINS)
+        m = out["ambiguous"].astype(bool)
+        if dilate and m.any():
+            pad = np.pad(m, dilate)
+            acc = np.zeros_like(m)
+            H, W = m.shape
+            for dy in range(2 * dilate + 1):
+                for dx in range(2 * dilate + 1):
+                    acc |= pad[dy:dy + H, dx:dx + W]
+            m = acc
+        masks.append(m)
+    return masks
+
+
+def ill_conditioned(cams, params, factor=4.0):
+    """Gaussians whose footprint half-extent exceeds `factor` times the larger
+    image side in some view (near-plane or grazing splats): their gradient
+    sums thousands of cancelling per-pixel terms, which float32 accumulation
+    in any order cannot resolve to 1e-3."""
+    bad = np.zeros(np.asarray(params["means"]).shape[0], bool)
+    for cam in cams:
+        pre = oracle.preprocess(cam, params)
+        ext = pre["aux"][:, 5:7].max(axis=1)
+        bad |= pre["visible"] & (ext > factor * max(cam.width, cam.height))
+    return bad
+
+
+def oracle_grads(cams, params, targets, masks=None, lam=0.2, bg=(0.0, 0.0, 0.0), sh_degree=3):
+    """Oracle loss (batch mean) and parameter gradients, with dL/dC zeroed on
+    the masked pixels of each view."""
+    grads = oracle.zero_grads(params)
+    B = len(cams)
+    total = 0.0
+    for v, (cam, tgt) in enumerate(zip(cams, targets)):
+        pre, lists, out = oracle.render(cam, params, sh_degree, bg)
+        L, dL = oracle.loss(out["image"], tgt, lam, grad_scale=1.0 / B)
+        total += L / B
+        if masks is not None:
+            dL[:, masks[v]] = 0.0
+        sg = oracle.blend_backward(cam, pre, lists, dL, bg)
+        oracle.preprocess_backward(cam, params, sg, sh_degree, grads)
+    return total, grads
+
+
+def gpu_grads(params, cams, targets, masks=None, lam=0.2, bg=(0.0, 0.0, 0.0), sh_degree=3,
+              sh_dtype=torch.float32, tuning=None):
+    """GPU loss and gradients through the C ABI, with dL/dC zeroed on the
+    masked pixels of each view."""
+    rast, views, t, images = gpu_forward(params, cams, bg=bg, sh_degree=sh_degree,
+                                         sh_dtype=sh_dtype, tuning=tuning)
+    tg = views.concat([torch.from_numpy(np.asarray(x, np.float32)) for x in targets]).cuda()
+    loss = torch.zeros(1, device="cuda")
+    dl = torch.zeros_like(images)
+    rast.loss(images, tg, lam, loss, dl)
+    if masks is not None:
+        for v, m in enumerate(masks):
+            view = views.split(dl)[v]
+            view[:, torch.from_numpy(m).cuda()] = 0.0
+    grads = {k: torch.zeros(t[k].shape, device="cuda") for k in T.GROUPS}
+    rast.backward(T.params_struct(t), sh_degree, bg, dl, T.params_struct(grads))
+    torch.cuda.synchronize()
+    return float(loss.item()), {k: v.cpu().numpy() for k, v in grads.items()}, rast
+
+
+def grad_errors(gg, go, exclude=None):
+    """Relative L2 error per tensor over the Gaussians not excluded."""
+    out = {}
+    for k in T.GROUPS:
+        a, b = np.asarray(gg[k], np.float64), np.asarray(go[k], np.float64)
+        if exclude is not None and exclude.any():
+            a, b = a[~exclude], b[~exclude]
+        out[k] = rel_l2(a, b) if np.any(b) else float(np.abs(a).max(initial=0.0))
+    return out
 
 
 def rel_l2(a, b):

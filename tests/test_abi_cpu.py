@@ -40,9 +40,10 @@ def test_library_exports_every_declared_function(lib):
 def test_struct_sizes_match_c(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "fastergs.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(fgs_camera),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(fgs_camera),'
                    ' sizeof(fgs_params), sizeof(fgs_workspace_layout), sizeof(fgs_adam_state),'
-                   ' offsetof(fgs_adam_state, step_size));return 0;}\n')
+                   ' offsetof(fgs_adam_state, step_size), offsetof(fgs_workspace_layout, tuning));'
+                   'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
@@ -50,7 +51,8 @@ def test_struct_sizes_match_c(tmp_path):
     assert [int(x) for x in out] == [ctypes.sizeof(B.fgs_camera), ctypes.sizeof(B.fgs_params),
                                      ctypes.sizeof(B.fgs_workspace_layout),
                                      ctypes.sizeof(B.fgs_adam_state),
-                                     B.fgs_adam_state.step_size.offset]
+                                     B.fgs_adam_state.step_size.offset,
+                                     B.fgs_workspace_layout.tuning.offset]
 
 
 def test_workspace_layout(lib):

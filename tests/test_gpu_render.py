@@ -12,8 +12,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
-from gpu_util import (GRAD_REL_L2, IMAGE_TOL, compare_lists, gpu_forward,  # noqa: E402
-                      oracle_forward, rel_l2)
+from gpu_util import (GRAD_REL_L2, IMAGE_TOL, ambiguity_masks, compare_lists,  # noqa: E402
+                      gpu_forward, gpu_grads, grad_errors, ill_conditioned, oracle_forward,
+                      oracle_grads, rel_l2)
 from paper_2602_09999_gb300 import binding as B  # noqa: E402
 from paper_2602_09999_gb300 import scenes  # noqa: E402
 from paper_2602_09999_gb300 import train as T  # noqa: E402
@@ -56,9 +57,17 @@ def test_screen_state_matches_oracle(case):
         m = gvis & keep_any
         assert m.sum() > 100
         np.testing.assert_allclose(s[m, 0:2], pre["xy"][m], atol=2e-3, rtol=0)
-        cmax = np.maximum(np.abs(pre["conic"][m, 0]), np.abs(pre["conic"][m, 2]))[:, None]
-        conic_g = np.stack([s[m, 2], s[m, 3], s[m, 4]], 1)
-        assert np.all(np.abs(conic_g - pre["conic"][m]) <= 1e-4 * cmax + 1e-7)
+        # the conic in eigen form: eigenvalues lb >= ls and the major-axis angle
+        ca, cb, cc = (pre["conic"][m, i] for i in range(3))
+        half = np.sqrt(0.25 * (ca - cc) ** 2 + cb ** 2)
+        lb_o, ls_o = 0.5 * (ca + cc) + half, (ca * cc - cb * cb) / (0.5 * (ca + cc) + half)
+        np.testing.assert_allclose(s[m, 2], lb_o, rtol=1e-5)
+        np.testing.assert_allclose(s[m, 3], ls_o, rtol=1e-5)
+        c, sn = np.cos(s[m, 4].astype(np.float64)), np.sin(s[m, 4].astype(np.float64))
+        lb, ls = s[m, 2].astype(np.float64), s[m, 3].astype(np.float64)
+        conic_g = np.stack([ls * c * c + lb * sn * sn, (ls - lb) * sn * c, ls * sn * sn + lb * c * c], 1)
+        cmax = np.maximum(np.abs(ca), np.abs(cc))[:, None]
+        assert np.all(np.abs(conic_g - pre["conic"][m]) <= 1e-5 * cmax + 1e-7)
         np.testing.assert_allclose(s[m, 5], pre["opacity"][m], rtol=2e-6)
         np.testing.assert_allclose(s[m, 7], pre["depth"][m], rtol=2e-6)
         np.testing.assert_allclose(s[m, 8:11], pre["rgb"][m], atol=2e-5)
@@ -145,18 +154,22 @@ def test_loss_matches_oracle(sizes, lam):
 
 
 # --------------------------------------------------------------------------
-# backward: gradients through the C ABI vs the oracle's exact adjoint
+# backward: gradients through the C ABI vs the oracle's exact adjoint.
+# dL/dC is zeroed, on both sides, on pixels touched by a decision float32 may
+# take either way (dilated by the SSIM radius); Gaussians whose footprint
+# dwarfs the view (ill-conditioned sums) are left out of the relative L2.
 # --------------------------------------------------------------------------
-def _gpu_grads(params, cams, targets, lam=0.2, bg=(0.0, 0.0, 0.0), sh_degree=3):
-    rast, views, t, images = gpu_forward(params, cams, bg=bg, sh_degree=sh_degree)
-    tg = views.concat([torch.from_numpy(x) for x in targets]).cuda()
-    loss = torch.zeros(1, device="cuda")
-    dl = torch.zeros_like(images)
-    rast.loss(images, tg, lam, loss, dl)
-    grads = {k: torch.zeros(t[k].shape, device="cuda") for k in GROUPS}
-    rast.backward(T.params_struct(t), sh_degree, bg, dl, T.params_struct(grads))
-    torch.cuda.synchronize()
-    return float(loss.item()), {k: v.cpu().numpy() for k, v in grads.items()}, rast
+def _check_grads(params, cams, targets, bg=(0.0, 0.0, 0.0), deg=3, lam=0.2):
+    masks = ambiguity_masks(cams, params, deg, bg)
+    Lg, gg, _ = gpu_grads(params, cams, targets, masks, lam, bg, deg)
+    Lo, go = oracle_grads(cams, params, targets, masks, lam, bg, deg)
+    assert Lg == pytest.approx(Lo, rel=1e-5)
+    bad = ill_conditioned(cams, params)
+    errs = grad_errors(gg, go, bad)
+    print({k: f"{v:.2e}" for k, v in errs.items()}, "masked px", int(sum(m.sum() for m in masks)),
+          "ill-conditioned", int(bad.sum()))
+    for k, e in errs.items():
+        assert e <= GRAD_REL_L2, (k, e)
 
 
 @pytest.mark.parametrize("name,n,size,bg,deg", [("tiny", 4000, (128, 96), (0, 0, 0), 3),
@@ -166,14 +179,16 @@ def test_gradients_match_oracle(oracle_mod, name, n, size, bg, deg):
     params = scenes.tiny_scene(n, seed=20 + n)
     cams = [scenes.tiny_camera(*size)]
     targets = [scenes.target_image(*size, view=3)]
-    Lg, gg, _ = _gpu_grads(params, cams, targets, bg=bg, sh_degree=deg)
-    Lo, _, go, _, _ = oracle.train_step(cams, params, targets, sh_degree=deg, bg=bg)
-    assert Lg == pytest.approx(Lo, rel=1e-5)
-    for k in GROUPS:
-        if not np.any(go[k]):
-            assert not np.any(gg[k]), k
-            continue
-        assert rel_l2(gg[k], go[k]) <= GRAD_REL_L2, (k, rel_l2(gg[k], go[k]))
+    _check_grads(params, cams, targets, bg, deg)
+
+
+def test_gradients_match_oracle_anisotropic_scene(oracle_mod):
+    """Outdoor-shaped scene: strongly anisotropic Gaussians of many sizes,
+    near-plane splats among them."""
+    params = scenes.outdoor_scene(20_000, seed=81)
+    cams = scenes.orbit_cameras(2, 140, 100, radius=6.0, seed=8)
+    targets = [scenes.target_image(140, 100, view=i) for i in range(2)]
+    _check_grads(params, cams, targets)
 
 
 def test_batched_uneven_views_match_oracle(oracle_mod):
@@ -181,11 +196,7 @@ def test_batched_uneven_views_match_oracle(oracle_mod):
     sizes = [(120, 90), (77, 101), (64, 64)]
     cams = [scenes.look_at((0.5 * i, 0.3, 4.0), (0, 0, 0), w, h) for i, (w, h) in enumerate(sizes)]
     targets = [scenes.target_image(w, h, view=i) for i, (w, h) in enumerate(sizes)]
-    Lg, gg, rast = _gpu_grads(params, cams, targets)
-    Lo, imgs, go, _, _ = oracle.train_step(cams, params, targets)
-    assert Lg == pytest.approx(Lo, rel=1e-5)
-    for k in GROUPS:
-        assert rel_l2(gg[k], go[k]) <= GRAD_REL_L2, (k, rel_l2(gg[k], go[k]))
+    _check_grads(params, cams, targets)
 
 
 # --------------------------------------------------------------------------
@@ -295,6 +306,52 @@ def test_graph_replay_matches_eager():
     img1 = a.images.clone()
     a.forward_only()
     assert torch.equal(img1, a.images)
+
+
+# --------------------------------------------------------------------------
+# launch configurations change speed only
+# --------------------------------------------------------------------------
+def test_blend_configurations_agree(oracle_mod):
+    """Every blend launch configuration renders the same image bit for bit
+    (per-pixel arithmetic does not depend on it) and meets the gradient
+    parity bar against the oracle (only the order of float32 additions in the
+    per-Gaussian sums differs)."""
+    params = scenes.outdoor_scene(30_000, seed=71)
+    cams = scenes.orbit_cameras(2, 150, 111, radius=6.0, seed=3)
+    targets = [scenes.target_image(150, 111, view=i) for i in range(2)]
+    bad = ill_conditioned(cams, params)
+    masks = ambiguity_masks(cams, params)
+    Lo, go = oracle_grads(cams, params, targets, masks)
+    ref_img = None
+    for cfg in B.BLEND_CONFIGS:
+        L, gg, rast = gpu_grads(params, cams, targets, masks, tuning=cfg)
+        Tf, nc = (x.clone() for x in rast.per_pixel())
+        if ref_img is None:
+            ref_img = (Tf, nc)
+        assert torch.equal(Tf, ref_img[0]) and torch.equal(nc, ref_img[1]), cfg
+        assert L == pytest.approx(Lo, rel=1e-5), cfg
+        for k, e in grad_errors(gg, go, bad).items():
+            assert e <= GRAD_REL_L2, (cfg, k, e)
+
+
+def test_autotuner_picks_a_supported_configuration(tmp_path, monkeypatch):
+    from paper_2602_09999_gb300 import tune
+    monkeypatch.setattr(tune, "CACHE", str(tmp_path / "tuning.json"))
+    params = scenes.tiny_scene(5000, seed=72)
+    tr = T.Trainer(params, [scenes.tiny_camera(128, 96)], k_max=200_000)
+    choice, ms = tune.autotune(tr, reps=1)
+    assert tuple(choice) in B.BLEND_CONFIGS and len(ms) == len(B.BLEND_CONFIGS)
+    again, _ = tune.autotune(tr)           # cached
+    assert tuple(again) == tuple(choice)
+
+
+def test_unsupported_configuration_is_rejected():
+    params = scenes.tiny_scene(100, seed=73)
+    rast, views, t, images = gpu_forward(params, [scenes.tiny_camera(32, 32)])
+    rast.layout.tuning.blend_pixels_per_thread = 3
+    with pytest.raises(B.FGSError) as e:
+        rast.forward(T.params_struct(t), 3, (0, 0, 0), images)
+    assert e.value.code == -9
 
 
 # --------------------------------------------------------------------------
