@@ -97,7 +97,7 @@ typedef struct fgs_params {
 enum fgs_ws_slot {
     FGS_WS_HEADER = 0,
     FGS_WS_SCREEN,      /* 48-byte records [n_views*n]: float4 (mu2D, conic eigenvalues lb >= ls),
-                           float4 (major-axis angle, o, k = 2 ln(255 o), depth),
+                           float4 (major-axis direction cos, sin, o, depth),
                            float4 (rgb, bits: clamp mask 0..2, visible 3) */
     FGS_WS_RECT,        /* ushort4 [n_views*n]: tile rectangle x0, y0, x1, y1 (inclusive) */
     FGS_WS_LOCAL_OFF,   /* uint32 [n_views*n]: CTA-local exclusive prefix of tile counts */

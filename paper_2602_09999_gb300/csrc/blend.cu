@@ -25,7 +25,6 @@
 
 namespace fgs {
 
-constexpr int kBlendThreads = kTilePixels;  // 256
 constexpr float kLog2e = 1.4426950408889634f;
 
 // One list entry staged in shared memory: mean, the conic's eigen form
@@ -71,10 +70,9 @@ template <int PPT> struct TileMap {
 // half-extent is sqrt(k Sigma_yy) with Sigma_yy = s^2 / ls + c^2 / lb.
 __device__ __forceinline__ uint32_t warp_row_mask(const Screen& rec, int y0, int R, int nw)
 {
-    float sn, cs;
-    sincosf(rec.q1.x, &sn, &cs);
-    const float syy = sn * sn / rec.q0.w + cs * cs / rec.q0.z;
-    const float ey = sqrtf(rec.q1.z * syy) * 1.01f + 0.01f;
+    const float c = rec.q1.x, sn = rec.q1.y;
+    const float syy = sn * sn / rec.q0.w + c * c / rec.q0.z;
+    const float ey = sqrtf(opacity_k(rec.q1.z) * syy) * 1.01f + 0.01f;
     const float my = rec.q0.y;
     if (!(ey == ey)) return 0xffu;
     uint32_t m = 0;
@@ -87,11 +85,9 @@ __device__ __forceinline__ uint32_t warp_row_mask(const Screen& rec, int y0, int
 
 __device__ __forceinline__ void stage_entry(const Screen& rec, Entry& e)
 {
-    float sn, cs;
-    sincosf(rec.q1.x, &sn, &cs);
     e.xy = make_float2(rec.q0.x, rec.q0.y);
-    e.coef = make_float4(-0.5f * kLog2e * rec.q0.w, -0.5f * kLog2e * rec.q0.z, cs, sn);
-    e.rgbo = make_float4(rec.q2.x, rec.q2.y, rec.q2.z, rec.q1.y);
+    e.coef = make_float4(-0.5f * kLog2e * rec.q0.w, -0.5f * kLog2e * rec.q0.z, rec.q1.x, rec.q1.y);
+    e.rgbo = make_float4(rec.q2.x, rec.q2.y, rec.q2.z, rec.q1.z);
 }
 
 // Alpha of one fragment (Eq. 3 with the 3DGS rules), shared by the forward
@@ -244,7 +240,9 @@ blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
     __shared__ Entry s_e[BATCH];
     __shared__ uint8_t s_mask[BATCH];
     __shared__ uint32_t s_gid[BATCH];
-    __shared__ float s_acc[9][BATCH];
+    // one row per value; the row padding puts the 9 values of one entry in
+    // 9 different banks for the scattered shared atomics below
+    __shared__ float s_acc[9][BATCH + 1];
     __shared__ uint32_t s_max;
     const int tile = blockIdx.x;
     const Map tm(vt, tile);
@@ -317,7 +315,9 @@ blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
                 float u, w;
                 if (!(pos <= last[k] && eval_frag(fx, (float)tm.py[k] + 0.5f, e, f, u, w))) continue;
                 any = true;
-                const float Ti = T[k] / (1.0f - f.alpha);
+                // transmittance in front of the entry; 1 - alpha >= 0.01, so the
+                // approximate divide (2 ulp) is in range
+                const float Ti = __fdividef(T[k], 1.0f - f.alpha);
                 const float dalpha = Ti * (g0[k] * (e.rgbo.x - A0[k]) + g1[k] * (e.rgbo.y - A1[k]) +
                                            g2[k] * (e.rgbo.z - A2[k]));
                 const float wT = f.alpha * Ti;

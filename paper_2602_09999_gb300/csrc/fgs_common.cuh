@@ -44,9 +44,18 @@ struct ViewTable {
 // EigenConic below).
 struct alignas(16) Screen {
     float4 q0;  // mu2D.x, mu2D.y, conic eigenvalues lb >= ls
-    float4 q1;  // major-axis angle, opacity, k = 2 ln(255 o), depth
+    float4 q1;  // major-axis direction (cos, sin), opacity, depth
     float4 q2;  // rgb, bits: clamp mask (bits 0..2) | visible (bit 3)
 };
+
+// Opacity-aware extent (Sec. 3.2): alpha = o G reaches 1/255 where
+// d^T conic d <= k = 2 ln(255 o).  Preprocess, duplication and the blend
+// masks all derive k from the stored opacity with this one expression, so
+// their tile decisions agree bit for bit.
+__device__ __forceinline__ float opacity_k(float o)
+{
+    return fmaxf(2.0f * __logf(255.0f * o), 0.0f);
+}
 
 // Screen-space gradient accumulators of one (view, Gaussian): dL/dmu2D,
 // dL/dSigma2D as the full symmetric matrix [[H00, H01], [H01, H11]] (the
@@ -116,8 +125,8 @@ template <> __device__ __forceinline__ __half from_f32<__half>(float x) { return
 // ---------------------------------------------------------------------------
 
 // The conic (inverse dilated 2D covariance) is kept in eigen form: the two
-// eigenvalues (lb >= ls) and the angle th of the eigenvector of the small
-// one, i.e. the major axis of the splat.  With e = (cos th, sin th),
+// eigenvalues (lb >= ls) and the unit eigenvector (c, s) of the small one,
+// i.e. the major axis of the splat.  With e = (c, s),
 //   q(d) = d^T conic d = ls (e . d)^2 + lb (e_perp . d)^2,
 // a sum of two non-negative terms.  Storing (a, b, c) instead loses the small
 // eigenvalue of needle-like splats (a c - b^2 cancels), which moves q by
@@ -128,12 +137,13 @@ struct EigenConic {
     float lb, ls, c, s;  // eigenvalues and the major-axis direction
 };
 
-__device__ __forceinline__ EigenConic eigen_from_stored(float lb, float ls, float th)
+__device__ __forceinline__ EigenConic eigen_from_stored(float lb, float ls, float c, float s)
 {
     EigenConic e;
     e.lb = lb;
     e.ls = ls;
-    sincosf(th, &e.s, &e.c);
+    e.c = c;
+    e.s = s;
     return e;
 }
 

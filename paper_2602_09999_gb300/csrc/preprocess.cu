@@ -51,7 +51,7 @@ constexpr int kBigRect = 32;  // rectangles with more tiles are culled by the wh
 // Per-view screen geometry of one Gaussian (Eq. 1-2, Suppl. B.1 tests,
 // Suppl. C dilation, Sec. 3.2 opacity-aware rectangle).
 struct Geo {
-    float mx, my, k, depth, th;
+    float mx, my, k, depth;
     EigenConic e;
     int tx0, ty0, tw, ntiles;  // tile rectangle (ntiles = 0: not rendered)
 };
@@ -93,18 +93,30 @@ __device__ __forceinline__ void project(const Cam& cam, const float mu[3], const
     const float da = ca + kDilation, dc = cc + kDilation;
     const float detd = det2 + kDilation * (ca + cc) + kDilation * kDilation;
     // conic = (Sigma2D + 0.3 I)^-1 in eigen form: the dilated covariance has
-    // eigenvalues lmax = (da + dc)/2 + sqrt(((da - dc)/2)^2 + cb^2) (no
-    // cancellation) and lmin = detd / lmax, major axis at th
-    const float hdiff = 0.5f * (da - dc);
-    const float lmax = 0.5f * (da + dc) + sqrtf(hdiff * hdiff + cb * cb);
-    g.th = 0.5f * atan2f(2.0f * cb, da - dc);
+    // eigenvalues lmax = (da + dc)/2 + r, r = sqrt(((ca - cc)/2)^2 + cb^2) (no
+    // cancellation) and lmin = detd / lmax.  Its major axis makes the angle th
+    // with cos 2th = h / r, sin 2th = cb / r (h = (ca - cc)/2); the half-angle
+    // identities give (cos th, sin th) with the larger one from a sum of
+    // non-negative terms and the other from sin 2th = 2 sin th cos th.
+    const float h = 0.5f * (ca - cc);
+    const float r = sqrtf(h * h + cb * cb);
+    const float lmax = 0.5f * (da + dc) + r;
     g.e.ls = 1.0f / lmax;
     g.e.lb = lmax / detd;
-    sincosf(g.th, &g.e.s, &g.e.c);
+    if (!(r > 0.0f)) {
+        g.e.c = 1.0f;
+        g.e.s = 0.0f;
+    } else if (h >= 0.0f) {
+        g.e.c = sqrtf((r + h) / (2.0f * r));
+        g.e.s = cb / (2.0f * r * g.e.c);
+    } else {
+        g.e.s = copysignf(sqrtf((r - h) / (2.0f * r)), cb);
+        g.e.c = cb / (2.0f * r * g.e.s);
+    }
     g.mx = cam.fx * t[0] * iz + cam.cx;
     g.my = cam.fy * t[1] * iz + cam.cy;
     g.depth = t[2];
-    g.k = fmaxf(2.0f * __logf(255.0f * o), 0.0f);
+    g.k = opacity_k(o);
     const float ex = sqrtf(g.k * da), ey = sqrtf(g.k * dc);
     const float u0 = fmaxf(ceilf(g.mx - ex - 0.5f), 0.0f);
     const float u1 = fminf(floorf(g.mx + ex - 0.5f), (float)(cam.width - 1));
@@ -226,7 +238,7 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
             if (r1 < 0.f) { bits |= 2u; r1 = 0.f; }
             if (r2 < 0.f) { bits |= 4u; r2 = 0.f; }
             rec.q0 = make_float4(g.mx, g.my, g.e.lb, g.e.ls);
-            rec.q1 = make_float4(g.th, o, g.k, g.depth);
+            rec.q1 = make_float4(g.e.c, g.e.s, o, g.depth);
             rec.q2 = make_float4(r0, r1, r2, __uint_as_float(bits));
         }
         const int64_t vi = (int64_t)v * n + i;
@@ -313,10 +325,11 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
         const unsigned long long depth_bits = __float_as_uint(q1.w);
         const unsigned long long toff = (unsigned long long)vt.tile_off[v];
         const int tx_n = vt.tiles_x[v];
-        const EigenConic e = eigen_from_stored(q0.z, q0.w, q1.x);
+        const EigenConic e = eigen_from_stored(q0.z, q0.w, q1.x, q1.y);
+        const float k = opacity_k(q1.z);
         for (int t = 0; t < nt; ++t) {
             const int tx = r.x + t % tw, ty = r.y + t / tw;
-            if (!tile_keep(q0.x, q0.y, e, q1.z, tx, ty, width, height)) continue;
+            if (!tile_keep(q0.x, q0.y, e, k, tx, ty, width, height)) continue;
             if (off < (uint64_t)k_max) {
                 keys[off] = ((toff + ty * tx_n + tx) << 32) | depth_bits;
                 vals[off] = (uint32_t)i;
@@ -331,8 +344,9 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
         const float mx = __shfl_sync(0xffffffffu, q0.x, src), my = __shfl_sync(0xffffffffu, q0.y, src);
         const EigenConic e = eigen_from_stored(__shfl_sync(0xffffffffu, q0.z, src),
                                                __shfl_sync(0xffffffffu, q0.w, src),
-                                               __shfl_sync(0xffffffffu, q1.x, src));
-        const float k = __shfl_sync(0xffffffffu, q1.z, src);
+                                               __shfl_sync(0xffffffffu, q1.x, src),
+                                               __shfl_sync(0xffffffffu, q1.y, src));
+        const float k = opacity_k(__shfl_sync(0xffffffffu, q1.z, src));
         const unsigned long long depth_bits = __float_as_uint(__shfl_sync(0xffffffffu, q1.w, src));
         const int sv = __shfl_sync(0xffffffffu, v, src);
         const uint32_t sid = (uint32_t)__shfl_sync(0xffffffffu, (unsigned long long)i, src);
@@ -425,7 +439,7 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
             const uint32_t bits = __float_as_uint(rec.q2.w);
             const ScreenGrad g = sgrad[vi];
             const Cam cam = load_cam(cams, v);
-            const float o = rec.q1.y;
+            const float o = rec.q1.z;
             float t[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r)

@@ -57,18 +57,19 @@ def test_screen_state_matches_oracle(case):
         m = gvis & keep_any
         assert m.sum() > 100
         np.testing.assert_allclose(s[m, 0:2], pre["xy"][m], atol=2e-3, rtol=0)
-        # the conic in eigen form: eigenvalues lb >= ls and the major-axis angle
+        # the conic in eigen form: eigenvalues lb >= ls and the major-axis direction
         ca, cb, cc = (pre["conic"][m, i] for i in range(3))
         half = np.sqrt(0.25 * (ca - cc) ** 2 + cb ** 2)
         lb_o, ls_o = 0.5 * (ca + cc) + half, (ca * cc - cb * cb) / (0.5 * (ca + cc) + half)
         np.testing.assert_allclose(s[m, 2], lb_o, rtol=1e-5)
         np.testing.assert_allclose(s[m, 3], ls_o, rtol=1e-5)
-        c, sn = np.cos(s[m, 4].astype(np.float64)), np.sin(s[m, 4].astype(np.float64))
+        c, sn = s[m, 4].astype(np.float64), s[m, 5].astype(np.float64)
+        np.testing.assert_allclose(c * c + sn * sn, 1.0, atol=1e-6)
         lb, ls = s[m, 2].astype(np.float64), s[m, 3].astype(np.float64)
         conic_g = np.stack([ls * c * c + lb * sn * sn, (ls - lb) * sn * c, ls * sn * sn + lb * c * c], 1)
         cmax = np.maximum(np.abs(ca), np.abs(cc))[:, None]
         assert np.all(np.abs(conic_g - pre["conic"][m]) <= 1e-5 * cmax + 1e-7)
-        np.testing.assert_allclose(s[m, 5], pre["opacity"][m], rtol=2e-6)
+        np.testing.assert_allclose(s[m, 6], pre["opacity"][m], rtol=2e-6)
         np.testing.assert_allclose(s[m, 7], pre["depth"][m], rtol=2e-6)
         np.testing.assert_allclose(s[m, 8:11], pre["rgb"][m], atol=2e-5)
         clamp_g = np.stack([(bits[m] >> c) & 1 for c in range(3)], 1)
