@@ -116,6 +116,9 @@ enum fgs_ws_slot {
     FGS_WS_LOSS_MAPS,   /* float [9*total_pixels]: SSIM partial-derivative maps */
     FGS_WS_LOSS_PART,   /* double [loss blocks*2]: per-CTA L1 / SSIM sums */
     FGS_WS_N_BLENDED,   /* uint32 [total_pixels]: fragments blended into each pixel */
+    FGS_WS_TILE_QUEUE,  /* uint32 [4 + total_tiles]: work-queue counters (forward head and
+                           exits, backward head and exits), then every tile of every view in
+                           descending order of list length (written by each forward) */
     FGS_WS_NUM_SLOTS
 };
 
@@ -128,8 +131,15 @@ enum fgs_ws_slot {
 typedef struct fgs_tuning {
     int32_t blend_pixels_per_thread;
     int32_t blend_batch;
-    int32_t reserved[6];
+    int32_t blend_schedule;  /* FGS_SCHEDULE_QUEUE (default) or FGS_SCHEDULE_GRID */
+    int32_t reserved[5];
 } fgs_tuning;
+
+/* How the blend kernels visit tiles.  QUEUE: one resident CTA set per SM
+ * (SMs x occupancy CTAs) takes tiles from a work queue, longest list first
+ * (a longest-processing-time order, so no long tile starts last).  GRID: one
+ * CTA per tile, tiles in row-major order of each view. */
+enum { FGS_SCHEDULE_QUEUE = 0, FGS_SCHEDULE_GRID = 1 };
 
 typedef struct fgs_workspace_layout {
     size_t total_bytes;

@@ -25,7 +25,7 @@ FGS_FLAG_CAPACITY = 1
 (FGS_WS_HEADER, FGS_WS_SCREEN, FGS_WS_RECT, FGS_WS_LOCAL_OFF, FGS_WS_BLOCK_SUM, FGS_WS_KEYS,
  FGS_WS_VALS, FGS_WS_KEYS_ALT, FGS_WS_VALS_ALT, FGS_WS_SORT_HIST, FGS_WS_RANGES, FGS_WS_T_FINAL,
  FGS_WS_N_CONTRIB, FGS_WS_SCREEN_GRAD, FGS_WS_LOSS_MAPS, FGS_WS_LOSS_PART, FGS_WS_N_BLENDED,
- FGS_WS_NUM_SLOTS) = range(18)
+ FGS_WS_TILE_QUEUE, FGS_WS_NUM_SLOTS) = range(19)
 
 STATUS = {0: "FGS_OK", -1: "FGS_ERR_NULL", -2: "FGS_ERR_SHAPE", -3: "FGS_ERR_SH_DEGREE",
           -4: "FGS_ERR_WORKSPACE", -5: "FGS_ERR_DTYPE", -6: "FGS_ERR_CUDA", -7: "FGS_ERR_VIEWS",
@@ -60,10 +60,12 @@ class fgs_params(ctypes.Structure):
 
 class fgs_tuning(ctypes.Structure):
     _fields_ = [("blend_pixels_per_thread", ctypes.c_int32), ("blend_batch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("blend_schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 BLEND_CONFIGS = ((1, 256), (2, 128), (2, 256), (4, 64), (4, 128), (4, 256))
+FGS_SCHEDULE_QUEUE, FGS_SCHEDULE_GRID = 0, 1
+BLEND_SCHEDULES = (FGS_SCHEDULE_QUEUE, FGS_SCHEDULE_GRID)
 
 
 class fgs_workspace_layout(ctypes.Structure):

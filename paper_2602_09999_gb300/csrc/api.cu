@@ -25,14 +25,15 @@ int radix_sort(unsigned long long* keys, uint32_t* vals, unsigned long long* key
 cudaError_t launch_set_count(uint32_t* dst, uint32_t value, cudaStream_t st);
 cudaError_t launch_tile_ranges(const unsigned long long* keys, const uint32_t* n_dev, int64_t n_max,
                                uint2* ranges, int total_tiles, cudaStream_t st);
+cudaError_t launch_tile_order(const uint2* ranges, int total_tiles, uint32_t* queue, cudaStream_t st);
 cudaError_t launch_blend_fwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                              const Screen* screen, const float bg[3], float* images, float* T_final,
-                             uint32_t* n_contrib, uint32_t* n_blended, int ppt, int batch,
-                             cudaStream_t st);
+                             uint32_t* n_contrib, uint32_t* n_blended, uint32_t* queue, int ppt, int batch,
+                             int schedule, cudaStream_t st);
 cudaError_t launch_blend_bwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                              const Screen* screen, const float bg[3], const float* dL_dimg,
                              const float* T_final, const uint32_t* n_contrib, ScreenGrad* sgrad,
-                             int ppt, int batch, cudaStream_t st);
+                             uint32_t* queue, int ppt, int batch, int schedule, cudaStream_t st);
 bool blend_config_supported(int ppt, int batch);
 
 static const int kDefaultPPT = 2, kDefaultBatch = 128;
@@ -140,6 +141,7 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     sz[FGS_WS_LOSS_MAPS] = sizeof(float) * 9 * (size_t)vt->total_pixels;
     sz[FGS_WS_LOSS_PART] = sizeof(double) * 2 * (size_t)vt->total_tiles;
     sz[FGS_WS_N_BLENDED] = sizeof(uint32_t) * (size_t)vt->total_pixels;
+    sz[FGS_WS_TILE_QUEUE] = sizeof(uint32_t) * (4 + (size_t)vt->total_tiles);
     size_t off = 0;
     for (int s = 0; s < FGS_WS_NUM_SLOTS; ++s) {
         L->offset[s] = off;
@@ -156,6 +158,7 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     L->sorted_in_alt = ((L->sort_bits + 7) / 8) & 1;
     L->tuning.blend_pixels_per_thread = kDefaultPPT;
     L->tuning.blend_batch = kDefaultBatch;
+    L->tuning.blend_schedule = FGS_SCHEDULE_QUEUE;
     return FGS_OK;
 }
 
@@ -170,6 +173,8 @@ static int check_layout(void* ws, const fgs_workspace_layout* L, const fgs_camer
     if (memcmp(mine.offset, L->offset, sizeof(mine.offset)) != 0 || mine.total_bytes != L->total_bytes)
         return FGS_ERR_WORKSPACE;
     if (!blend_config_supported(L->tuning.blend_pixels_per_thread, L->tuning.blend_batch))
+        return FGS_ERR_ARG;
+    if (L->tuning.blend_schedule != FGS_SCHEDULE_QUEUE && L->tuning.blend_schedule != FGS_SCHEDULE_GRID)
         return FGS_ERR_ARG;
     return FGS_OK;
 }
@@ -246,11 +251,16 @@ int fgs_render_forward(void* ws, const fgs_workspace_layout* L, const fgs_params
     uint2* ranges = slot<uint2>(ws, L, FGS_WS_RANGES);
     if ((rc = cuda_rc(launch_tile_ranges(skeys, k_dev, L->k_max, ranges, vt.total_tiles, st))) != FGS_OK)
         return rc;
+    uint32_t* queue = slot<uint32_t>(ws, L, FGS_WS_TILE_QUEUE);
+    if (L->tuning.blend_schedule == FGS_SCHEDULE_QUEUE &&
+        (rc = cuda_rc(launch_tile_order(ranges, vt.total_tiles, queue, st))) != FGS_OK)
+        return rc;
     return cuda_rc(launch_blend_fwd(vt, n, ranges, svals, screen, bg, images,
                                     slot<float>(ws, L, FGS_WS_T_FINAL),
                                     slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB),
-                                    slot<uint32_t>(ws, L, FGS_WS_N_BLENDED),
-                                    L->tuning.blend_pixels_per_thread, L->tuning.blend_batch, st));
+                                    slot<uint32_t>(ws, L, FGS_WS_N_BLENDED), queue,
+                                    L->tuning.blend_pixels_per_thread, L->tuning.blend_batch,
+                                    L->tuning.blend_schedule, st));
 }
 
 int fgs_loss_l1_dssim(void* ws, const fgs_workspace_layout* L, const fgs_camera* cams_host,
@@ -292,8 +302,9 @@ int fgs_render_backward(void* ws, const fgs_workspace_layout* L, const fgs_param
     if ((rc = cuda_rc(launch_blend_bwd(vt, n, slot<uint2>(ws, L, FGS_WS_RANGES), svals, screen, bg,
                                        dl_dimages, slot<float>(ws, L, FGS_WS_T_FINAL),
                                        slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB), sgrad,
+                                       slot<uint32_t>(ws, L, FGS_WS_TILE_QUEUE),
                                        L->tuning.blend_pixels_per_thread, L->tuning.blend_batch,
-                                       st))) != FGS_OK)
+                                       L->tuning.blend_schedule, st))) != FGS_OK)
         return rc;
     return cuda_rc(launch_preprocess_bwd(n, sh_degree, params, cams_device, vt, screen, sgrad, grads, st));
 }

@@ -110,17 +110,88 @@ __device__ __forceinline__ bool eval_frag(float px, float py, const Entry& e, Fr
     return f.alpha >= kAlphaMin;
 }
 
+// Tile scheduling.  With a queue (head != nullptr) the CTAs of a resident
+// grid take the next entry of `order` (tiles by descending list length) until
+// it is exhausted, and the last CTA out zeroes the counters for the next
+// launch; nothing waits on another CTA.  Without one, CTA b takes tile b.
+struct TileSched {
+    uint32_t* head;   // next queue position
+    uint32_t* exits;  // CTAs that found the queue empty
+    const uint32_t* order;
+};
+
+__device__ __forceinline__ int sched_next(const TileSched& s, int total, int& iter, uint32_t& s_slot)
+{
+    if (!s.head) return iter++ == 0 ? (int)blockIdx.x : -1;
+    __syncthreads();  // every thread is done with the previous tile's shared state
+    if (threadIdx.x == 0) {
+        const uint32_t i = atomicAdd(s.head, 1u);
+        if (i < (uint32_t)total) {
+            s_slot = s.order[i];
+        } else {
+            s_slot = 0xffffffffu;
+            // each CTA exits once, after its last use of the head
+            if (atomicAdd(s.exits, 1u) == gridDim.x - 1) {
+                *s.head = 0;
+                *s.exits = 0;
+            }
+        }
+    }
+    __syncthreads();
+    return s_slot == 0xffffffffu ? -1 : (int)s_slot;
+}
+
+// Bucket of a tile's list length for the queue order: a quarter octave per
+// bucket, longest first (a longest-processing-time order needs only rough
+// sorting); empty tiles last.
+constexpr int kOrderBuckets = 130;
+
+__device__ __forceinline__ int length_bucket(uint2 r)
+{
+    const uint32_t c = r.y - r.x;
+    if (c == 0) return kOrderBuckets - 1;
+    const int e = 31 - __clz(c);
+    const uint32_t m = e >= 2 ? (c >> (e - 2)) & 3u : (c << (2 - e)) & 3u;
+    return 128 - (4 * e + (int)m);
+}
+
+// One CTA: counting sort of all tiles by length_bucket into q[4..], and
+// zeroes the four queue counters q[0..3].
+__global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restrict__ ranges, int total,
+                                                          uint32_t* __restrict__ q)
+{
+    __shared__ uint32_t s_cnt[kOrderBuckets];
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_cnt[b] = 0;
+    if (threadIdx.x < 4) q[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < total; t += blockDim.x) atomicAdd(&s_cnt[length_bucket(ranges[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int b = 0; b < kOrderBuckets; ++b) {
+            const uint32_t c = s_cnt[b];
+            s_cnt[b] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+    uint32_t* order = q + 4;
+    for (int t = threadIdx.x; t < total; t += blockDim.x)
+        order[atomicAdd(&s_cnt[length_bucket(ranges[t])], 1u)] = (uint32_t)t;
+}
+
+// Forward of one tile (the whole CTA): front-to-back blending of its list.
 template <int PPT, int BATCH>
-__global__ void __launch_bounds__(kTilePixels / PPT)
-blend_fwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
-                 const uint32_t* __restrict__ gids, const Screen* __restrict__ screen, float bg0,
-                 float bg1, float bg2, float* __restrict__ images, float* __restrict__ T_final,
-                 uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ n_blended)
+__device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, const uint2* __restrict__ ranges,
+                                               const uint32_t* __restrict__ gids,
+                                               const Screen* __restrict__ screen, float bg0, float bg1,
+                                               float bg2, float* __restrict__ images,
+                                               float* __restrict__ T_final, uint32_t* __restrict__ n_contrib,
+                                               uint32_t* __restrict__ n_blended, int tile)
 {
     using Map = TileMap<PPT>;
     __shared__ Entry s_e[BATCH];
     __shared__ uint8_t s_mask[BATCH];
-    const int tile = blockIdx.x;
     const Map tm(vt, tile);
     const int warp = threadIdx.x >> 5;
     const uint2 range = ranges[tile];
@@ -194,6 +265,20 @@ blend_fwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
     }
 }
 
+template <int PPT, int BATCH>
+__global__ void __launch_bounds__(kTilePixels / PPT)
+blend_fwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
+                 const uint32_t* __restrict__ gids, const Screen* __restrict__ screen, float bg0,
+                 float bg1, float bg2, float* __restrict__ images, float* __restrict__ T_final,
+                 uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ n_blended, TileSched sched)
+{
+    __shared__ uint32_t s_slot;
+    int iter = 0;
+    for (int tile; (tile = sched_next(sched, vt.total_tiles, iter, s_slot)) >= 0;)
+        blend_fwd_tile<PPT, BATCH>(vt, n, ranges, gids, screen, bg0, bg1, bg2, images, T_final, n_contrib,
+                                   n_blended, tile);
+}
+
 __device__ __forceinline__ float warp_sum(float x)
 {
 #pragma unroll
@@ -228,13 +313,15 @@ __device__ __forceinline__ float warp_sum8_scatter(const float v[8], int lane)
     return c;
 }
 
+// Backward of one tile (the whole CTA): back-to-front over its list.
 template <int PPT, int BATCH>
-__global__ void __launch_bounds__(kTilePixels / PPT)
-blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
-                 const uint32_t* __restrict__ gids, const Screen* __restrict__ screen, float bg0,
-                 float bg1, float bg2, const float* __restrict__ dL_dimg,
-                 const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
-                 ScreenGrad* __restrict__ sgrad)
+__device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, const uint2* __restrict__ ranges,
+                                               const uint32_t* __restrict__ gids,
+                                               const Screen* __restrict__ screen, float bg0, float bg1,
+                                               float bg2, const float* __restrict__ dL_dimg,
+                                               const float* __restrict__ T_final,
+                                               const uint32_t* __restrict__ n_contrib,
+                                               ScreenGrad* __restrict__ sgrad, int tile)
 {
     using Map = TileMap<PPT>;
     __shared__ Entry s_e[BATCH];
@@ -244,7 +331,6 @@ blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
     // 9 different banks for the scattered shared atomics below
     __shared__ float s_acc[9][BATCH + 1];
     __shared__ uint32_t s_max;
-    const int tile = blockIdx.x;
     const Map tm(vt, tile);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint2 range = ranges[tile];
@@ -371,24 +457,71 @@ blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
     }
 }
 
-// Launch configurations the tuner may pick: pixels per thread x batch.
+template <int PPT, int BATCH>
+__global__ void __launch_bounds__(kTilePixels / PPT)
+blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
+                 const uint32_t* __restrict__ gids, const Screen* __restrict__ screen, float bg0,
+                 float bg1, float bg2, const float* __restrict__ dL_dimg,
+                 const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
+                 ScreenGrad* __restrict__ sgrad, TileSched sched)
+{
+    __shared__ uint32_t s_slot;
+    int iter = 0;
+    for (int tile; (tile = sched_next(sched, vt.total_tiles, iter, s_slot)) >= 0;)
+        blend_bwd_tile<PPT, BATCH>(vt, n, ranges, gids, screen, bg0, bg1, bg2, dL_dimg, T_final, n_contrib,
+                                   sgrad, tile);
+}
+
+// Launch configurations the tuner may pick: pixels per thread x batch, and
+// the schedule.  A queue launch is one resident grid: SMs x CTAs per SM.
+static int sm_count()
+{
+    static int cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = sms > 0 ? sms : 1;
+    }
+    return cache[dev];
+}
+
+template <typename K>
+static int grid_for(K kernel, int threads, int total_tiles, const TileSched& sched)
+{
+    if (!sched.head) return total_tiles;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const long long g = (long long)per_sm * sm_count();
+    return (int)(g < total_tiles ? g : total_tiles);
+}
+
 template <int PPT, int BATCH>
 static void launch_pair_fwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                             const Screen* screen, const float bg[3], float* images, float* T_final,
-                            uint32_t* n_contrib, uint32_t* n_blended, cudaStream_t st)
+                            uint32_t* n_contrib, uint32_t* n_blended, const TileSched& sched,
+                            cudaStream_t st)
 {
-    blend_fwd_kernel<PPT, BATCH><<<vt.total_tiles, kTilePixels / PPT, 0, st>>>(
-        vt, n, ranges, gids, screen, bg[0], bg[1], bg[2], images, T_final, n_contrib, n_blended);
+    const int threads = kTilePixels / PPT;
+    const int grid = grid_for(blend_fwd_kernel<PPT, BATCH>, threads, vt.total_tiles, sched);
+    blend_fwd_kernel<PPT, BATCH><<<grid, threads, 0, st>>>(vt, n, ranges, gids, screen, bg[0], bg[1], bg[2],
+                                                           images, T_final, n_contrib, n_blended, sched);
 }
 
 template <int PPT, int BATCH>
 static void launch_pair_bwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                             const Screen* screen, const float bg[3], const float* dL_dimg,
                             const float* T_final, const uint32_t* n_contrib, ScreenGrad* sgrad,
-                            cudaStream_t st)
+                            const TileSched& sched, cudaStream_t st)
 {
-    blend_bwd_kernel<PPT, BATCH><<<vt.total_tiles, kTilePixels / PPT, 0, st>>>(
-        vt, n, ranges, gids, screen, bg[0], bg[1], bg[2], dL_dimg, T_final, n_contrib, sgrad);
+    const int threads = kTilePixels / PPT;
+    const int grid = grid_for(blend_bwd_kernel<PPT, BATCH>, threads, vt.total_tiles, sched);
+    blend_bwd_kernel<PPT, BATCH><<<grid, threads, 0, st>>>(vt, n, ranges, gids, screen, bg[0], bg[1], bg[2],
+                                                           dL_dimg, T_final, n_contrib, sgrad, sched);
 }
 
 #define FGS_BLEND_CONFIGS(X) X(1, 256) X(2, 128) X(2, 256) X(4, 64) X(4, 128) X(4, 256)
@@ -401,14 +534,34 @@ bool blend_config_supported(int ppt, int batch)
     return false;
 }
 
+cudaError_t launch_tile_order(const uint2* ranges, int total_tiles, uint32_t* queue, cudaStream_t st)
+{
+    if (total_tiles <= 0) return cudaSuccess;
+    tile_order_kernel<<<1, 1024, 0, st>>>(ranges, total_tiles, queue);
+    profile_mark(st, "tile_order");
+    return cudaGetLastError();
+}
+
+static TileSched make_sched(uint32_t* queue, int schedule, bool backward)
+{
+    TileSched s{nullptr, nullptr, nullptr};
+    if (schedule == FGS_SCHEDULE_QUEUE && queue) {
+        s.head = queue + (backward ? 2 : 0);
+        s.exits = queue + (backward ? 3 : 1);
+        s.order = queue + 4;
+    }
+    return s;
+}
+
 cudaError_t launch_blend_fwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                              const Screen* screen, const float bg[3], float* images, float* T_final,
-                             uint32_t* n_contrib, uint32_t* n_blended, int ppt, int batch,
-                             cudaStream_t st)
+                             uint32_t* n_contrib, uint32_t* n_blended, uint32_t* queue, int ppt, int batch,
+                             int schedule, cudaStream_t st)
 {
     if (vt.total_tiles <= 0) return cudaSuccess;
+    const TileSched sched = make_sched(queue, schedule, false);
 #define FGS_GO(P, Bt) \
-    if (ppt == P && batch == Bt) launch_pair_fwd<P, Bt>(vt, n, ranges, gids, screen, bg, images, T_final, n_contrib, n_blended, st);
+    if (ppt == P && batch == Bt) launch_pair_fwd<P, Bt>(vt, n, ranges, gids, screen, bg, images, T_final, n_contrib, n_blended, sched, st);
     FGS_BLEND_CONFIGS(FGS_GO)
 #undef FGS_GO
     profile_mark(st, "blend_fwd");
@@ -418,11 +571,12 @@ cudaError_t launch_blend_fwd(const ViewTable& vt, int64_t n, const uint2* ranges
 cudaError_t launch_blend_bwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                              const Screen* screen, const float bg[3], const float* dL_dimg,
                              const float* T_final, const uint32_t* n_contrib, ScreenGrad* sgrad,
-                             int ppt, int batch, cudaStream_t st)
+                             uint32_t* queue, int ppt, int batch, int schedule, cudaStream_t st)
 {
     if (vt.total_tiles <= 0) return cudaSuccess;
+    const TileSched sched = make_sched(queue, schedule, true);
 #define FGS_GO(P, Bt) \
-    if (ppt == P && batch == Bt) launch_pair_bwd<P, Bt>(vt, n, ranges, gids, screen, bg, dL_dimg, T_final, n_contrib, sgrad, st);
+    if (ppt == P && batch == Bt) launch_pair_bwd<P, Bt>(vt, n, ranges, gids, screen, bg, dL_dimg, T_final, n_contrib, sgrad, sched, st);
     FGS_BLEND_CONFIGS(FGS_GO)
 #undef FGS_GO
     profile_mark(st, "blend_bwd");

@@ -1,12 +1,13 @@
 """Autotuner for the launch choices of the blend kernels.
 
-The choices (pixels per blend thread, list entries per shared-memory batch;
-see fgs_tuning in include/fastergs.h) change speed only: every choice gives
-bit-identical images and the same gradients up to atomic-add order.  The
-tuner times forward + loss + backward of the caller's own batch shape for
-each supported choice with CUDA events, keeps the fastest, and caches it in
-a JSON file keyed by GPU name, Gaussian count and pixel count (rounded to
-powers of two), so later runs of the same shape skip the search.
+The choices (pixels per blend thread, list entries per shared-memory batch,
+and the tile schedule -- a work queue in longest-list-first order or one CTA
+per tile; see fgs_tuning in include/fastergs.h) change speed only: every
+choice gives bit-identical images and the same gradients up to atomic-add
+order.  The tuner times forward + loss + backward of the caller's own batch
+shape for each supported choice with CUDA events, keeps the fastest, and
+caches it in a JSON file keyed by GPU name, Gaussian count and pixel count
+(rounded to powers of two), so later runs of the same shape skip the search.
 """
 from __future__ import annotations
 
@@ -43,17 +44,29 @@ def _store(table):
 
 
 def apply(layout, choice):
+    """choice = (pixels per thread, batch[, schedule])."""
     layout.tuning.blend_pixels_per_thread = int(choice[0])
     layout.tuning.blend_batch = int(choice[1])
+    layout.tuning.blend_schedule = int(choice[2]) if len(choice) > 2 else B.FGS_SCHEDULE_QUEUE
 
 
-def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=B.BLEND_CONFIGS):
+def label(choice) -> str:
+    sched = "grid" if len(choice) > 2 and choice[2] == B.FGS_SCHEDULE_GRID else "queue"
+    return f"{choice[0]}x{choice[1]}/{sched}"
+
+
+def all_choices():
+    return [(p, b, s) for s in B.BLEND_SCHEDULES for (p, b) in B.BLEND_CONFIGS]
+
+
+def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=None):
     """Picks the fastest blend configuration for `trainer`'s batch shape and
     writes it into its workspace layout.  Runs forward, loss and backward
     only (the parameters are not updated).  Returns (choice, timings_ms)."""
+    configs = all_choices() if configs is None else [tuple(c) for c in configs]
     key = _key(trainer.n, trainer.views.total_pixels)
     table = _load() if use_cache else {}
-    if key in table:
+    if key in table and len(table[key].get("choice", [])) == 3:
         choice = tuple(table[key]["choice"])
         apply(trainer.rast.layout, choice)
         return choice, table[key].get("ms", {})
@@ -69,8 +82,8 @@ def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=B.BLEND_CON
             trainer.forward_backward()
         t1.record(stream)
         t1.synchronize()
-        timings[f"{cfg[0]}x{cfg[1]}"] = t0.elapsed_time(t1) / reps
-    best = min(configs, key=lambda c: timings[f"{c[0]}x{c[1]}"])
+        timings[label(cfg)] = t0.elapsed_time(t1) / reps
+    best = min(configs, key=lambda c: timings[label(c)])
     apply(trainer.rast.layout, best)
     if use_cache:
         table[key] = {"choice": list(best), "ms": timings}

@@ -8,6 +8,7 @@ import torch
 import oracle
 from paper_2602_09999_gb300 import binding as B
 from paper_2602_09999_gb300 import train as T
+from paper_2602_09999_gb300 import tune
 
 IMAGE_TOL = 2e-4          # max abs image error (fixed by the hot-path target)
 GRAD_REL_L2 = 1e-3        # relative L2 error per gradient tensor (same source)
@@ -21,7 +22,7 @@ def gpu_forward(params, cams, k_max=None, sh_degree=3, bg=(0.0, 0.0, 0.0), sh_dt
         k_max = max(4096, 64 * n * len(cams))
     rast = T.Rasterizer(n, views, k_max)
     if tuning is not None:
-        rast.layout.tuning.blend_pixels_per_thread, rast.layout.tuning.blend_batch = tuning
+        tune.apply(rast.layout, tuning)
     t = T.to_device_params(params, sh_dtype=sh_dtype)
     images = torch.zeros(3 * views.total_pixels, device="cuda")
     rast.forward(T.params_struct(t), sh_degree, bg, images)
