@@ -99,7 +99,10 @@ enum fgs_ws_slot {
     FGS_WS_SCREEN,      /* 48-byte records [n_views*n]: float4 (mu2D, conic eigenvalues lb >= ls),
                            float4 (major-axis direction cos, sin, o, depth),
                            float4 (rgb, bits: clamp mask 0..2, visible 3) */
-    FGS_WS_RECT,        /* ushort4 [n_views*n]: tile rectangle x0, y0, x1, y1 (inclusive) */
+    FGS_WS_RECT,        /* 16-byte records [n_views*n]: tile rectangle x0, y0, x1, y1 (uint16,
+                           inclusive; x0 > x1 when not rendered), then for rectangles of at most
+                           32 tiles the uint32 mask of tiles kept by culling (bit t = row-major
+                           tile t), then an unused uint32 */
     FGS_WS_LOCAL_OFF,   /* uint32 [n_views*n]: CTA-local exclusive prefix of tile counts */
     FGS_WS_BLOCK_SUM,   /* uint32 [n_views*ceil(n/256)+1]: prefix of CTA totals */
     FGS_WS_KEYS,        /* uint64 [k_max]: (global tile << 32) | depth bits */

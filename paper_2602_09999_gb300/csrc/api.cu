@@ -9,10 +9,10 @@
 
 namespace fgs {
 cudaError_t launch_preprocess_fwd(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                                  const ViewTable& vt, Screen* screen, ushort4* rects,
+                                  const ViewTable& vt, Screen* screen, TileRect* rects,
                                   uint32_t* local_off, uint32_t* block_sum, cudaStream_t st);
 cudaError_t launch_scan_and_duplicate(int64_t n, const ViewTable& vt, const Screen* screen,
-                                      const ushort4* rects, const uint32_t* local_off,
+                                      const TileRect* rects, const uint32_t* local_off,
                                       uint32_t* block_sum, WsHeader* hdr, int64_t k_max,
                                       unsigned long long* keys, uint32_t* vals, cudaStream_t st);
 cudaError_t launch_preprocess_bwd(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
@@ -126,7 +126,7 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     size_t sz[FGS_WS_NUM_SLOTS];
     sz[FGS_WS_HEADER] = sizeof(WsHeader);
     sz[FGS_WS_SCREEN] = sizeof(Screen) * (size_t)vn;
-    sz[FGS_WS_RECT] = sizeof(ushort4) * (size_t)vn;
+    sz[FGS_WS_RECT] = sizeof(TileRect) * (size_t)vn;
     sz[FGS_WS_LOCAL_OFF] = sizeof(uint32_t) * (size_t)vn;
     sz[FGS_WS_BLOCK_SUM] = sizeof(uint32_t) * (size_t)(nv * nblk + 1);
     sz[FGS_WS_KEYS] = sizeof(unsigned long long) * (size_t)k_max;
@@ -228,7 +228,7 @@ int fgs_render_forward(void* ws, const fgs_workspace_layout* L, const fgs_params
     const int64_t n = L->n;
     WsHeader* hdr = slot<WsHeader>(ws, L, FGS_WS_HEADER);
     Screen* screen = slot<Screen>(ws, L, FGS_WS_SCREEN);
-    ushort4* rects = slot<ushort4>(ws, L, FGS_WS_RECT);
+    TileRect* rects = slot<TileRect>(ws, L, FGS_WS_RECT);
     uint32_t* local_off = slot<uint32_t>(ws, L, FGS_WS_LOCAL_OFF);
     uint32_t* block_sum = slot<uint32_t>(ws, L, FGS_WS_BLOCK_SUM);
     unsigned long long* keys = slot<unsigned long long>(ws, L, FGS_WS_KEYS);

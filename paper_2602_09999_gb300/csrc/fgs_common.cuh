@@ -48,6 +48,16 @@ struct alignas(16) Screen {
     float4 q2;  // rgb, bits: clamp mask (bits 0..2) | visible (bit 3)
 };
 
+// Tile set of one (view, Gaussian): its tile rectangle (inclusive; x0 > x1
+// when it is not rendered) and, for rectangles of at most 32 tiles, the
+// tiles that survive culling (bit t = row-major tile t of the rectangle), so
+// the duplication pass need not test them again.
+struct alignas(16) TileRect {
+    ushort4 r;
+    uint32_t keep;
+    uint32_t unused;
+};
+
 // Opacity-aware extent (Sec. 3.2): alpha = o G reaches 1/255 where
 // d^T conic d <= k = 2 ln(255 o).  Preprocess, duplication and the blend
 // masks all derive k from the stored opacity with this one expression, so

@@ -132,14 +132,19 @@ __device__ __forceinline__ void project(const Cam& cam, const float mu[3], const
 // Kept tiles of one Gaussian: the thread alone for small rectangles; for
 // large ones every lane of the warp takes a stride of the rectangle and the
 // counts are reduced (the warp must be converged; `g` is per lane).
-__device__ __forceinline__ uint32_t count_tiles(const Geo& g, bool has, int width, int height)
+// For small rectangles `keep` receives the kept tiles (bit t = tile t).
+__device__ __forceinline__ uint32_t count_tiles(const Geo& g, bool has, int width, int height,
+                                                uint32_t& keep)
 {
     const int lane = threadIdx.x & 31;
     uint32_t count = 0;
+    keep = 0;
     const bool big = has && g.ntiles > kBigRect;
     if (has && !big) {
         for (int t = 0; t < g.ntiles; ++t)
-            count += tile_keep(g.mx, g.my, g.e, g.k, g.tx0 + t % g.tw, g.ty0 + t / g.tw, width, height);
+            if (tile_keep(g.mx, g.my, g.e, g.k, g.tx0 + t % g.tw, g.ty0 + t / g.tw, width, height))
+                keep |= 1u << t;
+        count = __popc(keep);
     }
     unsigned bigmask = __ballot_sync(0xffffffffu, big);
     while (bigmask) {
@@ -169,7 +174,7 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
                       const float* __restrict__ log_scales, const float* __restrict__ quats,
                       const float* __restrict__ opac, const SHT* __restrict__ sh_dc,
                       const SHT* __restrict__ sh_rest, const fgs_camera* __restrict__ cams,
-                      ViewTable vt, Screen* __restrict__ screen, ushort4* __restrict__ rects,
+                      ViewTable vt, Screen* __restrict__ screen, TileRect* __restrict__ rects,
                       uint32_t* __restrict__ local_off, uint32_t* __restrict__ block_sum,
                       int nblk)
 {
@@ -205,16 +210,20 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
         g.ntiles = 0;
         if (ok) project(cam, mu, M, o, g);
         const bool has = g.ntiles > 0;
-        const uint32_t count = count_tiles(g, has, cam.width, cam.height);
+        uint32_t keep;
+        const uint32_t count = count_tiles(g, has, cam.width, cam.height, keep);
         Screen rec;
         rec.q0 = make_float4(0.f, 0.f, 0.f, 0.f);
         rec.q1 = make_float4(0.f, 0.f, 0.f, 0.f);
         rec.q2 = make_float4(0.f, 0.f, 0.f, 0.f);
-        ushort4 rect = make_ushort4(1, 1, 0, 0);
+        TileRect rect;
+        rect.r = make_ushort4(1, 1, 0, 0);
+        rect.keep = keep;
+        rect.unused = 0;
         if (count > 0) {
-            rect = make_ushort4((unsigned short)g.tx0, (unsigned short)g.ty0,
-                                (unsigned short)(g.tx0 + g.tw - 1),
-                                (unsigned short)(g.ty0 + g.ntiles / g.tw - 1));
+            rect.r = make_ushort4((unsigned short)g.tx0, (unsigned short)g.ty0,
+                                  (unsigned short)(g.tx0 + g.tw - 1),
+                                  (unsigned short)(g.ty0 + g.ntiles / g.tw - 1));
             // SH colour from the view direction, streamed from memory
             float d0 = mu[0] - cam.pos[0], d1 = mu[1] - cam.pos[1], d2 = mu[2] - cam.pos[2];
             const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
@@ -289,11 +298,12 @@ scan_block_sums_kernel(uint32_t* __restrict__ block_sum, int64_t count, WsHeader
 
 // Emits (global tile << 32 | depth bits, Gaussian id) for every kept tile
 // of every (view, Gaussian), in row-major tile order at the scanned offset.
-// Large rectangles are emitted by the whole warp, 32 tiles per step, with a
-// ballot prefix keeping the row-major order.
+// Small rectangles walk the kept-tile mask the preprocess recorded; large
+// ones are culled again by the whole warp, 32 tiles per step, with a ballot
+// prefix keeping the row-major order.
 __global__ void __launch_bounds__(256)
 duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
-                 const ushort4* __restrict__ rects, const uint32_t* __restrict__ local_off,
+                 const TileRect* __restrict__ rects, const uint32_t* __restrict__ local_off,
                  const uint32_t* __restrict__ block_sum, int nblk, int64_t k_max,
                  unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals)
 {
@@ -304,32 +314,32 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
     int64_t i = 0;
     bool vis = false;
     float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
-    ushort4 r = make_ushort4(1, 1, 0, 0);
+    TileRect tr;
+    tr.r = make_ushort4(1, 1, 0, 0);
+    tr.keep = 0;
     uint64_t off = 0;
     if (valid) {
         v = (int)(gi / n);
         i = gi - (int64_t)v * n;
-        vis = (__float_as_uint(screen[gi].q2.w) & 8u) != 0;
-        if (vis) {
-            q0 = screen[gi].q0;
-            q1 = screen[gi].q1;
-            r = rects[gi];
-            off = (uint64_t)local_off[gi] + block_sum[(int64_t)v * nblk + i / kPreBlock];
-        }
+        tr = rects[gi];
+        vis = tr.r.x <= tr.r.z;
+        if (vis) off = (uint64_t)local_off[gi] + block_sum[(int64_t)v * nblk + i / kPreBlock];
     }
+    const ushort4 r = tr.r;
     const int tw = (int)r.z - (int)r.x + 1;
     const int nt = vis ? tw * ((int)r.w - (int)r.y + 1) : 0;
     const bool big = vis && nt > kBigRect;
+    if (big) {
+        q0 = screen[gi].q0;
+        q1 = screen[gi].q1;
+    }
     if (vis && !big) {
-        const int width = vt.width[v], height = vt.height[v];
-        const unsigned long long depth_bits = __float_as_uint(q1.w);
+        const unsigned long long depth_bits = __float_as_uint(screen[gi].q1.w);
         const unsigned long long toff = (unsigned long long)vt.tile_off[v];
         const int tx_n = vt.tiles_x[v];
-        const EigenConic e = eigen_from_stored(q0.z, q0.w, q1.x, q1.y);
-        const float k = opacity_k(q1.z);
-        for (int t = 0; t < nt; ++t) {
+        for (uint32_t m = tr.keep; m; m &= m - 1) {
+            const int t = __ffs(m) - 1;
             const int tx = r.x + t % tw, ty = r.y + t / tw;
-            if (!tile_keep(q0.x, q0.y, e, k, tx, ty, width, height)) continue;
             if (off < (uint64_t)k_max) {
                 keys[off] = ((toff + ty * tx_n + tx) << 32) | depth_bits;
                 vals[off] = (uint32_t)i;
@@ -616,7 +626,7 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
 // ---------------------------------------------------------------------------
 template <typename SHT>
 static cudaError_t launch_pre_fwd_t(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                                    const ViewTable& vt, Screen* screen, ushort4* rects,
+                                    const ViewTable& vt, Screen* screen, TileRect* rects,
                                     uint32_t* local_off, uint32_t* block_sum, cudaStream_t st)
 {
     const int nblk = (int)((n + kPreBlock - 1) / kPreBlock);
@@ -629,7 +639,7 @@ static cudaError_t launch_pre_fwd_t(int64_t n, int deg, const fgs_params* p, con
 }
 
 cudaError_t launch_preprocess_fwd(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                                  const ViewTable& vt, Screen* screen, ushort4* rects,
+                                  const ViewTable& vt, Screen* screen, TileRect* rects,
                                   uint32_t* local_off, uint32_t* block_sum, cudaStream_t st)
 {
     switch (p->dtype[4]) {
@@ -643,7 +653,7 @@ cudaError_t launch_preprocess_fwd(int64_t n, int deg, const fgs_params* p, const
 }
 
 cudaError_t launch_scan_and_duplicate(int64_t n, const ViewTable& vt, const Screen* screen,
-                                      const ushort4* rects, const uint32_t* local_off,
+                                      const TileRect* rects, const uint32_t* local_off,
                                       uint32_t* block_sum, WsHeader* hdr, int64_t k_max,
                                       unsigned long long* keys, uint32_t* vals, cudaStream_t st)
 {
