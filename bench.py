@@ -14,8 +14,10 @@ steps, inputs resident in HBM), ms_per_step, e2e (the same step through the
 public API with the target image and camera copied from pinned host memory
 and the loss read back every step), the batched variant (B views per step,
 CUDA graph, bf16 SH and moments), a roofline entry for the kernel that takes
-the most time (per-kernel CUDA events recorded by the library during the
-timed region), the clocks seen, and the FP64 oracle timed on the host cores.
+the most time (per-kernel CUDA events recorded by the library during a
+second pass over the same workload right after the timed region; the events
+are kept out of the timed region itself, where they would cost ~0.2 ms per
+step), the clocks seen, and the FP64 oracle timed on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -178,6 +180,13 @@ def algorithmic_bytes(label, n, views, instances, pixels, sh_bytes, moment_bytes
         return n * 44 + visible * 48 * sh_bytes / 4 + views * n * (48 + 8 + 4)
     if label == "preprocess_bwd":
         return n * 44 + views * n * 48 * 2 + visible * 48 * sh_bytes / 4 + n * 236
+    if label == "preprocess_bwd_adam":
+        # visibility words of every (view, Gaussian), the rest of the screen
+        # and screen-gradient records of visible ones, and the Adam step of
+        # every element: parameter, first and second moment read and written
+        widths, p_bytes = (3, 3, 4, 1, 3, 45), (4, 4, 4, 4, sh_bytes, sh_bytes)
+        adam = sum(w * (2 * pb + 4 * moment_bytes) for w, pb in zip(widths, p_bytes))
+        return views * n * 16 + visible * views * (32 + 48) + n * adam
     if label == "duplicate":
         return views * n * 8 + visible * (48 + 8 + 4) + instances * 12
     if label in ("sort_downsweep",):
@@ -273,20 +282,6 @@ def run_ours(args, dist):
     if flags:
         raise RuntimeError(f"device flags {flags} after warm-up (capacity)")
 
-    # per-kernel events for the timed region
-    per_step_events = 48
-    cap = per_step_events * args.steps + 8
-    prof_events, prof_labels = None, None
-    if not args.no_profile:
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
-        for e in evs:
-            e.record(stream)
-        torch.cuda.synchronize()
-        handles = (ctypes.c_void_p * cap)(*[e.cuda_event for e in evs])
-        prof_labels = (ctypes.c_char_p * cap)()
-        B.fgs_profile_attach(handles, prof_labels, cap)
-        prof_events = evs
-
     clock = ClockSampler(dist.local)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -302,10 +297,6 @@ def run_ours(args, dist):
     clocks = clock.stop()
     dist.barrier()
     elapsed_ms = t0.elapsed_time(t1)
-    recorded = 0
-    if prof_events is not None:
-        recorded = B.fgs_profile_count()
-        B.fgs_profile_attach(None, None, 0)
     flags, inst_last = tr.rast.error()
     if flags:
         raise RuntimeError(f"device flags {flags} in the timed region")
@@ -313,21 +304,44 @@ def run_ours(args, dist):
     ms_per_step = max_ms / args.steps
     views_per_s = dist.world * args.steps / (max_ms / 1000.0)
 
-    # per-kernel times from consecutive events
-    phases = {}
-    launches = 0
-    if prof_events is not None and recorded > 1:
+    # Per-kernel times: a second pass over the same workload (the cameras that
+    # follow) with a CUDA event recorded after every kernel of the library.
+    # Kept out of the timed region above: the events themselves cost about
+    # 0.2 ms per step.
+    def profile_pass(step_fn, first, nsteps):
+        cap = 48 * nsteps + 8
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
+        for e in evs:
+            e.record(stream)
+        torch.cuda.synchronize()
+        handles = (ctypes.c_void_p * cap)(*[e.cuda_event for e in evs])
+        labels = (ctypes.c_char_p * cap)()
+        B.fgs_profile_attach(handles, labels, cap)
+        for i in range(nsteps):
+            step_fn(first + i)
+        torch.cuda.synchronize()
+        recorded = B.fgs_profile_count()
+        B.fgs_profile_attach(None, None, 0)
+        ph, nl = {}, 0
         for j in range(1, recorded):
-            lab = prof_labels[j].decode()
+            lab = labels[j].decode()
             if lab == "begin":
                 continue
-            dt = prof_events[j - 1].elapsed_time(prof_events[j])
-            ph = phases.setdefault(lab, [0.0, 0])
-            ph[0] += dt
-            ph[1] += 1
+            acc = ph.setdefault(lab, [0.0, 0])
+            acc[0] += evs[j - 1].elapsed_time(evs[j])
+            acc[1] += 1
             if not lab.startswith("zero_"):
-                launches += 1
-    # labels from memsets are not our kernels; everything else is one launch
+                nl += 1   # memsets are not kernels of ours
+        return ph, nl / nsteps
+
+    def per_step_ms(ph, nsteps):
+        return {k: round(v[0] / nsteps, 5) for k, v in sorted(ph.items(), key=lambda kv: -kv[1][0])}
+
+    prof_start = args.warmup + args.steps
+    prof_steps = min(args.steps, 60)
+    phases, launches_per_step = {}, None
+    if not args.no_profile:
+        phases, launches_per_step = profile_pass(one_step, prof_start, prof_steps)
 
     # roofline of the dominant kernel
     visible_est = None
@@ -343,8 +357,8 @@ def run_ours(args, dist):
         if dom in BLEND_FLOPS:
             # fragment counts of every camera the timed region visited
             visits = {}
-            for i in range(args.steps):
-                c = (args.warmup + i) % len(cams)
+            for i in range(prof_steps):
+                c = (prof_start + i) % len(cams)
                 visits[c] = visits.get(c, 0) + 1
             ev = bl = 0.0
             for c, cnt in visits.items():
@@ -353,8 +367,8 @@ def run_ours(args, dist):
                 a, b = tr.rast.fragment_counts()
                 ev += a * cnt
                 bl += b * cnt
-            ev /= args.steps
-            bl /= args.steps
+            ev /= prof_steps
+            bl /= prof_steps
             f_eval, f_blend = BLEND_FLOPS[dom]
             flops = f_eval * ev + f_blend * bl
             props = torch.cuda.get_device_properties(dev)
@@ -387,8 +401,7 @@ def run_ours(args, dist):
             roofline = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None,
                         "unit": None, "frac": None, "traffic": None,
                         "avg_launch_ms": round(avg_ms, 5)}
-    phase_ms = {k: round(v[0] / args.steps, 5) for k, v in sorted(phases.items(),
-                                                                  key=lambda kv: -kv[1][0])}
+    phase_ms = per_step_ms(phases, prof_steps)
 
     # e2e through the public API: target and camera from pinned host memory,
     # loss back to the host, every step
@@ -399,7 +412,8 @@ def run_ours(args, dist):
         host_cams = [torch.frombuffer(bytearray(bytes(B.camera_array([c]))), dtype=torch.uint8)
                      .pin_memory() for c in cams]
         loss_host = torch.zeros(1, pin_memory=True)
-        steps_e2e = max(20, args.steps // 2)
+        # the same camera and target sequence as the timed region
+        steps_e2e = args.steps
         for i in range(3):
             tr.targets.copy_(host_targets[i % n_targets], non_blocking=True)
             tr.views.device.copy_(host_cams[i % len(cams)], non_blocking=True)
@@ -408,7 +422,7 @@ def run_ours(args, dist):
         torch.cuda.synchronize()
         dist.barrier()
         e0 = time.perf_counter()
-        for i in range(steps_e2e):
+        for i in range(args.warmup, args.warmup + steps_e2e):
             tr.targets.copy_(host_targets[i % n_targets], non_blocking=True)
             tr.views.device.copy_(host_cams[i % len(cams)], non_blocking=True)
             tr.step()
@@ -465,17 +479,28 @@ def run_ours(args, dist):
         if tb.rast.error()[0]:
             raise RuntimeError("capacity exceeded in the batched variant")
         bvps = dist.world * steps_b * Bv / (bms / 1000.0)
-        batched.append({"views_per_s": round(bvps, 3), "ms_per_step": round(bms / steps_b, 4),
-                        "views_per_step": Bv, "resolution": f"{W}x{H}", "graph": True,
-                        "storage": "bf16 SH parameters, bf16 Adam moments", "steps": steps_b,
-                        "blend_config": list(tb_tuned[0]) if tb_tuned else None,
-                        "ratio_vs_plain": round(bvps / views_per_s, 4)})
+        entry = {"views_per_s": round(bvps, 3), "ms_per_step": round(bms / steps_b, 4),
+                 "views_per_step": Bv, "resolution": f"{W}x{H}", "graph": True,
+                 "storage": "bf16 SH parameters, bf16 Adam moments", "steps": steps_b,
+                 "blend_config": list(tb_tuned[0]) if tb_tuned else None,
+                 "ratio_vs_plain": round(bvps / views_per_s, 4)}
+        if not args.no_profile:
+            # per-kernel split from eager steps (the graph replays carry no events)
+            def eager_step(i):
+                load_batch(i)
+                tb.step()
+            nb = 4
+            ph_b, _ = profile_pass(eager_step, args.warmup + steps_b, nb)
+            entry["kernel_ms_per_step"] = per_step_ms(ph_b, nb)
+        batched.append(entry)
         del tb
 
     return dict(tuned=list(tuned[0]) if tuned else None, tuning_ms=tuned[1] if tuned else None,
                 ms_per_step=ms_per_step, views_per_s=views_per_s, elapsed_ms=max_ms,
-                phase_ms=phase_ms, launches_per_step=launches / max(args.steps, 1),
-                launches=launches, roofline=roofline, clocks=clocks, e2e=e2e, batched=batched,
+                phase_ms=phase_ms, launches_per_step=launches_per_step,
+                launches=(None if launches_per_step is None
+                          else int(round(launches_per_step * args.steps))),
+                roofline=roofline, clocks=clocks, e2e=e2e, batched=batched,
                 k_max=k_max, instances_last=inst_last, visible_last=visible_est, n=n)
 
 

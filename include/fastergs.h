@@ -242,6 +242,28 @@ int fgs_adam_step_device(const fgs_params *params, const fgs_params *grads,
                          const fgs_params *exp_avg, const fgs_params *exp_avg_sq,
                          fgs_adam_state *state_device, void *stream);
 
+/* Backward pass fused with the Adam step (Sec. 3.3 "Fusing Backward and
+ * Optimizer"): the blend backward of fgs_render_backward, then one kernel
+ * that forms each Gaussian's parameter gradients (summed over the views)
+ * and applies the fgs_adam_step_device update to all of its values right
+ * away, so the gradients never round-trip through memory.  Every Gaussian
+ * is updated, zero-gradient ones included.  params are updated in place
+ * (the same buffers the forward read).  exp_avg / exp_avg_sq: one moment
+ * dtype for all groups; supported pairs (SH dtype, moment dtype): (F32,
+ * F32), (BF16, F32), (BF16, BF16), (F16, F32), (F16, F16); others return
+ * FGS_ERR_DTYPE.  An FP16 second moment is stored as sqrt(v), as in
+ * fgs_adam_step.  grads: optional (NULL skips them); when given, float32
+ * groups that receive the gradients used.  state_device as for
+ * fgs_adam_step_device (its step is incremented).  Results equal
+ * fgs_render_backward followed by fgs_adam_step_device up to the order of
+ * the float32 atomic additions in the blend backward. */
+int fgs_render_backward_adam(void *ws, const fgs_workspace_layout *layout, const fgs_params *params,
+                             int32_t sh_degree, const fgs_camera *cams_host,
+                             const fgs_camera *cams_device, const float bg[3],
+                             const float *dl_dimages, const fgs_params *exp_avg,
+                             const fgs_params *exp_avg_sq, fgs_adam_state *state_device,
+                             const fgs_params *grads, void *stream);
+
 /* Stable LSD radix sort of (uint64 key, uint32 value) pairs on the low
  * `bits` key bits (1..64), 8 bits per pass (Sec. 3.2 "Sorting": a single
  * radix sort of the combined keys).  keys/vals hold the input; keys_alt /

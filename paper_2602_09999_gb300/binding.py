@@ -33,7 +33,8 @@ STATUS = {0: "FGS_OK", -1: "FGS_ERR_NULL", -2: "FGS_ERR_SHAPE", -3: "FGS_ERR_SH_
 FGS_STATIC_SORT_MAX_PAIRS = 1 << 20
 
 EXPORTED = ("fgs_workspace_size", "fgs_render_forward", "fgs_loss_l1_dssim",
-            "fgs_render_backward", "fgs_adam_step", "fgs_adam_step_device",
+            "fgs_render_backward", "fgs_render_backward_adam", "fgs_adam_step",
+            "fgs_adam_step_device",
             "fgs_sort_scratch_bytes", "fgs_sort_pairs", "fgs_sort_pairs_static", "fgs_get_error",
             "fgs_profile_attach",
             "fgs_profile_count", "fgs_strerror")
@@ -112,6 +113,7 @@ def lib():
             L.fgs_render_forward.argtypes = [P, P, P, I32, P, P, P, P, P]
             L.fgs_loss_l1_dssim.argtypes = [P, P, P, P, P, ctypes.c_float, P, P, P]
             L.fgs_render_backward.argtypes = [P, P, P, I32, P, P, P, P, P, P]
+            L.fgs_render_backward_adam.argtypes = [P, P, P, I32, P, P, P, P, P, P, P, P, P]
             L.fgs_adam_step.argtypes = [P, P, P, P, P, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, I32, P]
             L.fgs_adam_step_device.argtypes = [P, P, P, P, P, P]
@@ -183,6 +185,18 @@ def fgs_render_backward(ws, layout, params, sh_degree, cams_host, cams_device, b
            lib().fgs_render_backward(ws, ctypes.byref(layout), ctypes.byref(params),
                                      int(sh_degree), cams_host, cams_device, _float3(bg),
                                      dl_dimages, ctypes.byref(grads), stream))
+
+
+def fgs_render_backward_adam(ws, layout, params, sh_degree, cams_host, cams_device, bg, dl_dimages,
+                             exp_avg, exp_avg_sq, state_device, grads, stream):
+    """grads: an fgs_params or None (the gradients are then not stored)."""
+    _check("fgs_render_backward_adam",
+           lib().fgs_render_backward_adam(ws, ctypes.byref(layout), ctypes.byref(params),
+                                          int(sh_degree), cams_host, cams_device, _float3(bg),
+                                          dl_dimages, ctypes.byref(exp_avg),
+                                          ctypes.byref(exp_avg_sq), state_device,
+                                          ctypes.byref(grads) if grads is not None else None,
+                                          stream))
 
 
 def fgs_adam_step(params, grads, exp_avg, exp_avg_sq, lr, beta1, beta2, eps, step, stream):

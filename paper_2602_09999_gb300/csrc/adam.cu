@@ -10,37 +10,9 @@
 // Storage: parameters float32 / bf16 / fp16; moments float32 / bf16 / fp16.
 // An fp16 second moment is stored as sqrt(v): g^2 underflows fp16 for
 // |g| < 2.4e-4 while |g| itself stays representable.
-#include "fgs_common.cuh"
+#include "adam_math.cuh"
 
 namespace fgs {
-
-template <typename MT> struct VStore {
-    static __device__ __forceinline__ float load(MT x) { return to_f32(x); }
-    static __device__ __forceinline__ MT store(float v) { return from_f32<MT>(v); }
-};
-template <> struct VStore<__half> {
-    static __device__ __forceinline__ float load(__half x) { const float s = __half2float(x); return s * s; }
-    static __device__ __forceinline__ __half store(float v) { return __float2half_rn(sqrtf(v)); }
-};
-
-struct AdamScalars {
-    float step_size, inv_bc2_sqrt, b1, b2, omb1, omb2, eps;
-};
-
-// Scalars of group g: from the kernel argument, or from the device state.
-__device__ __forceinline__ AdamScalars resolve(AdamScalars a, const fgs_adam_state* st, int g)
-{
-    if (st) {
-        a.step_size = st->step_size[g];
-        a.inv_bc2_sqrt = st->inv_bc2_sqrt;
-        a.b1 = st->beta1_f;
-        a.b2 = st->beta2_f;
-        a.omb1 = st->one_minus_beta1_f;
-        a.omb2 = st->one_minus_beta2_f;
-        a.eps = st->eps_f;
-    }
-    return a;
-}
 
 // One thread: advance the step and derive the step sizes (double precision)
 // with the exponential decay of the means learning rate of Suppl. A.
@@ -64,14 +36,6 @@ __global__ void adam_prepare_kernel(fgs_adam_state* st)
     st->one_minus_beta1_f = (float)(1.0 - st->beta1);
     st->one_minus_beta2_f = (float)(1.0 - st->beta2);
     st->eps_f = (float)st->eps;
-}
-
-__device__ __forceinline__ float adam_update(float p, float g, float& m, float& v, const AdamScalars& a)
-{
-    m = m + a.omb1 * (g - m);
-    v = v * a.b2 + a.omb2 * g * g;
-    const float denom = sqrtf(v) * a.inv_bc2_sqrt + a.eps;
-    return p - a.step_size * (m / denom);
 }
 
 template <typename PT, typename MT>

@@ -1,0 +1,54 @@
+// adam_math.cuh -- the per-element Adam update shared by the standalone
+// Adam kernels and the fused preprocess-backward + Adam kernel, so both take
+// exactly the same steps (Suppl. A hyper-parameters; PyTorch's order of
+// operations, Sec. 3.3 "Parameter Updates").
+#pragma once
+#include "fgs_common.cuh"
+
+namespace fgs {
+
+template <typename MT> struct VStore {
+    static __device__ __forceinline__ float load(MT x) { return to_f32(x); }
+    static __device__ __forceinline__ MT store(float v) { return from_f32<MT>(v); }
+};
+template <> struct VStore<__half> {
+    static __device__ __forceinline__ float load(__half x) { const float s = __half2float(x); return s * s; }
+    static __device__ __forceinline__ __half store(float v) { return __float2half_rn(sqrtf(v)); }
+};
+
+// The same second-moment encoding on float values (fp16 holds sqrt(v)):
+// VStore<MT>::load(x) == v_decode<MT>(to_f32(x)) and
+// VStore<MT>::store(v) == from_f32<MT>(v_encode<MT>(v)).
+template <typename MT> __device__ __forceinline__ float v_decode(float stored) { return stored; }
+template <> __device__ __forceinline__ float v_decode<__half>(float s) { return s * s; }
+template <typename MT> __device__ __forceinline__ float v_encode(float v) { return v; }
+template <> __device__ __forceinline__ float v_encode<__half>(float v) { return sqrtf(v); }
+
+struct AdamScalars {
+    float step_size, inv_bc2_sqrt, b1, b2, omb1, omb2, eps;
+};
+
+// Scalars of group g: from the kernel argument, or from the device state.
+__device__ __forceinline__ AdamScalars resolve(AdamScalars a, const fgs_adam_state* st, int g)
+{
+    if (st) {
+        a.step_size = st->step_size[g];
+        a.inv_bc2_sqrt = st->inv_bc2_sqrt;
+        a.b1 = st->beta1_f;
+        a.b2 = st->beta2_f;
+        a.omb1 = st->one_minus_beta1_f;
+        a.omb2 = st->one_minus_beta2_f;
+        a.eps = st->eps_f;
+    }
+    return a;
+}
+
+__device__ __forceinline__ float adam_update(float p, float g, float& m, float& v, const AdamScalars& a)
+{
+    m = m + a.omb1 * (g - m);
+    v = v * a.b2 + a.omb2 * g * g;
+    const float denom = sqrtf(v) * a.inv_bc2_sqrt + a.eps;
+    return p - a.step_size * (m / denom);
+}
+
+}  // namespace fgs

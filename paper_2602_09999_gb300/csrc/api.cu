@@ -43,6 +43,11 @@ cudaError_t launch_adam_group(int64_t count, int pdt, int mdt, void* p, const fl
                               void* v, float step_size, float inv_bc2_sqrt, double b1, double b2,
                               double eps, const fgs_adam_state* ds, int grp, cudaStream_t st);
 cudaError_t launch_adam_prepare(fgs_adam_state* ds, cudaStream_t st);
+cudaError_t launch_preprocess_bwd_adam(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
+                                       const ViewTable& vt, const Screen* screen, const ScreenGrad* sgrad,
+                                       const fgs_params* g, const fgs_params* m, const fgs_params* v,
+                                       const fgs_adam_state* ds, cudaStream_t st);
+bool fused_adam_supported(int sh_dtype, int moment_dtype);
 
 static const int64_t kGroupWidth[FGS_NUM_GROUPS] = {3, 3, 4, 1, 3, 45};
 
@@ -278,6 +283,25 @@ int fgs_loss_l1_dssim(void* ws, const fgs_workspace_layout* L, const fgs_camera*
                                (cudaStream_t)stream));
 }
 
+// Blend backward into the screen-gradient records (shared by both backward
+// entry points).
+static int backward_blend(void* ws, const fgs_workspace_layout* L, const ViewTable& vt, const float bg[3],
+                          const float* dl_dimages, cudaStream_t st)
+{
+    const int64_t n = L->n;
+    const uint32_t* svals = slot<uint32_t>(ws, L, L->sorted_in_alt ? FGS_WS_VALS_ALT : FGS_WS_VALS);
+    Screen* screen = slot<Screen>(ws, L, FGS_WS_SCREEN);
+    ScreenGrad* sgrad = slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD);
+    if (cudaMemsetAsync(sgrad, 0, L->bytes[FGS_WS_SCREEN_GRAD], st) != cudaSuccess) return FGS_ERR_CUDA;
+    profile_mark(st, "zero_screen_grads");
+    return cuda_rc(launch_blend_bwd(vt, n, slot<uint2>(ws, L, FGS_WS_RANGES), svals, screen, bg, dl_dimages,
+                                    slot<float>(ws, L, FGS_WS_T_FINAL),
+                                    slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB), sgrad,
+                                    slot<uint32_t>(ws, L, FGS_WS_TILE_QUEUE),
+                                    L->tuning.blend_pixels_per_thread, L->tuning.blend_batch,
+                                    L->tuning.blend_schedule, st));
+}
+
 int fgs_render_backward(void* ws, const fgs_workspace_layout* L, const fgs_params* params,
                         int32_t sh_degree, const fgs_camera* cams_host,
                         const fgs_camera* cams_device, const float bg[3], const float* dl_dimages,
@@ -291,22 +315,41 @@ int fgs_render_backward(void* ws, const fgs_workspace_layout* L, const fgs_param
     if ((rc = check_params(params, L->n, false)) != FGS_OK) return rc;
     if ((rc = check_params(grads, L->n, true)) != FGS_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    const int64_t n = L->n;
-    const int alt = L->sorted_in_alt;
-    const uint32_t* svals = slot<uint32_t>(ws, L, alt ? FGS_WS_VALS_ALT : FGS_WS_VALS);
-    Screen* screen = slot<Screen>(ws, L, FGS_WS_SCREEN);
-    ScreenGrad* sgrad = slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD);
     profile_mark(st, "begin");
-    cudaMemsetAsync(sgrad, 0, L->bytes[FGS_WS_SCREEN_GRAD], st);
-    profile_mark(st, "zero_screen_grads");
-    if ((rc = cuda_rc(launch_blend_bwd(vt, n, slot<uint2>(ws, L, FGS_WS_RANGES), svals, screen, bg,
-                                       dl_dimages, slot<float>(ws, L, FGS_WS_T_FINAL),
-                                       slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB), sgrad,
-                                       slot<uint32_t>(ws, L, FGS_WS_TILE_QUEUE),
-                                       L->tuning.blend_pixels_per_thread, L->tuning.blend_batch,
-                                       L->tuning.blend_schedule, st))) != FGS_OK)
-        return rc;
-    return cuda_rc(launch_preprocess_bwd(n, sh_degree, params, cams_device, vt, screen, sgrad, grads, st));
+    if ((rc = backward_blend(ws, L, vt, bg, dl_dimages, st)) != FGS_OK) return rc;
+    return cuda_rc(launch_preprocess_bwd(L->n, sh_degree, params, cams_device, vt,
+                                         slot<Screen>(ws, L, FGS_WS_SCREEN),
+                                         slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD), grads, st));
+}
+
+int fgs_render_backward_adam(void* ws, const fgs_workspace_layout* L, const fgs_params* params,
+                             int32_t sh_degree, const fgs_camera* cams_host,
+                             const fgs_camera* cams_device, const float bg[3], const float* dl_dimages,
+                             const fgs_params* exp_avg, const fgs_params* exp_avg_sq,
+                             fgs_adam_state* state_device, const fgs_params* grads, void* stream)
+{
+    ViewTable vt;
+    int rc = check_layout(ws, L, cams_host, &vt);
+    if (rc != FGS_OK) return rc;
+    if (!cams_device || !bg || !dl_dimages || !exp_avg || !exp_avg_sq || !state_device) return FGS_ERR_NULL;
+    if (sh_degree < 0 || sh_degree > 3) return FGS_ERR_SH_DEGREE;
+    if ((rc = check_params(params, L->n, false)) != FGS_OK) return rc;
+    if (grads && (rc = check_params(grads, L->n, true)) != FGS_OK) return rc;
+    if (exp_avg->n != L->n || exp_avg_sq->n != L->n) return FGS_ERR_SHAPE;
+    for (int g = 0; g < FGS_NUM_GROUPS; ++g) {
+        if (!exp_avg->data[g] || !exp_avg_sq->data[g]) return FGS_ERR_NULL;
+        if (exp_avg->dtype[g] != exp_avg->dtype[0] || exp_avg_sq->dtype[g] != exp_avg->dtype[0])
+            return FGS_ERR_DTYPE;
+    }
+    if (!fused_adam_supported(params->dtype[4], exp_avg->dtype[0])) return FGS_ERR_DTYPE;
+    cudaStream_t st = (cudaStream_t)stream;
+    profile_mark(st, "begin");
+    if ((rc = backward_blend(ws, L, vt, bg, dl_dimages, st)) != FGS_OK) return rc;
+    if (launch_adam_prepare(state_device, st) != cudaSuccess) return FGS_ERR_CUDA;
+    return cuda_rc(launch_preprocess_bwd_adam(L->n, sh_degree, params, cams_device, vt,
+                                              slot<Screen>(ws, L, FGS_WS_SCREEN),
+                                              slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD), grads, exp_avg,
+                                              exp_avg_sq, state_device, st));
 }
 
 int fgs_adam_step(const fgs_params* params, const fgs_params* grads, const fgs_params* exp_avg,

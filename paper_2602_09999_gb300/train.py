@@ -116,6 +116,16 @@ class Rasterizer:
                             targets.data_ptr(), lam, loss_out.data_ptr(), dl.data_ptr(),
                             current_stream())
 
+    def backward_adam(self, params: B.fgs_params, sh_degree: int, bg, dl: torch.Tensor,
+                      exp_avg: B.fgs_params, exp_avg_sq: B.fgs_params, adam_state: int,
+                      grads=None):
+        """Backward fused with the Adam step (params updated in place);
+        grads (optional) receives the gradients used."""
+        B.fgs_render_backward_adam(self.ws.data_ptr(), self.layout, params, sh_degree,
+                                   self.views.host, self.views.device.data_ptr(), bg,
+                                   dl.data_ptr(), exp_avg, exp_avg_sq, adam_state, grads,
+                                   current_stream())
+
     def backward(self, params: B.fgs_params, sh_degree: int, bg, dl: torch.Tensor,
                  grads: B.fgs_params):
         B.fgs_render_backward(self.ws.data_ptr(), self.layout, params, sh_degree, self.views.host,
@@ -182,16 +192,27 @@ def to_device_params(params, device="cuda", sh_dtype=torch.float32):
     return out
 
 
+# (SH dtype, moment dtype) pairs the fused backward + Adam supports
+FUSED_PAIRS = {(torch.float32, torch.float32), (torch.bfloat16, torch.float32),
+               (torch.bfloat16, torch.bfloat16), (torch.float16, torch.float32),
+               (torch.float16, torch.float16)}
+
+
 class Trainer:
     """Parameters, gradients, Adam moments and the per-step buffers of one
     batch shape.  ``step()`` runs forward, loss, backward and Adam on the
     current stream without host synchronisation; ``capture()`` records it
-    as a CUDA graph that ``replay()`` re-launches."""
+    as a CUDA graph that ``replay()`` re-launches.  With ``fused_adam`` (the
+    default where the storage pair allows it) the backward and the Adam
+    step are one call and the gradients are stored only if ``store_grads``."""
 
     def __init__(self, params, cams: Sequence, k_max: int, sh_degree=3, lam=0.2,
                  bg=(0.0, 0.0, 0.0), lr=DEFAULT_LR, sh_dtype=torch.float32,
-                 moment_dtype=torch.float32, lr_means_final=0.0, decay_steps=0, device="cuda"):
+                 moment_dtype=torch.float32, lr_means_final=0.0, decay_steps=0, device="cuda",
+                 fused_adam=True, store_grads=False):
         self.device = device
+        self.fused_adam = bool(fused_adam) and (sh_dtype, moment_dtype) in FUSED_PAIRS
+        self.store_grads = bool(store_grads)
         self.params = to_device_params(params, device, sh_dtype)
         self.n = self.params["means"].shape[0]
         self.grads = {k: torch.zeros(self.params[k].shape, device=device) for k in GROUPS}
@@ -234,6 +255,11 @@ class Trainer:
         s = current_stream()
         self.rast.forward(self.p_s, self.sh_degree, self.bg, self.images)
         self.rast.loss(self.images, self.targets, self.lam, self.loss, self.dl)
+        if self.fused_adam:
+            self.rast.backward_adam(self.p_s, self.sh_degree, self.bg, self.dl, self.m_s, self.v_s,
+                                    self.adam_state.data_ptr(),
+                                    self.g_s if self.store_grads else None)
+            return
         self.rast.backward(self.p_s, self.sh_degree, self.bg, self.dl, self.g_s)
         B.fgs_adam_step_device(self.p_s, self.g_s, self.m_s, self.v_s, self.adam_state.data_ptr(), s)
 

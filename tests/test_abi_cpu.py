@@ -113,3 +113,7 @@ def test_null_pointer_checks_before_any_launch(lib):
     with pytest.raises(B.FGSError) as e:
         B.fgs_sort_pairs(None, None, None, None, 10, 32, None, 0, None)
     assert e.value.code == -1
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_render_backward_adam(None, L, B.fgs_params(), 3, cam, None, (0, 0, 0), None,
+                                   B.fgs_params(), B.fgs_params(), None, None, None)
+    assert e.value.code == -1

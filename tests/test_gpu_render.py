@@ -284,6 +284,50 @@ def test_full_step_matches_oracle(oracle_mod):
         np.testing.assert_array_equal(got[still], np.asarray(params[k], np.float64)[still])
 
 
+@pytest.mark.parametrize("sh_dt,m_dt", [("f32", "f32"), ("bf16", "bf16"), ("f16", "f16"),
+                                         ("bf16", "f32")])
+def test_fused_backward_adam_matches_separate(oracle_mod, sh_dt, m_dt):
+    """fgs_render_backward_adam equals fgs_render_backward followed by
+    fgs_adam_step_device: the gradients up to atomic-add order, and its
+    update exactly the Adam step of the gradients it used (every Gaussian,
+    invisible ones included)."""
+    dts = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+    params = scenes.outdoor_scene(20_000, seed=81)
+    cams = scenes.orbit_cameras(2, 160, 120, radius=6.0, seed=4)
+    targets = [scenes.target_image(160, 120, view=i) for i in range(2)]
+    kw = dict(k_max=400_000, sh_dtype=dts[sh_dt], moment_dtype=dts[m_dt])
+    sep = T.Trainer(params, cams, fused_adam=False, **kw)
+    fus = T.Trainer(params, cams, fused_adam=True, store_grads=True, **kw)
+    ref = T.Trainer(params, cams, fused_adam=False, **kw)   # Adam of the fused gradients
+    assert fus.fused_adam and not sep.fused_adam
+    for tr in (sep, fus):
+        tr.set_targets(targets)
+        tr.step()
+    torch.cuda.synchronize()
+    assert fus.adam_step_count() == sep.adam_step_count() == 1
+    assert torch.equal(fus.images, sep.images)
+    bad = ill_conditioned(cams, params)
+    for k in GROUPS:
+        a, b = fus.grads[k].cpu().numpy(), sep.grads[k].cpu().numpy()
+        assert np.any(b != 0), k
+        assert rel_l2(a[~bad], b[~bad]) < 1e-5, k
+    for k in GROUPS:
+        ref.grads[k].copy_(fus.grads[k])
+    B.fgs_adam_step_device(ref.p_s, ref.g_s, ref.m_s, ref.v_s, ref.adam_state.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for i, k in enumerate(GROUPS):
+        for got, want in ((fus.params[k], ref.params[k]), (fus.exp_avg[k], ref.exp_avg[k]),
+                          (fus.exp_avg_sq[k], ref.exp_avg_sq[k])):
+            g64, w64 = got.double().cpu().numpy(), want.double().cpu().numpy()
+            # same arithmetic; allow one unit of the storage type for contraction choices
+            eps = torch.finfo(got.dtype).eps
+            assert np.all(np.abs(g64 - w64) <= eps * np.abs(w64) + 1e-30), k
+        # zero-gradient (invisible) Gaussians are part of the comparison (Sec. 3.3)
+        zero = (fus.grads[k].reshape(fus.n, -1) == 0).all(dim=1).cpu().numpy()
+        assert zero.any()
+
+
 def test_graph_replay_matches_eager():
     params = scenes.tiny_scene(4000, seed=51)
     cams = [scenes.tiny_camera(128, 128)]
