@@ -187,12 +187,18 @@ def algorithmic_bytes(label, n, views, instances, pixels, sh_bytes, moment_bytes
         widths, p_bytes = (3, 3, 4, 1, 3, 45), (4, 4, 4, 4, sh_bytes, sh_bytes)
         adam = sum(w * (2 * pb + 4 * moment_bytes) for w, pb in zip(widths, p_bytes))
         return views * n * 16 + visible * views * (32 + 48) + n * adam
+    if label == "compact_visible":
+        return views * n * 16 + visible * 16
     if label == "duplicate":
-        return views * n * 8 + visible * (48 + 8 + 4) + instances * 12
-    if label in ("sort_downsweep",):
-        return instances * 24
+        return visible * (4 + 16 + 4) + instances * 8
+    if label == "sort_downsweep":
+        return instances * 16
     if label == "sort_upsweep":
-        return instances * 8
+        return instances * 4
+    if label == "depth_sort_downsweep":
+        return visible * 16
+    if label == "depth_sort_upsweep":
+        return visible * 4
     if label == "blend_fwd":
         return instances * 52 + pixels * 20
     if label == "blend_bwd":

@@ -103,13 +103,13 @@ enum fgs_ws_slot {
                            inclusive; x0 > x1 when not rendered), then for rectangles of at most
                            32 tiles the uint32 mask of tiles kept by culling (bit t = row-major
                            tile t), then an unused uint32 */
-    FGS_WS_LOCAL_OFF,   /* uint32 [n_views*n]: CTA-local exclusive prefix of tile counts */
-    FGS_WS_BLOCK_SUM,   /* uint32 [n_views*ceil(n/256)+1]: prefix of CTA totals */
-    FGS_WS_KEYS,        /* uint64 [k_max]: (global tile << 32) | depth bits */
+    FGS_WS_LOCAL_OFF,   /* uint32 [n_views*n]: CTA-local exclusive prefix of the rendered flags */
+    FGS_WS_BLOCK_SUM,   /* uint32 [n_views*ceil(n/256)+1]: prefix of the CTA totals */
+    FGS_WS_KEYS,        /* uint32 [k_max]: global tile id of each instance (tile sort keys) */
     FGS_WS_VALS,        /* uint32 [k_max]: Gaussian index */
-    FGS_WS_KEYS_ALT,    /* uint64 [k_max]: sort ping-pong buffer */
+    FGS_WS_KEYS_ALT,    /* uint32 [k_max]: sort ping-pong buffer */
     FGS_WS_VALS_ALT,    /* uint32 [k_max] */
-    FGS_WS_SORT_HIST,   /* uint32 radix histograms */
+    FGS_WS_SORT_HIST,   /* uint32 radix histograms (shared by both sorts) */
     FGS_WS_RANGES,      /* uint2 [total_tiles]: [start, end) of each tile's list */
     FGS_WS_T_FINAL,     /* float [total_pixels]: final transmittance */
     FGS_WS_N_CONTRIB,   /* uint32 [total_pixels]: list position of the last blended entry */
@@ -122,6 +122,12 @@ enum fgs_ws_slot {
     FGS_WS_TILE_QUEUE,  /* uint32 [4 + total_tiles]: work-queue counters (forward head and
                            exits, backward head and exits), then every tile of every view in
                            descending order of list length (written by each forward) */
+    FGS_WS_DEPTH_KEYS,  /* uint32 [n_views*n]: depth bits of the rendered (view, Gaussian) pairs */
+    FGS_WS_DEPTH_VALS,  /* uint32 [n_views*n]: view * n + Gaussian index of those pairs */
+    FGS_WS_DEPTH_KEYS_ALT, /* uint32 [n_views*n]: depth-sort ping-pong buffers */
+    FGS_WS_DEPTH_VALS_ALT,
+    FGS_WS_SORTED_OFF,  /* uint32 [n_views*n]: instance offsets in depth order (CTA-local) */
+    FGS_WS_SORTED_BLOCK, /* uint32 [ceil(n_views*n/1024)+1]: prefix of those CTA totals */
     FGS_WS_NUM_SLOTS
 };
 
@@ -153,8 +159,8 @@ typedef struct fgs_workspace_layout {
     int32_t n_views;
     int32_t total_tiles;
     int64_t total_pixels;
-    int32_t sort_bits;       /* key bits the radix sort orders */
-    int32_t sorted_in_alt;   /* 1: sorted keys/values end in the *_ALT slots */
+    int32_t sort_bits;       /* tile-id bits the tile sort orders (the depth sort: 32) */
+    int32_t sorted_in_alt;   /* 1: the tile-sorted keys/values end in the *_ALT slots */
     fgs_tuning tuning;       /* launch choices (defaults filled in) */
 } fgs_workspace_layout;
 

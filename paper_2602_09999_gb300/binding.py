@@ -25,7 +25,8 @@ FGS_FLAG_CAPACITY = 1
 (FGS_WS_HEADER, FGS_WS_SCREEN, FGS_WS_RECT, FGS_WS_LOCAL_OFF, FGS_WS_BLOCK_SUM, FGS_WS_KEYS,
  FGS_WS_VALS, FGS_WS_KEYS_ALT, FGS_WS_VALS_ALT, FGS_WS_SORT_HIST, FGS_WS_RANGES, FGS_WS_T_FINAL,
  FGS_WS_N_CONTRIB, FGS_WS_SCREEN_GRAD, FGS_WS_LOSS_MAPS, FGS_WS_LOSS_PART, FGS_WS_N_BLENDED,
- FGS_WS_TILE_QUEUE, FGS_WS_NUM_SLOTS) = range(19)
+ FGS_WS_TILE_QUEUE, FGS_WS_DEPTH_KEYS, FGS_WS_DEPTH_VALS, FGS_WS_DEPTH_KEYS_ALT,
+ FGS_WS_DEPTH_VALS_ALT, FGS_WS_SORTED_OFF, FGS_WS_SORTED_BLOCK, FGS_WS_NUM_SLOTS) = range(25)
 
 STATUS = {0: "FGS_OK", -1: "FGS_ERR_NULL", -2: "FGS_ERR_SHAPE", -3: "FGS_ERR_SH_DEGREE",
           -4: "FGS_ERR_WORKSPACE", -5: "FGS_ERR_DTYPE", -6: "FGS_ERR_CUDA", -7: "FGS_ERR_VIEWS",

@@ -11,19 +11,26 @@ namespace fgs {
 cudaError_t launch_preprocess_fwd(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
                                   const ViewTable& vt, Screen* screen, TileRect* rects,
                                   uint32_t* local_off, uint32_t* block_sum, cudaStream_t st);
-cudaError_t launch_scan_and_duplicate(int64_t n, const ViewTable& vt, const Screen* screen,
-                                      const TileRect* rects, const uint32_t* local_off,
-                                      uint32_t* block_sum, WsHeader* hdr, int64_t k_max,
-                                      unsigned long long* keys, uint32_t* vals, cudaStream_t st);
+cudaError_t launch_compact_visible(int64_t n, const ViewTable& vt, const Screen* screen,
+                                   const TileRect* rects, const uint32_t* local_off, uint32_t* block_sum,
+                                   WsHeader* hdr, uint32_t* dkeys, uint32_t* dvals, cudaStream_t st);
+cudaError_t launch_sorted_duplicate(int64_t n, const ViewTable& vt, const Screen* screen,
+                                    const TileRect* rects, const uint32_t* svals, uint32_t* sorted_off,
+                                    uint32_t* sorted_block, WsHeader* hdr, int64_t k_max, uint32_t* keys,
+                                    uint32_t* vals, cudaStream_t st);
+int64_t count_scan_blocks(int64_t pairs);
 cudaError_t launch_preprocess_bwd(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
                                   const ViewTable& vt, const Screen* screen,
                                   const ScreenGrad* sgrad, const fgs_params* g, cudaStream_t st);
 size_t sort_hist_bytes(int64_t n_max);
+int radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n_max,
+                   const uint32_t* n_dev, int bits, uint32_t* hist, bool depth, cudaStream_t st,
+                   cudaError_t* err);
 int radix_sort(unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
                uint32_t* vals_alt, int64_t n_max, const uint32_t* n_dev, int bits, uint32_t* hist,
                cudaStream_t st, cudaError_t* err);
 cudaError_t launch_set_count(uint32_t* dst, uint32_t value, cudaStream_t st);
-cudaError_t launch_tile_ranges(const unsigned long long* keys, const uint32_t* n_dev, int64_t n_max,
+cudaError_t launch_tile_ranges(const uint32_t* keys, const uint32_t* n_dev, int64_t n_max,
                                uint2* ranges, int total_tiles, cudaStream_t st);
 cudaError_t launch_tile_order(const uint2* ranges, int total_tiles, uint32_t* queue, cudaStream_t st);
 cudaError_t launch_blend_fwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
@@ -110,12 +117,16 @@ static int build_views(const fgs_camera* cams, int32_t nv, ViewTable* vt)
     return FGS_OK;
 }
 
+// Key bits of the tile sort: enough for every global tile id.
 static int sort_bits_for(int64_t total_tiles)
 {
-    int b = 0;
+    int b = 1;
     while ((1ll << b) < total_tiles) ++b;
-    return 32 + b;
+    return b;
 }
+
+// The depth sort orders all 32 bits of the (positive) float depths.
+static const int kDepthBits = 32;
 
 static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_max,
                        fgs_workspace_layout* L, ViewTable* vt)
@@ -134,11 +145,11 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     sz[FGS_WS_RECT] = sizeof(TileRect) * (size_t)vn;
     sz[FGS_WS_LOCAL_OFF] = sizeof(uint32_t) * (size_t)vn;
     sz[FGS_WS_BLOCK_SUM] = sizeof(uint32_t) * (size_t)(nv * nblk + 1);
-    sz[FGS_WS_KEYS] = sizeof(unsigned long long) * (size_t)k_max;
+    sz[FGS_WS_KEYS] = sizeof(uint32_t) * (size_t)k_max;
     sz[FGS_WS_VALS] = sizeof(uint32_t) * (size_t)k_max;
     sz[FGS_WS_KEYS_ALT] = sz[FGS_WS_KEYS];
     sz[FGS_WS_VALS_ALT] = sz[FGS_WS_VALS];
-    sz[FGS_WS_SORT_HIST] = sort_hist_bytes(k_max);
+    sz[FGS_WS_SORT_HIST] = sort_hist_bytes(k_max > vn ? k_max : vn);
     sz[FGS_WS_RANGES] = sizeof(uint2) * (size_t)vt->total_tiles;
     sz[FGS_WS_T_FINAL] = sizeof(float) * (size_t)vt->total_pixels;
     sz[FGS_WS_N_CONTRIB] = sizeof(uint32_t) * (size_t)vt->total_pixels;
@@ -147,6 +158,12 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     sz[FGS_WS_LOSS_PART] = sizeof(double) * 2 * (size_t)vt->total_tiles;
     sz[FGS_WS_N_BLENDED] = sizeof(uint32_t) * (size_t)vt->total_pixels;
     sz[FGS_WS_TILE_QUEUE] = sizeof(uint32_t) * (4 + (size_t)vt->total_tiles);
+    sz[FGS_WS_DEPTH_KEYS] = sizeof(uint32_t) * (size_t)vn;
+    sz[FGS_WS_DEPTH_VALS] = sizeof(uint32_t) * (size_t)vn;
+    sz[FGS_WS_DEPTH_KEYS_ALT] = sizeof(uint32_t) * (size_t)vn;
+    sz[FGS_WS_DEPTH_VALS_ALT] = sizeof(uint32_t) * (size_t)vn;
+    sz[FGS_WS_SORTED_OFF] = sizeof(uint32_t) * (size_t)vn;
+    sz[FGS_WS_SORTED_BLOCK] = sizeof(uint32_t) * (size_t)(count_scan_blocks(vn) + 1);
     size_t off = 0;
     for (int s = 0; s < FGS_WS_NUM_SLOTS; ++s) {
         L->offset[s] = off;
@@ -236,22 +253,38 @@ int fgs_render_forward(void* ws, const fgs_workspace_layout* L, const fgs_params
     TileRect* rects = slot<TileRect>(ws, L, FGS_WS_RECT);
     uint32_t* local_off = slot<uint32_t>(ws, L, FGS_WS_LOCAL_OFF);
     uint32_t* block_sum = slot<uint32_t>(ws, L, FGS_WS_BLOCK_SUM);
-    unsigned long long* keys = slot<unsigned long long>(ws, L, FGS_WS_KEYS);
+    uint32_t* keys = slot<uint32_t>(ws, L, FGS_WS_KEYS);
     uint32_t* vals = slot<uint32_t>(ws, L, FGS_WS_VALS);
-    unsigned long long* keys_alt = slot<unsigned long long>(ws, L, FGS_WS_KEYS_ALT);
+    uint32_t* keys_alt = slot<uint32_t>(ws, L, FGS_WS_KEYS_ALT);
     uint32_t* vals_alt = slot<uint32_t>(ws, L, FGS_WS_VALS_ALT);
+    uint32_t* dkeys = slot<uint32_t>(ws, L, FGS_WS_DEPTH_KEYS);
+    uint32_t* dvals = slot<uint32_t>(ws, L, FGS_WS_DEPTH_VALS);
+    uint32_t* dkeys_alt = slot<uint32_t>(ws, L, FGS_WS_DEPTH_KEYS_ALT);
+    uint32_t* dvals_alt = slot<uint32_t>(ws, L, FGS_WS_DEPTH_VALS_ALT);
+    uint32_t* hist = slot<uint32_t>(ws, L, FGS_WS_SORT_HIST);
+    const int64_t vn = (int64_t)vt.n_views * n;
     if ((rc = cuda_rc(launch_preprocess_fwd(n, sh_degree, params, cams_device, vt, screen, rects,
                                             local_off, block_sum, st))) != FGS_OK)
         return rc;
-    if ((rc = cuda_rc(launch_scan_and_duplicate(n, vt, screen, rects, local_off, block_sum, hdr,
-                                                L->k_max, keys, vals, st))) != FGS_OK)
+    // stage 1: the rendered (view, Gaussian) pairs by depth (stable: ties keep (view, id) order)
+    if ((rc = cuda_rc(launch_compact_visible(n, vt, screen, rects, local_off, block_sum, hdr, dkeys, dvals,
+                                             st))) != FGS_OK)
+        return rc;
+    cudaError_t e;
+    const int dalt = radix_sort_u32(dkeys, dvals, dkeys_alt, dvals_alt, vn, &hdr->counters[1], kDepthBits,
+                                    hist, true, st, &e);
+    if (e != cudaSuccess) return FGS_ERR_CUDA;
+    // stage 2: their instances, emitted in depth order, stably by tile id
+    if ((rc = cuda_rc(launch_sorted_duplicate(n, vt, screen, rects, dalt ? dvals_alt : dvals,
+                                              slot<uint32_t>(ws, L, FGS_WS_SORTED_OFF),
+                                              slot<uint32_t>(ws, L, FGS_WS_SORTED_BLOCK), hdr, L->k_max,
+                                              keys, vals, st))) != FGS_OK)
         return rc;
     const uint32_t* k_dev = &hdr->counters[0];
-    cudaError_t e;
-    const int alt = radix_sort(keys, vals, keys_alt, vals_alt, L->k_max, k_dev, L->sort_bits,
-                               slot<uint32_t>(ws, L, FGS_WS_SORT_HIST), st, &e);
+    const int alt = radix_sort_u32(keys, vals, keys_alt, vals_alt, L->k_max, k_dev, L->sort_bits, hist,
+                                   false, st, &e);
     if (e != cudaSuccess) return FGS_ERR_CUDA;
-    const unsigned long long* skeys = alt ? keys_alt : keys;
+    const uint32_t* skeys = alt ? keys_alt : keys;
     const uint32_t* svals = alt ? vals_alt : vals;
     uint2* ranges = slot<uint2>(ws, L, FGS_WS_RANGES);
     if ((rc = cuda_rc(launch_tile_ranges(skeys, k_dev, L->k_max, ranges, vt.total_tiles, st))) != FGS_OK)

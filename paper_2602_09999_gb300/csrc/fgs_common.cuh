@@ -49,13 +49,13 @@ struct alignas(16) Screen {
 };
 
 // Tile set of one (view, Gaussian): its tile rectangle (inclusive; x0 > x1
-// when it is not rendered) and, for rectangles of at most 32 tiles, the
-// tiles that survive culling (bit t = row-major tile t of the rectangle), so
-// the duplication pass need not test them again.
+// when it is not rendered), for rectangles of at most 32 tiles the tiles
+// that survive culling (bit t = row-major tile t of the rectangle), so the
+// duplication pass need not test them again, and the number of kept tiles.
 struct alignas(16) TileRect {
     ushort4 r;
     uint32_t keep;
-    uint32_t unused;
+    uint32_t count;
 };
 
 // Opacity-aware extent (Sec. 3.2): alpha = o G reaches 1/255 where

@@ -219,7 +219,7 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
         TileRect rect;
         rect.r = make_ushort4(1, 1, 0, 0);
         rect.keep = keep;
-        rect.unused = 0;
+        rect.count = count;
         if (count > 0) {
             rect.r = make_ushort4((unsigned short)g.tx0, (unsigned short)g.ty0,
                                   (unsigned short)(g.tx0 + g.tw - 1),
@@ -255,18 +255,21 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
             screen[vi] = rec;
             rects[vi] = rect;
         }
+        // compaction offsets of the rendered (view, Gaussian) pairs
         uint32_t total;
-        const uint32_t excl = block_exclusive_scan(count, warp_tot, total);
+        const uint32_t excl = block_exclusive_scan(count > 0 ? 1u : 0u, warp_tot, total);
         if (valid) local_off[vi] = excl;
         if (threadIdx.x == 0) block_sum[(int64_t)v * nblk + blockIdx.x] = total;
     }
 }
 
-// Exclusive prefix of the CTA totals (one CTA); writes the total instance
-// count (may exceed k_max) and the clamped count used by the sort.
+// Exclusive prefix of the CTA totals (one CTA).  instances: the totals are
+// instance counts -- writes the total (may exceed k_max), the clamped count
+// the tile sort uses (counters[0]) and the capacity flag; otherwise they
+// count rendered (view, Gaussian) pairs -- writes that count (counters[1]).
 __global__ void __launch_bounds__(1024)
 scan_block_sums_kernel(uint32_t* __restrict__ block_sum, int64_t count, WsHeader* __restrict__ hdr,
-                       int64_t k_max)
+                       int64_t k_max, bool instances)
 {
     __shared__ unsigned long long part[1024];
     const int t = threadIdx.x;
@@ -290,58 +293,118 @@ scan_block_sums_kernel(uint32_t* __restrict__ block_sum, int64_t count, WsHeader
     }
     if (t == 1023) {
         const unsigned long long tot = part[1023];
-        hdr->instances = tot;
-        hdr->counters[0] = (uint32_t)min(tot, (unsigned long long)k_max);
-        if (tot > (unsigned long long)k_max) set_flag(hdr, FGS_FLAG_CAPACITY);
+        if (instances) {
+            hdr->instances = tot;
+            hdr->counters[0] = (uint32_t)min(tot, (unsigned long long)k_max);
+            if (tot > (unsigned long long)k_max) set_flag(hdr, FGS_FLAG_CAPACITY);
+        } else {
+            hdr->counters[1] = (uint32_t)tot;
+        }
     }
 }
 
-// Emits (global tile << 32 | depth bits, Gaussian id) for every kept tile
-// of every (view, Gaussian), in row-major tile order at the scanned offset.
-// Small rectangles walk the kept-tile mask the preprocess recorded; large
-// ones are culled again by the whole warp, 32 tiles per step, with a ballot
-// prefix keeping the row-major order.
+// Rendered (view, Gaussian) pairs in (view, id) order, as (depth bits,
+// view * n + id) for the depth sort (depths are > 0, so their float bits
+// order like the values).
 __global__ void __launch_bounds__(256)
-duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
-                 const TileRect* __restrict__ rects, const uint32_t* __restrict__ local_off,
-                 const uint32_t* __restrict__ block_sum, int nblk, int64_t k_max,
-                 unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals)
+compact_visible_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
+                       const TileRect* __restrict__ rects, const uint32_t* __restrict__ local_off,
+                       const uint32_t* __restrict__ block_sum, int nblk, uint32_t* __restrict__ dkeys,
+                       uint32_t* __restrict__ dvals)
 {
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= (int64_t)vt.n_views * n) return;
+    const ushort4 r = rects[gi].r;
+    if (r.x > r.z) return;
+    const int v = (int)(gi / n);
+    const int64_t i = gi - (int64_t)v * n;
+    const uint32_t pos = local_off[gi] + block_sum[(int64_t)v * nblk + i / kPreBlock];
+    dkeys[pos] = __float_as_uint(screen[gi].q1.w);
+    dvals[pos] = (uint32_t)gi;
+}
+
+// Instance offsets in depth order: exclusive prefix, within each CTA of
+// kCountTile sorted entries, of their instance counts, and the CTA totals.
+constexpr int kCountItems = 4;
+constexpr int kCountTile = kPreBlock * kCountItems;
+
+__global__ void __launch_bounds__(kPreBlock)
+sorted_count_scan_kernel(const uint32_t* __restrict__ n_dev, const uint32_t* __restrict__ svals,
+                         const TileRect* __restrict__ rects, uint32_t* __restrict__ sorted_off,
+                         uint32_t* __restrict__ sorted_block)
+{
+    __shared__ uint32_t warp_tot[kPreBlock / 32];
+    const uint32_t F = *n_dev;
+    const int64_t base = (int64_t)blockIdx.x * kCountTile + (int64_t)threadIdx.x * kCountItems;
+    uint32_t c[kCountItems], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kCountItems; ++q) {
+        const int64_t j = base + q;
+        c[q] = j < (int64_t)F ? rects[svals[j]].count : 0u;
+        sum += c[q];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(sum, warp_tot, total);
+#pragma unroll
+    for (int q = 0; q < kCountItems; ++q) {
+        const int64_t j = base + q;
+        if (j < (int64_t)F) sorted_off[j] = run;
+        run += c[q];
+    }
+    if (threadIdx.x == 0) sorted_block[blockIdx.x] = total;
+}
+
+// Emits (global tile, Gaussian id) for every kept tile of every rendered
+// (view, Gaussian) pair into the range its depth-order offset gives it, so
+// that a stable sort by tile keeps depth order, ties by id, inside each
+// tile.  Small rectangles walk the kept-tile mask the preprocess recorded;
+// large ones are culled again by the whole warp, 32 tiles per step, with a
+// ballot prefix.  Lane l of warp w takes entry l * W + w (W warps in use):
+// near splats, which have the large rectangles, come first in depth order,
+// and this spreads them over all warps instead of a few.
+__global__ void __launch_bounds__(256)
+duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
+                 const TileRect* __restrict__ rects, const uint32_t* __restrict__ n_vis,
+                 const uint32_t* __restrict__ svals, const uint32_t* __restrict__ sorted_off,
+                 const uint32_t* __restrict__ sorted_block, int64_t k_max, uint32_t* __restrict__ keys,
+                 uint32_t* __restrict__ vals)
+{
     const int lane = threadIdx.x & 31;
-    const bool valid = gi < (int64_t)vt.n_views * n;
+    const int64_t F = *n_vis;
+    const int64_t W = (F + 31) / 32;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t j = (int64_t)lane * W + wg;
+    const bool has = wg < W && j < F;
     int v = 0;
-    int64_t i = 0;
-    bool vis = false;
-    float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
+    int64_t i = 0, gi = 0;
     TileRect tr;
     tr.r = make_ushort4(1, 1, 0, 0);
     tr.keep = 0;
     uint64_t off = 0;
-    if (valid) {
+    if (has) {
+        gi = svals[j];
         v = (int)(gi / n);
         i = gi - (int64_t)v * n;
         tr = rects[gi];
-        vis = tr.r.x <= tr.r.z;
-        if (vis) off = (uint64_t)local_off[gi] + block_sum[(int64_t)v * nblk + i / kPreBlock];
+        off = (uint64_t)sorted_off[j] + sorted_block[j / kCountTile];
     }
     const ushort4 r = tr.r;
     const int tw = (int)r.z - (int)r.x + 1;
-    const int nt = vis ? tw * ((int)r.w - (int)r.y + 1) : 0;
-    const bool big = vis && nt > kBigRect;
+    const int nt = has ? tw * ((int)r.w - (int)r.y + 1) : 0;
+    const bool big = has && nt > kBigRect;
+    float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
     if (big) {
         q0 = screen[gi].q0;
         q1 = screen[gi].q1;
     }
-    if (vis && !big) {
-        const unsigned long long depth_bits = __float_as_uint(screen[gi].q1.w);
-        const unsigned long long toff = (unsigned long long)vt.tile_off[v];
+    if (has && !big) {
+        const uint32_t toff = (uint32_t)vt.tile_off[v];
         const int tx_n = vt.tiles_x[v];
         for (uint32_t m = tr.keep; m; m &= m - 1) {
             const int t = __ffs(m) - 1;
             const int tx = r.x + t % tw, ty = r.y + t / tw;
             if (off < (uint64_t)k_max) {
-                keys[off] = ((toff + ty * tx_n + tx) << 32) | depth_bits;
+                keys[off] = toff + (uint32_t)(ty * tx_n + tx);
                 vals[off] = (uint32_t)i;
             }
             ++off;
@@ -357,14 +420,13 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
                                                __shfl_sync(0xffffffffu, q1.x, src),
                                                __shfl_sync(0xffffffffu, q1.y, src));
         const float k = opacity_k(__shfl_sync(0xffffffffu, q1.z, src));
-        const unsigned long long depth_bits = __float_as_uint(__shfl_sync(0xffffffffu, q1.w, src));
         const int sv = __shfl_sync(0xffffffffu, v, src);
         const uint32_t sid = (uint32_t)__shfl_sync(0xffffffffu, (unsigned long long)i, src);
         const int tx0 = __shfl_sync(0xffffffffu, (int)r.x, src), ty0 = __shfl_sync(0xffffffffu, (int)r.y, src);
         const int stw = __shfl_sync(0xffffffffu, tw, src), snt = __shfl_sync(0xffffffffu, nt, src);
         uint64_t soff = __shfl_sync(0xffffffffu, (unsigned long long)off, src);
         const int width = vt.width[sv], height = vt.height[sv], tx_n = vt.tiles_x[sv];
-        const unsigned long long toff = (unsigned long long)vt.tile_off[sv];
+        const uint32_t toff = (uint32_t)vt.tile_off[sv];
         for (int base = 0; base < snt; base += 32) {
             const int t = base + lane;
             const int tx = tx0 + t % stw, ty = ty0 + t / stw;
@@ -372,7 +434,7 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             const uint64_t pos = soff + __popc(m & ((1u << lane) - 1u));
             if (keep && pos < (uint64_t)k_max) {
-                keys[pos] = ((toff + ty * tx_n + tx) << 32) | depth_bits;
+                keys[pos] = toff + (uint32_t)(ty * tx_n + tx);
                 vals[pos] = sid;
             }
             soff += __popc(m);
@@ -799,20 +861,45 @@ cudaError_t launch_preprocess_fwd(int64_t n, int deg, const fgs_params* p, const
     }
 }
 
-cudaError_t launch_scan_and_duplicate(int64_t n, const ViewTable& vt, const Screen* screen,
-                                      const TileRect* rects, const uint32_t* local_off,
-                                      uint32_t* block_sum, WsHeader* hdr, int64_t k_max,
-                                      unsigned long long* keys, uint32_t* vals, cudaStream_t st)
+// After the preprocess: prefix of the CTA totals of rendered (view,
+// Gaussian) pairs and their compaction into (depth bits, view * n + id) for
+// the depth sort.
+cudaError_t launch_compact_visible(int64_t n, const ViewTable& vt, const Screen* screen,
+                                   const TileRect* rects, const uint32_t* local_off, uint32_t* block_sum,
+                                   WsHeader* hdr, uint32_t* dkeys, uint32_t* dvals, cudaStream_t st)
 {
     const int nblk = (int)((n + kPreBlock - 1) / kPreBlock);
-    scan_block_sums_kernel<<<1, 1024, 0, st>>>(block_sum, (int64_t)vt.n_views * nblk, hdr, k_max);
+    scan_block_sums_kernel<<<1, 1024, 0, st>>>(block_sum, (int64_t)vt.n_views * nblk, hdr, 0, false);
     profile_mark(st, "scan_block_sums");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)vt.n_views * n;
-    const int grid = (int)((total + 255) / 256);
-    duplicate_kernel<<<grid, 256, 0, st>>>(n, vt, screen, rects, local_off, block_sum, nblk, k_max,
-                                           keys, vals);
+    compact_visible_kernel<<<(int)((total + 255) / 256), 256, 0, st>>>(n, vt, screen, rects, local_off,
+                                                                       block_sum, nblk, dkeys, dvals);
+    profile_mark(st, "compact_visible");
+    return cudaGetLastError();
+}
+
+int64_t count_scan_blocks(int64_t pairs) { return (pairs + kCountTile - 1) / kCountTile; }
+
+// After the depth sort (svals: view * n + id in depth order): the instance
+// offsets in that order and the emission of the (tile, id) pairs.
+cudaError_t launch_sorted_duplicate(int64_t n, const ViewTable& vt, const Screen* screen,
+                                    const TileRect* rects, const uint32_t* svals, uint32_t* sorted_off,
+                                    uint32_t* sorted_block, WsHeader* hdr, int64_t k_max, uint32_t* keys,
+                                    uint32_t* vals, cudaStream_t st)
+{
+    const int64_t total = (int64_t)vt.n_views * n;
+    const int64_t nb = count_scan_blocks(total);
+    const uint32_t* n_vis = &hdr->counters[1];
+    sorted_count_scan_kernel<<<(int)nb, kPreBlock, 0, st>>>(n_vis, svals, rects, sorted_off, sorted_block);
+    profile_mark(st, "count_scan");
+    scan_block_sums_kernel<<<1, 1024, 0, st>>>(sorted_block, nb, hdr, k_max, true);
+    profile_mark(st, "scan_instance_sums");
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    duplicate_kernel<<<(int)((total + 255) / 256), 256, 0, st>>>(n, vt, screen, rects, n_vis, svals,
+                                                                 sorted_off, sorted_block, k_max, keys, vals);
     profile_mark(st, "duplicate");
     return cudaGetLastError();
 }

@@ -1,6 +1,9 @@
-// sort.cu -- stable LSD radix sort of (uint64 key, uint32 value) pairs and
-// the per-tile range extraction (Sec. 3.2 "Sorting": one radix sort of the
-// combined (tile << 32 | depth) keys; Suppl. B.2 complexity model O(k n)).
+// sort.cu -- stable LSD radix sort of (uint32 or uint64 key, uint32 value)
+// pairs and the per-tile range extraction (Sec. 3.2 "Sorting", Suppl. B.2:
+// O(k n) for k key bits).  The render path sorts in two stages: the visible
+// (view, Gaussian) pairs by their 32-bit depth, then the instances emitted
+// in that order by their tile id alone (a stable sort keeps the depth order
+// inside each tile); the standalone entry points sort 64-bit keys.
 //
 // Each pass orders 8 key bits (the last pass only the remaining ones) with
 // three kernels:
@@ -22,8 +25,9 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per CTA
 constexpr int kRadix = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 
+template <typename KT>
 __global__ void __launch_bounds__(kSortThreads)
-radix_upsweep_kernel(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ n_dev,
+radix_upsweep_kernel(const KT* __restrict__ keys, const uint32_t* __restrict__ n_dev,
                      int shift, uint32_t dmask, int nb_max, uint32_t* __restrict__ hist)
 {
     __shared__ uint32_t h[kSortWarps][kRadix];
@@ -85,8 +89,8 @@ radix_scan_kernel(uint32_t* __restrict__ hist, const uint32_t* __restrict__ n_de
     if (t == 255) dtot[blockIdx.x] = part[255];
 }
 
-struct DownSmem {
-    unsigned long long keys[kSortTile];
+template <typename KT> struct DownSmem {
+    KT keys[kSortTile];
     uint32_t vals[kSortTile];
     uint32_t cnt[kSortWarps][kRadix];
     uint32_t local_start[kRadix];
@@ -95,9 +99,10 @@ struct DownSmem {
     uint32_t scan_b[kRadix];
 };
 
-__device__ __forceinline__ void radix_downsweep_tile(DownSmem& S, const unsigned long long* __restrict__ keys_in,
+template <typename KT>
+__device__ __forceinline__ void radix_downsweep_tile(DownSmem<KT>& S, const KT* __restrict__ keys_in,
                                                      const uint32_t* __restrict__ vals_in,
-                                                     unsigned long long* __restrict__ keys_out,
+                                                     KT* __restrict__ keys_out,
                                                      uint32_t* __restrict__ vals_out,
                                                      const uint32_t* __restrict__ hist,
                                                      const uint32_t* __restrict__ dtot, uint32_t n,
@@ -109,14 +114,14 @@ __device__ __forceinline__ void radix_downsweep_tile(DownSmem& S, const unsigned
     for (int d = tid; d < kSortWarps * kRadix; d += kSortThreads) (&S.cnt[0][0])[d] = 0;
     __syncthreads();
 
-    unsigned long long k[kSortItems];
+    KT k[kSortItems];
     uint32_t val[kSortItems];
     uint32_t dr[kSortItems];  // digit (bits 24..31) | rank within the warp (bits 0..23)
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int64_t idx = base + (int64_t)warp * (kSortItems * 32) + r * 32 + lane;
         const bool valid = idx < n;
-        k[r] = valid ? keys_in[idx] : 0ull;
+        k[r] = valid ? keys_in[idx] : (KT)0;
         val[r] = valid ? vals_in[idx] : 0u;
         const uint32_t d = (uint32_t)(k[r] >> shift) & dmask;
         uint32_t peers = __ballot_sync(0xffffffffu, valid);
@@ -171,7 +176,7 @@ __device__ __forceinline__ void radix_downsweep_tile(DownSmem& S, const unsigned
     __syncthreads();
     const int count = (int)min((int64_t)kSortTile, (int64_t)n - base);
     for (int j = tid; j < count; j += kSortThreads) {
-        const unsigned long long key = S.keys[j];
+        const KT key = S.keys[j];
         const uint32_t dd = (uint32_t)(key >> shift) & dmask;
         const uint32_t g = S.glob_off[dd] + j;
         keys_out[g] = key;
@@ -179,15 +184,15 @@ __device__ __forceinline__ void radix_downsweep_tile(DownSmem& S, const unsigned
     }
 }
 
+template <typename KT>
 __global__ void __launch_bounds__(kSortThreads)
-radix_downsweep_kernel(const unsigned long long* __restrict__ keys_in,
-                       const uint32_t* __restrict__ vals_in, unsigned long long* __restrict__ keys_out,
-                       uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ hist,
-                       const uint32_t* __restrict__ dtot, const uint32_t* __restrict__ n_dev,
-                       int shift, uint32_t dmask, int nb_max)
+radix_downsweep_kernel(const KT* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                       KT* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                       const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dtot,
+                       const uint32_t* __restrict__ n_dev, int shift, uint32_t dmask, int nb_max)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    DownSmem& S = *reinterpret_cast<DownSmem*>(smem_raw);
+    DownSmem<KT>& S = *reinterpret_cast<DownSmem<KT>*>(smem_raw);
     const uint32_t n = *n_dev;
     const int nb = (int)((n + kSortTile - 1) / kSortTile);
     for (int b = blockIdx.x; b < nb; b += gridDim.x) {
@@ -196,19 +201,20 @@ radix_downsweep_kernel(const unsigned long long* __restrict__ keys_in,
     }
 }
 
-// [start, end) of each tile's run in the sorted keys; ranges must be zeroed.
+// [start, end) of each tile's run in the sorted tile keys; ranges must be
+// zeroed.
 __global__ void __launch_bounds__(256)
-tile_ranges_kernel(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ n_dev,
+tile_ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev,
                    uint2* __restrict__ ranges)
 {
     const uint32_t n = *n_dev;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t tile = (uint32_t)(keys[j] >> 32);
+        const uint32_t tile = keys[j];
         if (j == 0) {
             ranges[tile].x = 0;
         } else {
-            const uint32_t prev = (uint32_t)(keys[j - 1] >> 32);
+            const uint32_t prev = keys[j - 1];
             if (prev != tile) {
                 ranges[prev].y = (uint32_t)j;
                 ranges[tile].x = (uint32_t)j;
@@ -242,18 +248,21 @@ size_t sort_hist_bytes(int64_t n_max)
 }
 
 // Sorts n_dev[0] pairs on bits [0, bits).  Returns 1 when the result is in
-// the *_alt buffers.  hist: sort_hist_bytes(n_max) bytes.
-int radix_sort(unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
-               uint32_t* vals_alt, int64_t n_max, const uint32_t* n_dev, int bits,
-               uint32_t* hist, cudaStream_t st, cudaError_t* err)
+// the *_alt buffers.  hist: sort_hist_bytes(n_max) bytes.  `label` prefixes
+// the per-kernel profiling marks.
+template <typename KT>
+static int radix_sort_t(KT* keys, uint32_t* vals, KT* keys_alt, uint32_t* vals_alt, int64_t n_max,
+                        const uint32_t* n_dev, int bits, uint32_t* hist, cudaStream_t st, cudaError_t* err,
+                        const char* const labels[3])
 {
-    const int smem = (int)sizeof(DownSmem);
-    cudaFuncSetAttribute(radix_downsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int smem = (int)sizeof(DownSmem<KT>);
+    cudaFuncSetAttribute(radix_downsweep_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int nb_max = (int)((n_max + kSortTile - 1) / kSortTile);
-    const int grid = nb_max < resident_grid(2) ? nb_max : resident_grid(2);
+    const int per_sm = sizeof(KT) == 4 ? 3 : 2;
+    const int grid = nb_max < resident_grid(per_sm) ? nb_max : resident_grid(per_sm);
     uint32_t* dtot = hist + (int64_t)kRadix * (nb_max > 0 ? nb_max : 1);
     int passes = (bits + 7) / 8;
-    unsigned long long *ki = keys, *ko = keys_alt;
+    KT *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     *err = cudaSuccess;
     if (nb_max == 0) return 0;
@@ -261,25 +270,46 @@ int radix_sort(unsigned long long* keys, uint32_t* vals, unsigned long long* key
         const int shift = 8 * p;
         const int dbits = bits - shift < 8 ? bits - shift : 8;  // the last pass may be narrower
         const uint32_t dmask = (1u << dbits) - 1u;
-        radix_upsweep_kernel<<<grid, kSortThreads, 0, st>>>(ki, n_dev, shift, dmask, nb_max, hist);
-        profile_mark(st, "sort_upsweep");
+        radix_upsweep_kernel<KT><<<grid, kSortThreads, 0, st>>>(ki, n_dev, shift, dmask, nb_max, hist);
+        profile_mark(st, labels[0]);
         radix_scan_kernel<<<kRadix, 256, 0, st>>>(hist, n_dev, nb_max, dtot);
-        profile_mark(st, "sort_scan");
-        radix_downsweep_kernel<<<grid, kSortThreads, smem, st>>>(ki, vi, ko, vo, hist, dtot, n_dev,
-                                                                 shift, dmask, nb_max);
-        profile_mark(st, "sort_downsweep");
+        profile_mark(st, labels[1]);
+        radix_downsweep_kernel<KT><<<grid, kSortThreads, smem, st>>>(ki, vi, ko, vo, hist, dtot, n_dev,
+                                                                     shift, dmask, nb_max);
+        profile_mark(st, labels[2]);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             *err = e;
             return 0;
         }
-        unsigned long long* tk = ki; ki = ko; ko = tk;
+        KT* tk = ki; ki = ko; ko = tk;
         uint32_t* tv = vi; vi = vo; vo = tv;
     }
     return passes & 1;
 }
 
-cudaError_t launch_tile_ranges(const unsigned long long* keys, const uint32_t* n_dev, int64_t n_max,
+static const char* const kSortLabels[3] = {"sort_upsweep", "sort_scan", "sort_downsweep"};
+static const char* const kDepthSortLabels[3] = {"depth_sort_upsweep", "depth_sort_scan",
+                                                "depth_sort_downsweep"};
+
+int radix_sort(unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
+               uint32_t* vals_alt, int64_t n_max, const uint32_t* n_dev, int bits,
+               uint32_t* hist, cudaStream_t st, cudaError_t* err)
+{
+    return radix_sort_t<unsigned long long>(keys, vals, keys_alt, vals_alt, n_max, n_dev, bits, hist, st,
+                                            err, kSortLabels);
+}
+
+// 32-bit keys: the depth sort (depth = true) and the tile sort of the render path.
+int radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n_max,
+                   const uint32_t* n_dev, int bits, uint32_t* hist, bool depth, cudaStream_t st,
+                   cudaError_t* err)
+{
+    return radix_sort_t<uint32_t>(keys, vals, keys_alt, vals_alt, n_max, n_dev, bits, hist, st, err,
+                                  depth ? kDepthSortLabels : kSortLabels);
+}
+
+cudaError_t launch_tile_ranges(const uint32_t* keys, const uint32_t* n_dev, int64_t n_max,
                                uint2* ranges, int total_tiles, cudaStream_t st)
 {
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)total_tiles, st);

@@ -139,7 +139,7 @@ class Rasterizer:
     # read-only views of forward state, for tests and diagnostics
     def sorted_lists(self):
         alt = bool(self.layout.sorted_in_alt)
-        keys = self.slot(B.FGS_WS_KEYS_ALT if alt else B.FGS_WS_KEYS, torch.int64)
+        keys = self.slot(B.FGS_WS_KEYS_ALT if alt else B.FGS_WS_KEYS, torch.int32)  # tile ids
         vals = self.slot(B.FGS_WS_VALS_ALT if alt else B.FGS_WS_VALS, torch.int32)
         ranges = self.slot(B.FGS_WS_RANGES, torch.int32).view(-1, 2)
         return keys, vals, ranges

@@ -71,10 +71,9 @@ def compare_lists(rast, views, pre_list, lists_list):
                 for x, y in zip(got, want):
                     if x != y:
                         assert abs(d[x] - d[y]) <= 2e-6 * abs(d[x]), (v, t, x, y)
-            # tile ids and depth bits in the keys
+            # the tile-sort keys are the global tile ids
             if gb > ga:
-                kt = (keys[ga:gb] >> 32)
-                assert np.all(kt == tile_off + t)
+                assert np.all(keys[ga:gb] == tile_off + t)
             compared += 1
         tile_off += ntiles
     return compared, excluded

@@ -62,7 +62,7 @@ def test_workspace_layout(lib):
     tiles = 78 * 52 + 40 * 27
     assert L.total_tiles == tiles
     assert L.total_pixels == 1237 * 822 + 640 * 426
-    assert L.sort_bits == 32 + int(np.ceil(np.log2(tiles)))
+    assert L.sort_bits == int(np.ceil(np.log2(tiles)))
     assert L.sorted_in_alt == ((L.sort_bits + 7) // 8) % 2
     offs = list(L.offset)
     sizes = list(L.bytes)
@@ -72,7 +72,8 @@ def test_workspace_layout(lib):
             assert offs[i] + sizes[i] <= offs[i + 1]
     assert offs[-1] + sizes[-1] <= L.total_bytes
     assert sizes[B.FGS_WS_SCREEN] == 48 * 2 * 3_000_000
-    assert sizes[B.FGS_WS_KEYS] == 8 * 10_000_000
+    assert sizes[B.FGS_WS_KEYS] == 4 * 10_000_000
+    assert sizes[B.FGS_WS_DEPTH_KEYS] == 4 * 2 * 3_000_000
 
 
 @pytest.mark.parametrize("n,nv,k,code", [(0, 1, 10, -2), (2 ** 31, 1, 10, -2), (10, 0, 10, -7),
