@@ -36,16 +36,18 @@ struct Entry {
     float4 rgbo;  // r, g, b, o
 };
 
+// Thread -> pixel map with PPT pixels per thread: the CTA covers one 16x16
+// tile, split into 8 blocks of 8 columns x 4 rows (block b: columns
+// 8 (b & 1) .. +7, rows 4 (b >> 1) .. +3).  Pixel k of warp w lies in block
+// w PPT + k, lane l at the block's column l & 7 and row l >> 3, so a warp
+// can skip, per pixel slot, the blocks a splat's footprint misses.
 template <int PPT> struct TileMap {
     static constexpr int NT = kTilePixels / PPT;
     static constexpr int NW = NT / 32;
-    static constexpr int R = 2 * PPT;
-    int v, W, H, x0, y0, px;
-    int py[PPT];
+    static_assert(NW * PPT == 8, "eight blocks per tile");
+    int v, W, H, x0, y0;
+    int px[PPT], py[PPT];
     bool inside[PPT];
-    // Thread -> pixel map with PPT pixels per thread: the CTA covers one
-    // 16x16 tile; warp w covers rows [R w, R w + R) with R = 2 PPT, lane l
-    // the column l & 15 and the rows (l >> 4) + 2 k, k < PPT.
     __device__ __forceinline__ TileMap(const ViewTable& vt, int tile)
     {
         v = view_of_tile(vt, tile);
@@ -55,30 +57,36 @@ template <int PPT> struct TileMap {
         W = vt.width[v];
         H = vt.height[v];
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        px = x0 + (lane & 15);
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            py[k] = y0 + R * w + (lane >> 4) + 2 * k;
-            inside[k] = px < W && py[k] < H;
+            const int b = w * PPT + k;
+            px[k] = x0 + 8 * (b & 1) + (lane & 7);
+            py[k] = y0 + 4 * (b >> 1) + (lane >> 3);
+            inside[k] = px[k] < W && py[k] < H;
         }
     }
 };
 
-// Bit w set when the bounding box of the ellipse d^T conic d <= k (where
+// Bit b set when the bounding box of the ellipse d^T conic d <= k (where
 // alpha can reach 1/255), widened by 1% and 0.01 px against float32
-// rounding of the alpha test, meets the pixel rows of warp w.  The vertical
-// half-extent is sqrt(k Sigma_yy) with Sigma_yy = s^2 / ls + c^2 / lb.
-__device__ __forceinline__ uint32_t warp_row_mask(const Screen& rec, int y0, int R, int nw)
+// rounding of the alpha test, meets the pixel centres of block b of the
+// tile at (x0, y0).  The half-extents are sqrt(k Sigma_xx), sqrt(k Sigma_yy)
+// with Sigma_xx = c^2 / ls + s^2 / lb and Sigma_yy = s^2 / ls + c^2 / lb.
+__device__ __forceinline__ uint32_t block_mask(const Screen& rec, int x0, int y0)
 {
     const float c = rec.q1.x, sn = rec.q1.y;
+    const float kk = opacity_k(rec.q1.z);
+    const float sxx = c * c / rec.q0.w + sn * sn / rec.q0.z;
     const float syy = sn * sn / rec.q0.w + c * c / rec.q0.z;
-    const float ey = sqrtf(opacity_k(rec.q1.z) * syy) * 1.01f + 0.01f;
-    const float my = rec.q0.y;
-    if (!(ey == ey)) return 0xffu;
+    const float ex = sqrtf(kk * sxx) * 1.01f + 0.01f;
+    const float ey = sqrtf(kk * syy) * 1.01f + 0.01f;
+    const float mx = rec.q0.x, my = rec.q0.y;
+    if (!(ex == ex && ey == ey)) return 0xffu;
     uint32_t m = 0;
-    for (int w = 0; w < nw; ++w) {
-        const float r0 = (float)(y0 + R * w) + 0.5f, r1 = r0 + (float)(R - 1);
-        if (my + ey >= r0 && my - ey <= r1) m |= 1u << w;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const float bx0 = (float)(x0 + 8 * (b & 1)) + 0.5f, by0 = (float)(y0 + 4 * (b >> 1)) + 0.5f;
+        if (mx + ex >= bx0 && mx - ex <= bx0 + 7.0f && my + ey >= by0 && my - ey <= by0 + 3.0f) m |= 1u << b;
     }
     return m;
 }
@@ -196,7 +204,6 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
     const int warp = threadIdx.x >> 5;
     const uint2 range = ranges[tile];
     const Screen* scr = screen + (int64_t)tm.v * n;
-    const float fx = (float)tm.px + 0.5f;
     float T[PPT], C0[PPT], C1[PPT], C2[PPT];
     uint32_t last[PPT], blended[PPT];
     bool done[PPT];
@@ -218,13 +225,14 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
             if (j < range.y) {
                 const Screen rec = scr[gids[j]];
                 stage_entry(rec, s_e[e]);
-                s_mask[e] = (uint8_t)warp_row_mask(rec, tm.y0, Map::R, Map::NW);
+                s_mask[e] = (uint8_t)block_mask(rec, tm.x0, tm.y0);
             }
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)BATCH, range.y - start);
         for (int jj = 0; jj < cnt && !all_done; ++jj) {
-            if (!((s_mask[jj] >> warp) & 1u)) continue;
+            const uint32_t wm = ((uint32_t)s_mask[jj] >> (warp * PPT)) & ((1u << PPT) - 1u);
+            if (!wm) continue;  // uniform over the warp
             const Entry e = s_e[jj];
             all_done = true;
 #pragma unroll
@@ -232,7 +240,8 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
                 if (done[k]) continue;
                 Frag f;
                 float u, w;
-                if (eval_frag(fx, (float)tm.py[k] + 0.5f, e, f, u, w)) {
+                if (((wm >> k) & 1u) &&
+                    eval_frag((float)tm.px[k] + 0.5f, (float)tm.py[k] + 0.5f, e, f, u, w)) {
                     const float test = T[k] * (1.0f - f.alpha);
                     if (test < kTMin) {
                         done[k] = true;
@@ -255,7 +264,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         if (!tm.inside[k]) continue;
-        const int64_t pix = (int64_t)tm.py[k] * tm.W + tm.px;
+        const int64_t pix = (int64_t)tm.py[k] * tm.W + tm.px[k];
         img[pix] = C0[k] + T[k] * bg0;
         img[P + pix] = C1[k] + T[k] * bg1;
         img[2 * P + pix] = C2[k] + T[k] * bg2;
@@ -336,7 +345,6 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
     const uint2 range = ranges[tile];
     const Screen* scr = screen + (int64_t)tm.v * n;
     ScreenGrad* sg = sgrad + (int64_t)tm.v * n;
-    const float fx = (float)tm.px + 0.5f;
     const int64_t P = (int64_t)tm.W * tm.H;
     const float* dl = dL_dimg + 3 * vt.pix_off[tm.v];
 
@@ -352,7 +360,7 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
         A1[k] = bg1;
         A2[k] = bg2;
         if (tm.inside[k]) {
-            const int64_t pix = (int64_t)tm.py[k] * tm.W + tm.px;
+            const int64_t pix = (int64_t)tm.py[k] * tm.W + tm.px[k];
             g0[k] = dl[pix];
             g1[k] = dl[P + pix];
             g2[k] = dl[2 * P + pix];
@@ -379,7 +387,7 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
                 const Screen rec = scr[g];
                 s_gid[e] = g;
                 stage_entry(rec, s_e[e]);
-                s_mask[e] = (uint8_t)warp_row_mask(rec, tm.y0, Map::R, Map::NW);
+                s_mask[e] = (uint8_t)block_mask(rec, tm.x0, tm.y0);
             }
 #pragma unroll
             for (int k = 0; k < 9; ++k) s_acc[k][e] = 0.f;
@@ -387,7 +395,8 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
         __syncthreads();
         for (int jj = 0; jj < cnt; ++jj) {
             const uint32_t pos = bend - jj - range.x;  // 1-based list position
-            if (pos > warp_max || !((s_mask[jj] >> warp) & 1u)) continue;  // uniform over the warp
+            const uint32_t wm = ((uint32_t)s_mask[jj] >> (warp * PPT)) & ((1u << PPT) - 1u);
+            if (pos > warp_max || !wm) continue;  // uniform over the warp
             const Entry e = s_e[jj];
             // eigenvalues back from the pre-scaled form
             const float ls = -2.0f / kLog2e * e.coef.x, lb = -2.0f / kLog2e * e.coef.y;
@@ -399,7 +408,9 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
             for (int k = 0; k < PPT; ++k) {
                 Frag f;
                 float u, w;
-                if (!(pos <= last[k] && eval_frag(fx, (float)tm.py[k] + 0.5f, e, f, u, w))) continue;
+                if (!(((wm >> k) & 1u) && pos <= last[k] &&
+                      eval_frag((float)tm.px[k] + 0.5f, (float)tm.py[k] + 0.5f, e, f, u, w)))
+                    continue;
                 any = true;
                 // transmittance in front of the entry; 1 - alpha >= 0.01, so the
                 // approximate divide (2 ulp) is in range
