@@ -27,12 +27,18 @@ namespace fgs {
 
 constexpr float kLog2e = 1.4426950408889634f;
 
-// One list entry staged in shared memory: mean, the conic's eigen form
-// pre-scaled for exp2 (A = -ls log2(e) / 2, B = -lb log2(e) / 2), the
-// major-axis direction (cos, sin), colour and opacity.
+// 2 ln 2: converts the exp2-scaled axis coordinates back to C d (below).
+constexpr float kTwoLn2 = 1.3862943611198906f;
+
+// One list entry staged in shared memory: mean, the conic's eigen form as
+// its two axes pre-scaled for exp2, colour and opacity.  With a = ls log2(e)
+// / 2, b = lb log2(e) / 2 and the major axis (c, s), coef = (c sqrt(a),
+// s sqrt(a), c sqrt(b), s sqrt(b)), so that with u' = coef.x dx + coef.y dy
+// and w' = coef.z dy - coef.w dx the exponent of Eq. 3 in base 2 is
+// -(u'^2 + w'^2) = -(log2 e / 2) d^T conic d, never positive.
 struct Entry {
     float2 xy;
-    float4 coef;  // A, B, cos, sin
+    float4 coef;
     float4 rgbo;  // r, g, b, o
 };
 
@@ -93,25 +99,36 @@ __device__ __forceinline__ uint32_t block_mask(const Screen& rec, int x0, int y0
 
 __device__ __forceinline__ void stage_entry(const Screen& rec, Entry& e)
 {
+    const float sa = sqrtf(0.5f * kLog2e * rec.q0.w), sb = sqrtf(0.5f * kLog2e * rec.q0.z);
+    const float c = rec.q1.x, sn = rec.q1.y;
     e.xy = make_float2(rec.q0.x, rec.q0.y);
-    e.coef = make_float4(-0.5f * kLog2e * rec.q0.w, -0.5f * kLog2e * rec.q0.z, rec.q1.x, rec.q1.y);
+    e.coef = make_float4(c * sa, sn * sa, c * sb, sn * sb);
     e.rgbo = make_float4(rec.q2.x, rec.q2.y, rec.q2.z, rec.q1.z);
 }
 
+// 2^x for x <= 0 on the special-function unit; results below 2^-126 flush to
+// zero, far below any alpha that is blended.
+__device__ __forceinline__ float exp2_ftz(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Alpha of one fragment (Eq. 3 with the 3DGS rules), shared by the forward
-// and the backward so both take the same decisions: skip when the exponent
-// is positive or alpha < 1/255; alpha = min(0.99, o G).  Also returns the
-// offset along (u) and across (w) the major axis for the backward.
+// and the backward so both take the same decisions: skip alpha < 1/255;
+// alpha = min(0.99, o G).  The exponent is a negated sum of squares, so the
+// positive-exponent case cannot arise.  Also returns the scaled offsets u'
+// (along the major axis) and w' (across it) for the backward.
 __device__ __forceinline__ bool eval_frag(float px, float py, const Entry& e, Frag& f, float& u,
                                           float& w)
 {
     f.dx = __fsub_rn(px, e.xy.x);
     f.dy = __fsub_rn(py, e.xy.y);
-    u = __fmaf_rn(e.coef.z, f.dx, __fmul_rn(e.coef.w, f.dy));
+    u = __fmaf_rn(e.coef.x, f.dx, __fmul_rn(e.coef.y, f.dy));
     w = __fmaf_rn(e.coef.z, f.dy, -__fmul_rn(e.coef.w, f.dx));
-    const float l2 = __fmaf_rn(__fmul_rn(e.coef.x, u), u, __fmul_rn(__fmul_rn(e.coef.y, w), w));
-    if (l2 > 0.0f) return false;
-    f.G = exp2f(l2);
+    const float l2 = -__fmaf_rn(u, u, __fmul_rn(w, w));
+    f.G = exp2_ftz(l2);
     const float oG = __fmul_rn(e.rgbo.w, f.G);
     f.clamped = oG >= kAlphaMax;
     f.alpha = f.clamped ? kAlphaMax : oG;
@@ -398,8 +415,6 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
             const uint32_t wm = ((uint32_t)s_mask[jj] >> (warp * PPT)) & ((1u << PPT) - 1u);
             if (pos > warp_max || !wm) continue;  // uniform over the warp
             const Entry e = s_e[jj];
-            // eigenvalues back from the pre-scaled form
-            const float ls = -2.0f / kLog2e * e.coef.x, lb = -2.0f / kLog2e * e.coef.y;
             float d[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) d[k] = 0.f;
@@ -426,17 +441,17 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
                 A2[k] = f.alpha * e.rgbo.z + (1.0f - f.alpha) * A2[k];
                 T[k] = Ti;
                 if (!f.clamped) {
-                    // power = -q/2 with q = d^T C d; v = C d = ls u e + lb w e_perp
-                    // from the eigen form (no cancellation)
+                    // power = -q/2 with q = d^T C d; C d = ls u e + lb w e_perp from
+                    // the eigen form (no cancellation) = 2 ln 2 (vx, vy) below
                     const float dpow = dalpha * f.alpha;  // alpha = o G here
-                    const float lu = ls * u, lw = lb * w;
-                    const float vx = e.coef.z * lu - e.coef.w * lw;
-                    const float vy = e.coef.w * lu + e.coef.z * lw;
+                    const float vx = e.coef.x * u - e.coef.w * w;
+                    const float vy = e.coef.y * u + e.coef.z * w;
                     d[5] += dalpha * f.G;
-                    d[0] += dpow * vx;  // dL/dmu = dpow C d
-                    d[1] += dpow * vy;
-                    // dL/dSigma (full symmetric) = -C (dL/dC) C = dpow v v^T / 2
-                    const float hp = 0.5f * dpow;
+                    const float dk = dpow * kTwoLn2;
+                    d[0] += dk * vx;  // dL/dmu = dpow C d
+                    d[1] += dk * vy;
+                    // dL/dSigma (full symmetric) = -C (dL/dC) C = dpow (C d)(C d)^T / 2
+                    const float hp = 0.5f * dk * kTwoLn2;
                     d[2] += hp * vx * vx;
                     d[3] += hp * vx * vy;
                     d[4] += hp * vy * vy;
