@@ -605,6 +605,11 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
             if (__float_as_uint(screen[(int64_t)v * n + i].q2.w) & 8u) vis_mask |= 1u << v;
     float mu[3] = {0.f, 0.f, 0.f};
     const int ncoef = (sh_degree + 1) * (sh_degree + 1);
+    // this Gaussian's sh_rest gradient row in shared memory (stride 45 floats:
+    // consecutive threads fall in different banks), summed over the views
+    float* my = s_rest + 45 * threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 45; ++q) my[q] = 0.f;
     if (vis_mask) {
         mu[0] = means[3 * i]; mu[1] = means[3 * i + 1]; mu[2] = means[3 * i + 2];
         const float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
@@ -662,6 +667,14 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
                 // band 0 (Y_0 is constant)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) gdc[c] += SHC::c0 * grgb[c];
+                // bands 1..3: d/dsh_kc += Y_k(dir) grgb_c
+                float Y[16];
+                sh_basis(d[0], d[1], d[2], sh_degree, Y);
+#pragma unroll
+                for (int kk = 1; kk < 16; ++kk)
+                    if (kk < ncoef)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) my[3 * (kk - 1) + c] += Y[kk] * grgb[c];
             }
 
             // Eq. 1: mu2D = (fx tx/tz + cx, fy ty/tz + cy)
@@ -742,35 +755,6 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
         const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
 #pragma unroll
         for (int a = 0; a < 4; ++a) gq[a] = (dq[a] - qh[a] * qd) / qn;
-    }
-    // SH bands 1..3: d/dsh_kc = sum_v Y_k(dir_v) grgb_vc, four coefficients at a
-    // time, staged in shared memory for coalesced stores
-    float* my = s_rest + 45 * threadIdx.x;
-    for (int kb = 1; kb < 16; kb += 5) {
-        float acc[5][3];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) acc[q][0] = acc[q][1] = acc[q][2] = 0.f;
-        if (vis_mask && kb < ncoef) {
-            for (int v = 0; v < vt.n_views; ++v) {
-                if (!(vis_mask >> v & 1u)) continue;
-                const int64_t vi = (int64_t)v * n + i;
-                const uint32_t bits = __float_as_uint(screen[vi].q2.w);
-                const ScreenGrad g = sgrad[vi];
-                const Cam cam = load_cam(cams, v);
-                float d[3], il, grgb[3];
-                view_colour_grad(cam, mu, bits, g, d, il, grgb);
-                float Y[16];
-                sh_basis(d[0], d[1], d[2], sh_degree, Y);
-#pragma unroll
-                for (int q = 0; q < 5; ++q)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) acc[q][c] += Y[kb + q] * grgb[c];
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 5; ++q)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) my[3 * (kb - 1 + q) + c] = acc[q][c];
     }
     if (FUSED) {
         // slices: means [0, 384), log-scales [384, 768), quats [768, 1280),
