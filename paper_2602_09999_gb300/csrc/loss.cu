@@ -8,94 +8,118 @@
 // where D0 = dS/dmu_x (raw moments held fixed), D1 = dS/dE[x^2] and
 // D2 = dS/dE[xy] are per-pixel maps and * is the same zero-padded blur.
 //
-//   ssim_fwd : per 16x16 tile and channel: halo tile of x and y in shared
-//              memory, horizontal then vertical blur of the five moments,
-//              SSIM, D0..D2 written to the workspace maps, per-CTA sums of
-//              |x - y| and S.
-//   ssim_bwd : per 16x16 tile and channel: halo tile of D0..D2, blur, and
+//   ssim_fwd : per 32x16 block of pixels and channel: the block with its
+//              5-pixel halo for x and y in shared memory, horizontal then
+//              vertical blur of the five moments, SSIM, D0..D2 written to the
+//              workspace maps, per-CTA sums of |x - y| and S.
+//   ssim_bwd : per 32x16 block and channel: halo block of D0..D2, blur, and
 //              dL/dx = s ((1 - lambda) sign(x - y) - lambda dS/dx) with
 //              s = 1 / (3 H W n_views).
 //   loss_reduce : one CTA sums the per-CTA partials per view in a fixed
 //              order (double precision) and writes the scalar loss.
+// The window weights are computed once on the host (double precision,
+// rounded to float) and passed by value with the CTA grid of the views.
+#include <cmath>
+
 #include "fgs_common.cuh"
 
 namespace fgs {
 
 constexpr int kHalo = 5;
-constexpr int kSpan = kTile + 2 * kHalo;  // 26
+constexpr int kLTW = 32, kLTH = 16;         // output block of one CTA
+constexpr int kSpanX = kLTW + 2 * kHalo;    // 42
+constexpr int kSpanY = kLTH + 2 * kHalo;    // 26
+constexpr int kLX = 32, kLY = 8;            // CTA shape (threadIdx.x, threadIdx.y)
 
-// Normalised 11-tap Gaussian window (sigma 1.5) into shared memory; every
-// CTA computes it, so no upload or synchronisation is needed.
-__device__ __forceinline__ void load_window(float* w)
+// The CTA grid over all views and the window, passed by value.
+struct LossGrid {
+    int32_t cta_off[FGS_MAX_VIEWS + 1];  // first CTA of each view
+    int32_t ctas_x[FGS_MAX_VIEWS];       // CTAs per block row of each view
+    float w[11];                         // normalised Gaussian window, sigma 1.5
+};
+
+__device__ __forceinline__ int view_of_cta(const LossGrid& g, int nv, int b)
 {
-    if (threadIdx.x < 11) {
-        float s = 0.f;
-        for (int i = 0; i < 11; ++i) s += expf(-(float)((i - 5) * (i - 5)) / 4.5f);
-        const int d = (int)threadIdx.x - 5;
-        w[threadIdx.x] = expf(-(float)(d * d) / 4.5f) / s;
-    }
+    int v = 0;
+    while (v + 1 < nv && b >= g.cta_off[v + 1]) ++v;
+    return v;
 }
 
-__global__ void __launch_bounds__(256)
-ssim_fwd_kernel(ViewTable vt, const float* __restrict__ images, const float* __restrict__ targets,
-                float* __restrict__ maps, double* __restrict__ partials)
+// Sums a and b over the CTA (256 threads) into red; valid in thread 0.
+__device__ __forceinline__ void cta_sum2(float& a, float& b, float (*red)[kLY], int tid)
 {
-    __shared__ float sx[kSpan][kSpan + 1], sy[kSpan][kSpan + 1];
-    __shared__ float hs[5][kSpan][kTile + 1];
-    __shared__ float red[2][8];
-    __shared__ float c_win[11];
-    load_window(c_win);
-    const int tile = blockIdx.x;
-    const int v = view_of_tile(vt, tile);
-    const int lt = tile - vt.tile_off[v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = a;
+        red[1][tid >> 5] = b;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kLX * kLY)
+ssim_fwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
+                const float* __restrict__ targets, float* __restrict__ maps,
+                double* __restrict__ partials)
+{
+    __shared__ float sx[kSpanY][kSpanX + 1], sy[kSpanY][kSpanX + 1];
+    __shared__ float hs[5][kSpanY][kLTW + 1];
+    __shared__ float red[2][kLY];
+    const int b = blockIdx.x;
+    const int v = view_of_cta(lg, vt.n_views, b);
+    const int lb = b - lg.cta_off[v];
     const int W = vt.width[v], H = vt.height[v];
-    const int x0 = (lt % vt.tiles_x[v]) * kTile, y0 = (lt / vt.tiles_x[v]) * kTile;
+    const int x0 = (lb % lg.ctas_x[v]) * kLTW, y0 = (lb / lg.ctas_x[v]) * kLTH;
     const int64_t P = (int64_t)W * H;
     const int64_t ptot = vt.total_pixels;
-    const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
-    const int px = x0 + tx, py = y0 + ty;
-    const bool inside = px < W && py < H;
-    const int64_t pix = (int64_t)py * W + px;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kLX + tx;
+    const int px = x0 + tx;
     float l1 = 0.f, ssum = 0.f;
     for (int ch = 0; ch < 3; ++ch) {
         const float* X = images + 3 * vt.pix_off[v] + ch * P;
         const float* Yt = targets + 3 * vt.pix_off[v] + ch * P;
         __syncthreads();
-        for (int e = threadIdx.x; e < kSpan * kSpan; e += 256) {
-            const int r = e / kSpan, c = e % kSpan;
-            const int gx = x0 - kHalo + c, gy = y0 - kHalo + r;
-            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            sx[r][c] = in ? X[(int64_t)gy * W + gx] : 0.f;
-            sy[r][c] = in ? Yt[(int64_t)gy * W + gx] : 0.f;
+        for (int r = ty; r < kSpanY; r += kLY) {
+            const int gy = y0 - kHalo + r;
+            for (int c = tx; c < kSpanX; c += kLX) {
+                const int gx = x0 - kHalo + c;
+                const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+                sx[r][c] = in ? X[(int64_t)gy * W + gx] : 0.f;
+                sy[r][c] = in ? Yt[(int64_t)gy * W + gx] : 0.f;
+            }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < kSpan * kTile; e += 256) {
-            const int r = e / kTile, c = e % kTile;
-            float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+        for (int r = ty; r < kSpanY; r += kLY) {
+            float a = 0.f, bb_ = 0.f, aa = 0.f, yy = 0.f, ab = 0.f;
 #pragma unroll
             for (int k = 0; k < 11; ++k) {
-                const float w = c_win[k];
-                const float xv = sx[r][c + k], yv = sy[r][c + k];
+                const float w = lg.w[k];
+                const float xv = sx[r][tx + k], yv = sy[r][tx + k];
                 a += w * xv;
-                b += w * yv;
+                bb_ += w * yv;
                 aa += w * xv * xv;
-                bb += w * yv * yv;
+                yy += w * yv * yv;
                 ab += w * xv * yv;
             }
-            hs[0][r][c] = a; hs[1][r][c] = b; hs[2][r][c] = aa; hs[3][r][c] = bb; hs[4][r][c] = ab;
+            hs[0][r][tx] = a; hs[1][r][tx] = bb_; hs[2][r][tx] = aa; hs[3][r][tx] = yy; hs[4][r][tx] = ab;
         }
         __syncthreads();
-        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+        for (int oy = ty; oy < kLTH; oy += kLY) {
+            const int py = y0 + oy;
+            if (!(px < W && py < H)) continue;
+            float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = c_win[k];
-            mx += w * hs[0][ty + k][tx];
-            my += w * hs[1][ty + k][tx];
-            exx += w * hs[2][ty + k][tx];
-            eyy += w * hs[3][ty + k][tx];
-            exy += w * hs[4][ty + k][tx];
-        }
-        if (inside) {
+            for (int k = 0; k < 11; ++k) {
+                const float w = lg.w[k];
+                mx += w * hs[0][oy + k][tx];
+                my += w * hs[1][oy + k][tx];
+                exx += w * hs[2][oy + k][tx];
+                eyy += w * hs[3][oy + k][tx];
+                exy += w * hs[4][oy + k][tx];
+            }
             const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
             const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
             const float n1 = 2.f * mx * my + C1, n2 = 2.f * cxy + C2;
@@ -104,89 +128,80 @@ ssim_fwd_kernel(ViewTable vt, const float* __restrict__ images, const float* __r
             const float dS_dmx = S * (2.f * my / n1 - 2.f * mx / d1);
             const float dS_dvx = -S / d2;
             const float dS_dcxy = 2.f * S / n2;
-            const int64_t gp = vt.pix_off[v] + pix;
+            const int64_t gp = vt.pix_off[v] + (int64_t)py * W + px;
             maps[(int64_t)(3 * ch + 0) * ptot + gp] = dS_dmx - 2.f * mx * dS_dvx - my * dS_dcxy;
             maps[(int64_t)(3 * ch + 1) * ptot + gp] = dS_dvx;
             maps[(int64_t)(3 * ch + 2) * ptot + gp] = dS_dcxy;
             ssum += S;
-            l1 += fabsf(sx[ty + kHalo][tx + kHalo] - sy[ty + kHalo][tx + kHalo]);
+            l1 += fabsf(sx[oy + kHalo][tx + kHalo] - sy[oy + kHalo][tx + kHalo]);
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        l1 += __shfl_xor_sync(0xffffffffu, l1, o);
-        ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = l1;
-        red[1][threadIdx.x >> 5] = ssum;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < 8; ++w) {
+    cta_sum2(l1, ssum, red, tid);
+    if (tid == 0) {
+        double a = 0.0, c = 0.0;
+        for (int w = 0; w < kLY; ++w) {
             a += red[0][w];
-            b += red[1][w];
+            c += red[1][w];
         }
-        partials[2 * tile] = a;
-        partials[2 * tile + 1] = b;
+        partials[2 * b] = a;
+        partials[2 * b + 1] = c;
     }
 }
 
-__global__ void __launch_bounds__(256)
-ssim_bwd_kernel(ViewTable vt, const float* __restrict__ images, const float* __restrict__ targets,
-                const float* __restrict__ maps, float lambda, float* __restrict__ dL)
+__global__ void __launch_bounds__(kLX * kLY)
+ssim_bwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
+                const float* __restrict__ targets, const float* __restrict__ maps, float lambda,
+                float* __restrict__ dL)
 {
-    __shared__ float sm[3][kSpan][kSpan + 1];
-    __shared__ float hs[3][kSpan][kTile + 1];
-    __shared__ float c_win[11];
-    load_window(c_win);
-    const int tile = blockIdx.x;
-    const int v = view_of_tile(vt, tile);
-    const int lt = tile - vt.tile_off[v];
+    __shared__ float sm[3][kSpanY][kSpanX + 1];
+    __shared__ float hs[3][kSpanY][kLTW + 1];
+    const int b = blockIdx.x;
+    const int v = view_of_cta(lg, vt.n_views, b);
+    const int lb = b - lg.cta_off[v];
     const int W = vt.width[v], H = vt.height[v];
-    const int x0 = (lt % vt.tiles_x[v]) * kTile, y0 = (lt / vt.tiles_x[v]) * kTile;
+    const int x0 = (lb % lg.ctas_x[v]) * kLTW, y0 = (lb / lg.ctas_x[v]) * kLTH;
     const int64_t P = (int64_t)W * H;
     const int64_t ptot = vt.total_pixels;
-    const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
-    const int px = x0 + tx, py = y0 + ty;
-    const bool inside = px < W && py < H;
-    const int64_t pix = (int64_t)py * W + px;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int px = x0 + tx;
     const float scale = 1.0f / (3.0f * (float)P * (float)vt.n_views);
     for (int ch = 0; ch < 3; ++ch) {
         __syncthreads();
-        for (int e = threadIdx.x; e < kSpan * kSpan; e += 256) {
-            const int r = e / kSpan, c = e % kSpan;
-            const int gx = x0 - kHalo + c, gy = y0 - kHalo + r;
-            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            const int64_t gp = vt.pix_off[v] + (int64_t)gy * W + gx;
+        for (int r = ty; r < kSpanY; r += kLY) {
+            const int gy = y0 - kHalo + r;
+            for (int c = tx; c < kSpanX; c += kLX) {
+                const int gx = x0 - kHalo + c;
+                const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+                const int64_t gp = vt.pix_off[v] + (int64_t)gy * W + gx;
 #pragma unroll
-            for (int m = 0; m < 3; ++m) sm[m][r][c] = in ? maps[(int64_t)(3 * ch + m) * ptot + gp] : 0.f;
+                for (int m = 0; m < 3; ++m) sm[m][r][c] = in ? maps[(int64_t)(3 * ch + m) * ptot + gp] : 0.f;
+            }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < kSpan * kTile; e += 256) {
-            const int r = e / kTile, c = e % kTile;
-            float a = 0.f, b = 0.f, d = 0.f;
+        for (int r = ty; r < kSpanY; r += kLY) {
+            float a = 0.f, bb_ = 0.f, d = 0.f;
 #pragma unroll
             for (int k = 0; k < 11; ++k) {
-                const float w = c_win[k];
-                a += w * sm[0][r][c + k];
-                b += w * sm[1][r][c + k];
-                d += w * sm[2][r][c + k];
+                const float w = lg.w[k];
+                a += w * sm[0][r][tx + k];
+                bb_ += w * sm[1][r][tx + k];
+                d += w * sm[2][r][tx + k];
             }
-            hs[0][r][c] = a; hs[1][r][c] = b; hs[2][r][c] = d;
+            hs[0][r][tx] = a; hs[1][r][tx] = bb_; hs[2][r][tx] = d;
         }
         __syncthreads();
-        if (inside) {
+        for (int oy = ty; oy < kLTH; oy += kLY) {
+            const int py = y0 + oy;
+            if (!(px < W && py < H)) continue;
             float b0 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll
             for (int k = 0; k < 11; ++k) {
-                const float w = c_win[k];
-                b0 += w * hs[0][ty + k][tx];
-                b1 += w * hs[1][ty + k][tx];
-                b2 += w * hs[2][ty + k][tx];
+                const float w = lg.w[k];
+                b0 += w * hs[0][oy + k][tx];
+                b1 += w * hs[1][oy + k][tx];
+                b2 += w * hs[2][oy + k][tx];
             }
-            const int64_t off = 3 * vt.pix_off[v] + ch * P + pix;
+            const int64_t off = 3 * vt.pix_off[v] + ch * P + (int64_t)py * W + px;
             const float x = images[off], y = targets[off];
             const float dssim = b0 + 2.f * x * b1 + y * b2;
             const float diff = x - y;
@@ -197,14 +212,14 @@ ssim_bwd_kernel(ViewTable vt, const float* __restrict__ images, const float* __r
 }
 
 __global__ void __launch_bounds__(256)
-loss_reduce_kernel(ViewTable vt, const double* __restrict__ partials, float lambda,
+loss_reduce_kernel(ViewTable vt, LossGrid lg, const double* __restrict__ partials, float lambda,
                    float* __restrict__ loss_out)
 {
     __shared__ double red[2][256];
     double total = 0.0;
     for (int v = 0; v < vt.n_views; ++v) {
         double a = 0.0, b = 0.0;
-        for (int t = vt.tile_off[v] + threadIdx.x; t < vt.tile_off[v + 1]; t += 256) {
+        for (int t = lg.cta_off[v] + threadIdx.x; t < lg.cta_off[v + 1]; t += 256) {
             a += partials[2 * t];
             b += partials[2 * t + 1];
         }
@@ -225,15 +240,35 @@ loss_reduce_kernel(ViewTable vt, const double* __restrict__ partials, float lamb
     if (threadIdx.x == 0) loss_out[0] = (float)(total / vt.n_views);
 }
 
+static LossGrid loss_grid(const ViewTable& vt)
+{
+    LossGrid g;
+    int32_t off = 0;
+    for (int v = 0; v < vt.n_views; ++v) {
+        g.cta_off[v] = off;
+        g.ctas_x[v] = (vt.width[v] + kLTW - 1) / kLTW;
+        off += g.ctas_x[v] * ((vt.height[v] + kLTH - 1) / kLTH);
+    }
+    for (int v = vt.n_views; v <= FGS_MAX_VIEWS; ++v) g.cta_off[v] = off;
+    for (int v = vt.n_views; v < FGS_MAX_VIEWS; ++v) g.ctas_x[v] = 1;
+    double s = 0.0;
+    for (int i = 0; i < 11; ++i) s += std::exp(-(double)((i - 5) * (i - 5)) / 4.5);
+    for (int i = 0; i < 11; ++i) g.w[i] = (float)(std::exp(-(double)((i - 5) * (i - 5)) / 4.5) / s);
+    return g;
+}
+
 cudaError_t launch_loss(const ViewTable& vt, const float* images, const float* targets, float lambda,
                         float* maps, double* partials, float* loss_out, float* dL, cudaStream_t st)
 {
     if (vt.total_tiles <= 0) return cudaSuccess;
-    ssim_fwd_kernel<<<vt.total_tiles, 256, 0, st>>>(vt, images, targets, maps, partials);
+    const LossGrid lg = loss_grid(vt);
+    const int ctas = lg.cta_off[vt.n_views];
+    const dim3 block(kLX, kLY);
+    ssim_fwd_kernel<<<ctas, block, 0, st>>>(vt, lg, images, targets, maps, partials);
     profile_mark(st, "loss_ssim_fwd");
-    ssim_bwd_kernel<<<vt.total_tiles, 256, 0, st>>>(vt, images, targets, maps, lambda, dL);
+    ssim_bwd_kernel<<<ctas, block, 0, st>>>(vt, lg, images, targets, maps, lambda, dL);
     profile_mark(st, "loss_ssim_bwd");
-    loss_reduce_kernel<<<1, 256, 0, st>>>(vt, partials, lambda, loss_out);
+    loss_reduce_kernel<<<1, 256, 0, st>>>(vt, lg, partials, lambda, loss_out);
     profile_mark(st, "loss_reduce");
     return cudaGetLastError();
 }
