@@ -104,7 +104,7 @@ enum fgs_ws_slot {
                            32 tiles the uint32 mask of tiles kept by culling (bit t = row-major
                            tile t), then an unused uint32 */
     FGS_WS_LOCAL_OFF,   /* uint32 [n_views*n]: CTA-local exclusive prefix of the rendered flags */
-    FGS_WS_BLOCK_SUM,   /* uint32 [n_views*ceil(n/256)+1]: prefix of the CTA totals */
+    FGS_WS_BLOCK_SUM,   /* uint32 [n_views*ceil(n/128)+1]: prefix of the CTA totals */
     FGS_WS_KEYS,        /* uint32 [k_max]: global tile id of each instance (tile sort keys) */
     FGS_WS_VALS,        /* uint32 [k_max]: Gaussian index */
     FGS_WS_KEYS_ALT,    /* uint32 [k_max]: sort ping-pong buffer */
@@ -127,7 +127,7 @@ enum fgs_ws_slot {
     FGS_WS_DEPTH_KEYS_ALT, /* uint32 [n_views*n]: depth-sort ping-pong buffers */
     FGS_WS_DEPTH_VALS_ALT,
     FGS_WS_SORTED_OFF,  /* uint32 [n_views*n]: instance offsets in depth order (CTA-local) */
-    FGS_WS_SORTED_BLOCK, /* uint32 [ceil(n_views*n/1024)+1]: prefix of those CTA totals */
+    FGS_WS_SORTED_BLOCK, /* uint32 [ceil(n_views*n/512)+1]: prefix of those CTA totals */
     FGS_WS_NUM_SLOTS
 };
 

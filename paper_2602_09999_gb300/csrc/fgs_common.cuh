@@ -24,7 +24,7 @@ constexpr float kTMin = 1e-4f;
 constexpr float kQNormMin = 1e-4f;
 constexpr float kDetMin = 1e-6f;
 constexpr float kDilation = 0.3f;
-constexpr int kPreBlock = 256;  // Gaussians per preprocess CTA (scan granularity)
+constexpr int kPreBlock = 128;  // Gaussians per preprocess CTA (scan granularity)
 
 // Per-view sizes and prefix offsets, passed to kernels by value.  Sizes are
 // fixed for the lifetime of a captured graph; poses come from device memory.
