@@ -73,7 +73,7 @@ class _Margins(ctypes.Structure):
     _fields_ = [("rel", ctypes.c_double), ("q_rel", ctypes.c_double),
                 ("pos_rel", ctypes.c_double), ("px", ctypes.c_double),
                 ("t_rel", ctypes.c_double), ("depth_rel", ctypes.c_double),
-                ("tile_culling", ctypes.c_int32)]
+                ("value_tol", ctypes.c_double), ("tile_culling", ctypes.c_int32)]
 
 
 @dataclass
@@ -85,20 +85,25 @@ class Margins:
     q_rel: rounding of a quadratic form relative to the sum of its |terms|;
     pos_rel: error of mu2D relative to max(1, |mu2D|) in pixels, which moves
     the quadratic form by about 2 |C d| pos_err; px: rectangle edges;
-    t_rel: transmittance stop test; depth_rel: depth ties."""
+    t_rel: transmittance stop test; depth_rel: depth ties; value_tol: a
+    pixel is flagged only where taking such a decision the other way can move
+    its value by more than this (blend or skip an entry: alpha T (c - R), R
+    the normalised colour behind it; swap tied entries: T a1 a2 (c1 - c2);
+    0 flags every such decision)."""
     rel: float = 0.0
     q_rel: float = 0.0
     pos_rel: float = 0.0
     px: float = 0.0
     t_rel: float = 0.0
     depth_rel: float = 0.0
+    value_tol: float = 0.0
     tile_culling: int = 1
 
 
 # margins used when the oracle is compared with a float32 implementation:
 # roughly 10-30 float32 ulps of each quantity the decision depends on
 FP32_MARGINS = Margins(rel=2e-6, q_rel=1e-6, pos_rel=5e-7, px=2e-3, t_rel=1e-4,
-                       depth_rel=2e-6)
+                       depth_rel=2e-6, value_tol=5e-5)
 NO_MARGINS = Margins()
 
 
@@ -135,7 +140,8 @@ def _cam_struct(cam) -> _Camera:
 
 
 def _mg_struct(m: Margins) -> _Margins:
-    return _Margins(m.rel, m.q_rel, m.pos_rel, m.px, m.t_rel, m.depth_rel, int(m.tile_culling))
+    return _Margins(m.rel, m.q_rel, m.pos_rel, m.px, m.t_rel, m.depth_rel, m.value_tol,
+                    int(m.tile_culling))
 
 
 def _f64(a):
@@ -233,13 +239,15 @@ def blend_forward(cam, pre, lists, bg=(0.0, 0.0, 0.0), margins: Margins = NO_MAR
     bg = np.asarray(bg, np.float64)
     out = dict(image=np.zeros((3, H, W)), T_final=np.zeros((H, W)),
                n_contrib=np.zeros((H, W), np.int32), last_gid=np.zeros((H, W), np.int32),
-               ambiguous=np.zeros((H, W), np.uint8))
+               ambiguous=np.zeros((H, W), np.uint8), hard=np.zeros((H, W), np.uint8),
+               allowance=np.zeros((H, W)))
     m = _mg_struct(margins)
     lib.orc_blend_forward(ctypes.c_int32(W), ctypes.c_int32(H), _p(lists["ranges"]),
                           _p(lists["gid"]), _p(lists["flags"]), _p(pre["xy"]), _p(pre["conic"]),
                           _p(pre["opacity"]), _p(pre["rgb"]), _p(pre["depth"]), _p(bg),
                           ctypes.byref(m), _p(out["image"]), _p(out["T_final"]),
-                          _p(out["n_contrib"]), _p(out["last_gid"]), _p(out["ambiguous"]))
+                          _p(out["n_contrib"]), _p(out["last_gid"]), _p(out["ambiguous"]),
+                          _p(out["hard"]), _p(out["allowance"]))
     return out
 
 

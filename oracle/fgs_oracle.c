@@ -56,6 +56,8 @@ typedef struct {
     double px;         /* absolute margin (pixels) for rectangle edges */
     double t_rel;      /* relative margin for the transmittance stop test */
     double depth_rel;  /* relative depth difference treated as a tie */
+    double value_tol;  /* a pixel is flagged only if taking such a decision the other way
+                          can move its value by more than this (0: any such decision) */
     int32_t tile_culling; /* 1: per-tile culling (Sec. 3.2); 0: whole rectangle */
 } orc_margins;
 
@@ -547,24 +549,56 @@ int orc_emit_instances(const orc_camera *cam, int64_t n, int sh_degree, const do
  * min(0.99, o G), skip alpha < 1/255, stop before blending an entry whose
  * T (1 - alpha) would fall below 1e-4.  Returns the number of kept entries
  * up to and including the last blended one, its list index, and flags the
- * pixel if any decision lies within the margins. */
+ * pixel where a decision within the margins can move its value by more
+ * than mg->value_tol:
+ *  - whether entry j is blended (a culling candidate, the alpha >= 1/255
+ *    test, a zero exponent): blending it or not changes the pixel by
+ *    alpha T_j (c_j - R_j), R_j the colour behind it normalised by the
+ *    transmittance behind it, known once the walk is done (later decisions
+ *    held fixed);
+ *  - the order of two blended entries with tied depths: swapping adjacent
+ *    entries changes the pixel by T alpha_1 alpha_2 (c_1 - c_2);
+ *  - the stop test: always flagged.
+ * The 0.99 clamp leaves the value continuous; it is flagged only when every
+ * decision is (value_tol = 0), for scenes that must avoid kinks.  More than
+ * ORC_MAX_EVENTS blend decisions in one pixel flag it as well.  `hard` marks
+ * the flags whose effect is not bounded (stop test, overflow); `allowance`
+ * sums the bounded effects. */
+#define ORC_MAX_EVENTS 64
 typedef struct {
     double C[3];
     double T;
     int64_t n_contrib;   /* position among KEEP entries, 1-based; 0 if none */
     int64_t last;        /* list index of the last blended entry, -1 if none */
-    int amb;
+    int amb;             /* a decision within the margins moves the value by > value_tol */
+    int hard;            /* a decision whose effect is not bounded (stop test, overflow) */
+    double allowance;    /* sum of the bounded effects of all such decisions */
 } orc_pixel;
+
+typedef struct {
+    double T0, alpha, c[3], C_after[3], T_after;
+} orc_event;
+
+static double max_abs_diff3(const double *a, const double *b)
+{
+    double m = 0.0;
+    for (int ch = 0; ch < 3; ++ch) m = fmax(m, fabs(a[ch] - b[ch]));
+    return m;
+}
 
 static void pixel_walk(double px, double py, int64_t start, int64_t end, const int32_t *list_gid,
                        const uint8_t *list_flags, const double *xy, const double *conic,
-                       const double *opac, const double *rgb, const double *depth,
+                       const double *opac, const double *rgb, const double *depth, const double *bg,
                        const orc_margins *mg, orc_pixel *out)
 {
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};
     int64_t pos = 0, n = 0, last = -1;
-    int amb = 0;
-    double prev_depth = -1.0;
+    int amb = 0, hard = 0;
+    double allowance = 0.0;
+    orc_event ev[ORC_MAX_EVENTS];
+    int nev = 0;
+    double prev_depth = -1.0, prev_T = 0.0, prev_alpha = 0.0;
+    const double *prev_c = NULL;
     int have_prev = 0;
     for (int64_t j = start; j < end; ++j) {
         const int32_t g = list_gid[j];
@@ -587,45 +621,83 @@ static void pixel_walk(double px, double py, int64_t start, int64_t end, const i
                                ? form_error_scale(conic[3 * g], conic[3 * g + 1], conic[3 * g + 2], dx, dy)
                                : 0.0;
         const double slack = mg->rel + 0.5 * mg->q_rel * mag + pos_err * grad;
-        if (!keep || (f & ORC_IMARGINAL)) {
-            /* a candidate float32 may decide differently: flag the pixel
-             * when it would contribute here */
-            if (oG >= ORC_ALPHA_MIN * (1.0 - slack)) amb = 1;
-            if (!keep) continue;
+        /* is whether this entry is blended a decision float32 may take the other way? */
+        int uncertain = 0;
+        if (!keep || (f & ORC_IMARGINAL)) uncertain |= oG >= ORC_ALPHA_MIN * (1.0 - slack);
+        if (keep) {
+            uncertain |= fabs(power) <= 0.5 * mg->q_rel * mag + (mg->q_rel > 0.0 ? 1e-12 : 0.0);
+            uncertain |= fabs(oG - ORC_ALPHA_MIN) <= ORC_ALPHA_MIN * slack;
+            /* the clamp: no effect on the value, a kink for derivatives; flagged
+             * only when every decision is (value_tol = 0) */
+            if (mg->value_tol <= 0.0 && fabs(oG - ORC_ALPHA_MAX) <= ORC_ALPHA_MAX * slack) amb = 1;
         }
-        if (fabs(power) <= 0.5 * mg->q_rel * mag + (mg->q_rel > 0.0 ? 1e-12 : 0.0)) amb = 1;
-        if (power > 0.0) continue;
-        if (fabs(oG - ORC_ALPHA_MIN) <= ORC_ALPHA_MIN * slack) amb = 1;
-        if (fabs(oG - ORC_ALPHA_MAX) <= ORC_ALPHA_MAX * slack) amb = 1;
         const double alpha = oG < ORC_ALPHA_MAX ? oG : ORC_ALPHA_MAX;
-        if (alpha < ORC_ALPHA_MIN) continue;
-        if (have_prev && fabs(depth[g] - prev_depth) <= mg->depth_rel * fabs(depth[g])) amb = 1;
-        prev_depth = depth[g];
-        have_prev = 1;
-        const double test = T * (1.0 - alpha);
-        if (fabs(test - ORC_T_MIN) <= ORC_T_MIN * mg->t_rel) amb = 1;
-        if (test < ORC_T_MIN) break;
+        const int blend = keep && power <= 0.0 && alpha >= ORC_ALPHA_MIN;
+        double test = T;
+        if (blend) {
+            if (have_prev && fabs(depth[g] - prev_depth) <= mg->depth_rel * fabs(depth[g])) {
+                const double effect = prev_T * prev_alpha * alpha * max_abs_diff3(prev_c, rgb + 3 * g);
+                allowance += effect;
+                if (effect > mg->value_tol || mg->value_tol <= 0.0) amb = 1;
+            }
+            test = T * (1.0 - alpha);
+            if (fabs(test - ORC_T_MIN) <= ORC_T_MIN * mg->t_rel) amb = hard = 1;
+            if (test < ORC_T_MIN) break;
+        }
+        if (uncertain) {
+            if (nev == ORC_MAX_EVENTS) {
+                amb = hard = 1;
+            } else {
+                orc_event *e = &ev[nev++];
+                e->T0 = T;
+                e->alpha = alpha > ORC_ALPHA_MIN ? alpha : ORC_ALPHA_MIN;
+                for (int ch = 0; ch < 3; ++ch) {
+                    e->c[ch] = rgb[3 * g + ch];
+                    e->C_after[ch] = C[ch] + (blend ? alpha * T * rgb[3 * g + ch] : 0.0);
+                }
+                e->T_after = blend ? test : T;
+            }
+        }
+        if (!blend) continue;
         for (int ch = 0; ch < 3; ++ch) C[ch] += alpha * T * rgb[3 * g + ch];
+        prev_depth = depth[g];
+        prev_T = T;
+        prev_alpha = alpha;
+        prev_c = rgb + 3 * g;
+        have_prev = 1;
         T = test;
         n = pos;
         last = j;
+    }
+    /* effect of taking each uncertain blend decision the other way */
+    for (int k = 0; k < nev; ++k) {
+        const orc_event *e = &ev[k];
+        double R[3];
+        for (int ch = 0; ch < 3; ++ch) R[ch] = (C[ch] + T * bg[ch] - e->C_after[ch]) / e->T_after;
+        const double effect = e->alpha * e->T0 * max_abs_diff3(e->c, R);
+        allowance += effect;
+        if (effect > mg->value_tol || mg->value_tol <= 0.0) amb = 1;
     }
     for (int ch = 0; ch < 3; ++ch) out->C[ch] = C[ch];
     out->T = T;
     out->n_contrib = n;
     out->last = last;
     out->amb = amb;
+    out->hard = hard;
+    out->allowance = allowance;
 }
 
 /* Tile-based forward.  ranges[2*t], ranges[2*t+1] delimit tile t's entries
  * in list_gid/list_flags (sorted by depth, then Gaussian id).
  * Outputs: image[3,H,W] = C + T bg, T_final[H,W], n_contrib[H,W],
- * last_gid[H,W] (-1 if none), ambiguous[H,W]. */
+ * last_gid[H,W] (-1 if none), ambiguous[H,W], hard[H,W] and allowance[H,W]
+ * (see pixel_walk). */
 int orc_blend_forward(int32_t width, int32_t height, const int64_t *ranges,
                       const int32_t *list_gid, const uint8_t *list_flags, const double *xy,
                       const double *conic, const double *opac, const double *rgb,
                       const double *depth, const double *bg, const orc_margins *mg, double *image,
-                      double *T_final, int32_t *n_contrib, int32_t *last_gid, uint8_t *ambiguous)
+                      double *T_final, int32_t *n_contrib, int32_t *last_gid, uint8_t *ambiguous,
+                      uint8_t *hard, double *allowance)
 {
     const int tiles_x = (width + ORC_TILE - 1) / ORC_TILE;
     const int64_t npix = (int64_t)width * height;
@@ -635,12 +707,14 @@ int orc_blend_forward(int32_t width, int32_t height, const int64_t *ranges,
         const int t = (v / ORC_TILE) * tiles_x + (u / ORC_TILE);
         orc_pixel r;
         pixel_walk(u + 0.5, v + 0.5, ranges[2 * t], ranges[2 * t + 1], list_gid, list_flags, xy,
-                   conic, opac, rgb, depth, mg, &r);
+                   conic, opac, rgb, depth, bg, mg, &r);
         for (int ch = 0; ch < 3; ++ch) image[ch * npix + p] = r.C[ch] + r.T * bg[ch];
         T_final[p] = r.T;
         n_contrib[p] = (int32_t)r.n_contrib;
         last_gid[p] = r.last >= 0 ? list_gid[r.last] : -1;
         ambiguous[p] = (uint8_t)r.amb;
+        hard[p] = (uint8_t)r.hard;
+        allowance[p] = r.allowance;
     }
     return 0;
 }
@@ -653,12 +727,12 @@ int orc_blend_brute(int32_t width, int32_t height, int64_t count, const int32_t 
                     int32_t *last_gid)
 {
     const int64_t npix = (int64_t)width * height;
-    const orc_margins none = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1};
+    const orc_margins none = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1};
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t p = 0; p < npix; ++p) {
         const int u = (int)(p % width), v = (int)(p / width);
         orc_pixel r;
-        pixel_walk(u + 0.5, v + 0.5, 0, count, order, NULL, xy, conic, opac, rgb, depth, &none, &r);
+        pixel_walk(u + 0.5, v + 0.5, 0, count, order, NULL, xy, conic, opac, rgb, depth, bg, &none, &r);
         for (int ch = 0; ch < 3; ++ch) image[ch * npix + p] = r.C[ch] + r.T * bg[ch];
         T_final[p] = r.T;
         last_gid[p] = r.last >= 0 ? order[r.last] : -1;
@@ -803,7 +877,7 @@ int orc_preprocess_backward(const orc_camera *cam, int64_t n, int sh_degree, con
                             double *g_log_scales, double *g_quats, double *g_opacity,
                             double *g_sh_dc, double *g_sh_rest)
 {
-    const orc_margins none = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1};
+    const orc_margins none = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1};
     const double *R = cam->R;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
