@@ -218,6 +218,15 @@ def algorithmic_bytes(label, n, views, instances, pixels, sh_bytes, moment_bytes
 BLEND_FLOPS = {"blend_fwd": (12, 9), "blend_bwd": (12, 50)}
 
 
+# DRAM bytes per launch measured with ncu at the default workload (3M
+# Gaussians, one 1237x822 view; profiles/dram_outdoor_3M_1237x822.md), for
+# the roofline's "traffic" field.  Reported only for that workload and
+# launch configuration; a change to one of these kernels must refresh or drop
+# its entry.
+PROFILED_DRAM_BYTES = {"preprocess_bwd_adam": 4.643e9}
+PROFILED_WORKLOAD = (3_000_000, 1237, 822)
+
+
 def fp32_peak_tflops(sm_count, sm_mhz):
     """128 FP32 lanes per SM, one FMA (2 ops) per lane per clock."""
     return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -398,9 +407,12 @@ def run_ours(args, dist):
             pass
         elif alg is not None:
             achieved = alg / (avg_ms / 1000.0) / 1e9
+            traffic = None
+            if (n, W, H) == PROFILED_WORKLOAD and dom in PROFILED_DRAM_BYTES:
+                traffic = PROFILED_DRAM_BYTES[dom]
             roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
                         "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                        "traffic": None, "peak_source": peak_src,
+                        "traffic": traffic, "peak_source": peak_src,
                         "avg_launch_ms": round(avg_ms, 5),
                         "algorithmic_bytes_per_launch": int(alg)}
         else:

@@ -3,6 +3,7 @@ same seeded inputs: per-Gaussian screen state, tile lists (bit-exact after
 removing decisions float32 may take either way), images (max abs 2e-4
 outside ambiguous pixels), loss, gradients (relative L2 1e-3 per tensor),
 Adam and the full step, single and batched uneven views."""
+import dataclasses
 import math
 
 import numpy as np
@@ -13,8 +14,8 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 from gpu_util import (GRAD_REL_L2, IMAGE_TOL, ambiguity_masks, compare_lists,  # noqa: E402
-                      gpu_forward, gpu_grads, grad_errors, ill_conditioned, oracle_forward,
-                      oracle_grads, rel_l2)
+                      gpu_forward, gpu_grads, grad_errors, ill_conditioned, image_check,
+                      oracle_forward, oracle_grads, rel_l2)
 from paper_2602_09999_gb300 import binding as B  # noqa: E402
 from paper_2602_09999_gb300 import scenes  # noqa: E402
 from paper_2602_09999_gb300 import train as T  # noqa: E402
@@ -90,14 +91,19 @@ def test_images_within_tolerance(case):
     _, vals, ranges = [x.cpu().numpy() if hasattr(x, "cpu") else x
                        for x in case["rast"].sorted_lists()]
     pix_off = case["views"].pix_off
-    total_amb = 0
+    total_amb = total_hard = 0
     tile_off = 0
     for v, out in enumerate(case["outs"]):
         img = imgs[v].cpu().numpy()
-        amb = out["ambiguous"].astype(bool)
+        excess, worst, hard, allowed = image_check(img, out)
+        assert excess <= 0.0, (case["name"], excess, worst)
+        total_hard += hard
+        # per-pixel state (T_final, last contributor) changes with any decision
+        # float32 may take the other way: compared where there is none
+        strict = oracle.blend_forward(case["cams"][v], case["pres"][v], case["lists"][v],
+                                      margins=dataclasses.replace(oracle.FP32_MARGINS, value_tol=0.0))
+        amb = strict["ambiguous"].astype(bool)
         total_amb += int(amb.sum())
-        err = np.abs(img - out["image"]).max(axis=0)
-        assert err[~amb].max() <= IMAGE_TOL, (case["name"], float(err[~amb].max()))
         H, W = amb.shape
         Tv = Tg[pix_off[v]:pix_off[v + 1]].reshape(H, W)
         assert np.abs(Tv - out["T_final"])[~amb].max() <= 5e-5
@@ -111,8 +117,9 @@ def test_images_within_tolerance(case):
         np.testing.assert_array_equal(last[~amb], out["last_gid"][~amb])
         tile_off += case["lists"][v]["ranges"].shape[0]
     npx = sum(o["image"].shape[1] * o["image"].shape[2] for o in case["outs"])
-    print(f"{case['name']}: ambiguous pixels {total_amb} / {npx}")
-    assert total_amb <= 0.01 * npx
+    print(f"{case['name']}: unbounded-decision pixels {total_hard}, any-decision {total_amb} / {npx}")
+    assert total_hard <= 1e-2 * npx
+    assert total_amb <= 0.02 * npx
 
 
 def test_forward_is_deterministic(case):
@@ -156,9 +163,10 @@ def test_loss_matches_oracle(sizes, lam):
 
 # --------------------------------------------------------------------------
 # backward: gradients through the C ABI vs the oracle's exact adjoint.
-# dL/dC is zeroed, on both sides, on pixels touched by a decision float32 may
-# take either way (dilated by the SSIM radius); Gaussians whose footprint
-# dwarfs the view (ill-conditioned sums) are left out of the relative L2.
+# dL/dC is zeroed, on both sides, on pixels where decisions float32 may take
+# the other way can move the value beyond the image tolerance
+# (gpu_util.gradient_mask); Gaussians whose footprint dwarfs the view
+# (ill-conditioned sums) are left out of the relative L2.
 # --------------------------------------------------------------------------
 def _check_grads(params, cams, targets, bg=(0.0, 0.0, 0.0), deg=3, lam=0.2):
     masks = ambiguity_masks(cams, params, deg, bg)
