@@ -430,15 +430,17 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
                 // transmittance in front of the entry; 1 - alpha >= 0.01, so the
                 // approximate divide (2 ulp) is in range
                 const float Ti = __fdividef(T[k], 1.0f - f.alpha);
-                const float dalpha = Ti * (g0[k] * (e.rgbo.x - A0[k]) + g1[k] * (e.rgbo.y - A1[k]) +
-                                           g2[k] * (e.rgbo.z - A2[k]));
+                // colour minus colour behind, shared by dL/dalpha and the update of
+                // the colour behind, A <- A + alpha (c - A)
+                const float c0 = e.rgbo.x - A0[k], c1 = e.rgbo.y - A1[k], c2 = e.rgbo.z - A2[k];
+                const float dalpha = Ti * (g0[k] * c0 + g1[k] * c1 + g2[k] * c2);
                 const float wT = f.alpha * Ti;
                 d[6] += wT * g0[k];
                 d[7] += wT * g1[k];
                 d[8] += wT * g2[k];
-                A0[k] = f.alpha * e.rgbo.x + (1.0f - f.alpha) * A0[k];
-                A1[k] = f.alpha * e.rgbo.y + (1.0f - f.alpha) * A1[k];
-                A2[k] = f.alpha * e.rgbo.z + (1.0f - f.alpha) * A2[k];
+                A0[k] += f.alpha * c0;
+                A1[k] += f.alpha * c1;
+                A2[k] += f.alpha * c2;
                 T[k] = Ti;
                 if (!f.clamped) {
                     // power = -q/2 with q = d^T C d; C d = ls u e + lb w e_perp from
@@ -451,10 +453,10 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
                     d[0] += dk * vx;  // dL/dmu = dpow C d
                     d[1] += dk * vy;
                     // dL/dSigma (full symmetric) = -C (dL/dC) C = dpow (C d)(C d)^T / 2
-                    const float hp = 0.5f * dk * kTwoLn2;
-                    d[2] += hp * vx * vx;
-                    d[3] += hp * vx * vy;
-                    d[4] += hp * vy * vy;
+                    const float hx = dpow * (0.5f * kTwoLn2 * kTwoLn2) * vx;
+                    d[2] += hx * vx;
+                    d[3] += hx * vy;
+                    d[4] += dpow * (0.5f * kTwoLn2 * kTwoLn2) * vy * vy;
                 }
             }
             if (!__any_sync(0xffffffffu, any)) continue;
