@@ -29,6 +29,16 @@
  *                                               as in Sec. 3.2 "Rasterization
  *                                               Kernel Fusion")
  *   5 sh_rest     [n,15,3] same dtype as sh_dc (bands 1..3)
+ *   6 velocity    [n,3]  float32   (optional: dynamic Gaussians, below)
+ *   7 t0          [n]    float32   (optional: temporal centre)
+ *
+ * Dynamic (4D) Gaussians (Sec. 3.4, the conditional Gaussian of Yang et al.
+ * in its linear-velocity form): when groups 6 and 7 are set, a view taken at
+ * time t (fgs_camera.time) sees the mean mu + v (t - t0) -- the conditional
+ * mean with Sigma_{1:3,4} Sigma_{4,4}^-1 = v and mu_4 = t0 -- and the
+ * opacity multiplied by the temporal marginal exp(-(t - t0)^2 / (2
+ * sigma_t^2)) (fgs_params.sigma_t); the 3D covariance is used as is.  With
+ * both NULL the Gaussians are static (3D) and time is ignored.
  */
 #ifndef FASTERGS_H
 #define FASTERGS_H
@@ -42,7 +52,7 @@ extern "C" {
 
 #define FGS_TILE 16          /* tile edge in pixels (Sec. 3.1) */
 #define FGS_MAX_VIEWS 16     /* views per batched call */
-#define FGS_NUM_GROUPS 6     /* parameter groups in fgs_params */
+#define FGS_NUM_GROUPS 8     /* parameter groups in fgs_params (6 and 7 optional) */
 
 enum fgs_status {
     FGS_OK = 0,
@@ -71,7 +81,8 @@ enum fgs_dtype { FGS_F32 = 0, FGS_BF16 = 1, FGS_F16 = 2 };
  * intrinsics directly instead of a projection matrix).  Pixel (u, v) is
  * sampled at (u + 0.5, v + 0.5).  near_plane: Gaussians with camera depth
  * <= near_plane are not rendered.  cam_pos: camera centre in world space,
- * used for the SH view direction. */
+ * used for the SH view direction.  time: the view's timestamp, used by
+ * dynamic Gaussians only. */
 typedef struct fgs_camera {
     float R[9];
     float t[3];
@@ -79,15 +90,19 @@ typedef struct fgs_camera {
     int32_t width, height;
     float near_plane;
     float cam_pos[3];
+    float time;
 } fgs_camera;
 
 /* One tensor per parameter group (order above), each with its storage
  * type.  Used for parameters, gradients (always FGS_F32) and the two Adam
- * moments. */
+ * moments.  Groups 6 and 7 are both set or both NULL, and the gradient and
+ * moment structs follow the parameters.  sigma_t: temporal standard
+ * deviation of dynamic Gaussians (> 0 when groups 6 and 7 are set). */
 typedef struct fgs_params {
     int64_t n;
     void *data[FGS_NUM_GROUPS];
     int32_t dtype[FGS_NUM_GROUPS];
+    float sigma_t;
 } fgs_params;
 
 /* Sub-arrays of the caller-allocated workspace (byte offsets from its
@@ -206,9 +221,10 @@ int fgs_loss_l1_dssim(void *ws, const fgs_workspace_layout *layout, const fgs_ca
  * tile back to front from each pixel's last contributor (recovering T by
  * division, Suppl. B.1), reduce per-Gaussian gradients across each warp
  * and CTA before global atomics, then the chain rule of the preprocessing
- * (fused activation gradients, Sec. 3.2).  grads: float32 tensors for all
- * six groups; written for every Gaussian (zero where invisible), summed
- * over the views.  Needs the workspace of the matching forward. */
+ * (fused activation gradients, Sec. 3.2).  grads: float32 tensors for every
+ * group the parameters have (6, or 8 for dynamic Gaussians); written for
+ * every Gaussian (zero where invisible), summed over the views.  Needs the
+ * workspace of the matching forward. */
 int fgs_render_backward(void *ws, const fgs_workspace_layout *layout, const fgs_params *params,
                         int32_t sh_degree, const fgs_camera *cams_host,
                         const fgs_camera *cams_device, const float bg[3],
@@ -219,12 +235,13 @@ int fgs_render_backward(void *ws, const fgs_workspace_layout *layout, const fgs_
  * p -= lr/(1-b1^t) * m / (sqrt(v)/sqrt(1-b2^t) + eps), step t >= 1.
  * As in PyTorch, 1 - b1, 1 - b2 and the bias corrections are formed in
  * double precision and rounded to float once.
- * lr: host float[6] in group order.  Every Gaussian is updated, including
+ * lr: host float[8] in group order (6 and 7 used only when those groups
+ * are set).  Every Gaussian is updated, including
  * those with zero gradient (Sec. 3.3 "Fusing Backward and Optimizer").
  * params groups 4..5 and both moments may be FGS_BF16 or FGS_F16 (math in
  * float32, rounded to nearest on store); grads are float32. */
 int fgs_adam_step(const fgs_params *params, const fgs_params *grads, const fgs_params *exp_avg,
-                  const fgs_params *exp_avg_sq, const float lr[6], double beta1, double beta2,
+                  const fgs_params *exp_avg_sq, const float lr[8], double beta1, double beta2,
                   double eps, int32_t step, void *stream);
 
 /* Adam state kept in device memory, so that a captured graph can replay
@@ -233,11 +250,11 @@ int fgs_adam_step(const fgs_params *params, const fgs_params *grads, const fgs_p
  * bias correction, then updates every group. */
 typedef struct fgs_adam_state {
     double beta1, beta2, eps;  /* exact hyper-parameters (0.999 is not a float32) */
-    float lr[6];            /* base learning rates in group order (Suppl. A) */
+    float lr[8];            /* base learning rates in group order (Suppl. A) */
     float lr_means_final;   /* exponential decay target of lr[0] (Suppl. A); <= 0: constant */
     int32_t decay_steps;    /* steps over which lr[0] decays to lr_means_final */
     int32_t step;           /* steps taken so far; the call uses step + 1 and stores it */
-    float step_size[6];     /* written by the call: lr_t / (1 - beta1^t) */
+    float step_size[8];     /* written by the call: lr_t / (1 - beta1^t) */
     float inv_bc2_sqrt;     /* written by the call: 1 / sqrt(1 - beta2^t) */
     float beta1_f, beta2_f, one_minus_beta1_f, one_minus_beta2_f, eps_f; /* written by the call */
 } fgs_adam_state;

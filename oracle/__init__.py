@@ -66,7 +66,13 @@ class _Camera(ctypes.Structure):
                 ("fx", ctypes.c_double), ("fy", ctypes.c_double),
                 ("cx", ctypes.c_double), ("cy", ctypes.c_double),
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32),
-                ("near_plane", ctypes.c_double), ("cam_pos", ctypes.c_double * 3)]
+                ("near_plane", ctypes.c_double), ("cam_pos", ctypes.c_double * 3),
+                ("time", ctypes.c_double)]
+
+
+class _Motion(ctypes.Structure):
+    _fields_ = [("velocity", ctypes.c_void_p), ("t0", ctypes.c_void_p),
+                ("sigma_t", ctypes.c_double)]
 
 
 class _Margins(ctypes.Structure):
@@ -133,6 +139,7 @@ def _cam_struct(cam) -> _Camera:
     c.fy = float(np.float32(cam.fy))
     c.cx = float(np.float32(cam.cx))
     c.cy = float(np.float32(cam.cy))
+    c.time = float(np.float32(getattr(cam, "time", 0.0)))
     c.width = int(cam.width)
     c.height = int(cam.height)
     c.near_plane = float(np.float32(cam.near))
@@ -146,6 +153,34 @@ def _mg_struct(m: Margins) -> _Margins:
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+MOTION_NAMES = ("velocity", "t0")
+
+
+def is_dynamic(params) -> bool:
+    """Dynamic Gaussians carry a velocity, a temporal centre and sigma_t."""
+    return "velocity" in params
+
+
+def names_of(params):
+    return PARAM_NAMES + MOTION_NAMES if is_dynamic(params) else PARAM_NAMES
+
+
+class _MotionArrays:
+    """The orc_motion struct of params (a NULL pointer for static ones),
+    keeping its float64 arrays alive."""
+
+    def __init__(self, params):
+        self.arrays = None
+        if is_dynamic(params):
+            n = np.shape(params["means"])[0]
+            self.arrays = (_f64(params["velocity"]).reshape(n, 3), _f64(params["t0"]).reshape(n))
+            self.struct = _Motion(self.arrays[0].ctypes.data, self.arrays[1].ctypes.data,
+                                  float(np.float32(params["sigma_t"])))
+
+    def ref(self):
+        return ctypes.byref(self.struct) if self.arrays is not None else None
 
 
 def _param_arrays(params):
@@ -178,9 +213,9 @@ def preprocess(cam, params, sh_degree=3, margins: Margins = NO_MARGINS):
                rgb=np.zeros((n, 3)), clamped=np.zeros((n, 3), np.uint8), depth=np.zeros(n),
                rect=np.zeros((n, 4), np.int32), status=np.zeros(n, np.int32),
                aux=np.zeros((n, 8)))
-    c, m = _cam_struct(cam), _mg_struct(margins)
+    c, m, mo = _cam_struct(cam), _mg_struct(margins), _MotionArrays(params)
     rc = lib.orc_preprocess(ctypes.byref(c), ctypes.c_int64(n), ctypes.c_int(sh_degree),
-                            *[_p(a) for a in arrs], ctypes.byref(m),
+                            *[_p(a) for a in arrs], mo.ref(), ctypes.byref(m),
                             _p(out["xy"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]),
                             _p(out["clamped"]), _p(out["depth"]), _p(out["rect"]),
                             _p(out["status"]), _p(out["aux"]))
@@ -206,10 +241,10 @@ def build_lists(cam, params, pre, sh_degree=3, margins: Margins = NO_MARGINS):
     lib = _lib_handle()
     arrs = _param_arrays(params)
     n = arrs[0].shape[0]
-    c, m = _cam_struct(cam), _mg_struct(margins)
+    c, m, mo = _cam_struct(cam), _mg_struct(margins), _MotionArrays(params)
     counts = np.zeros(n, np.int64)
     lib.orc_count_instances(ctypes.byref(c), ctypes.c_int64(n), ctypes.c_int(sh_degree),
-                            *[_p(a) for a in arrs], ctypes.byref(m), _p(counts))
+                            *[_p(a) for a in arrs], mo.ref(), ctypes.byref(m), _p(counts))
     offsets = np.zeros(n, np.int64)
     if n > 1:
         offsets[1:] = np.cumsum(counts)[:-1]
@@ -218,8 +253,8 @@ def build_lists(cam, params, pre, sh_degree=3, margins: Margins = NO_MARGINS):
     gid = np.zeros(max(total, 1), np.int32)
     flags = np.zeros(max(total, 1), np.uint8)
     lib.orc_emit_instances(ctypes.byref(c), ctypes.c_int64(n), ctypes.c_int(sh_degree),
-                           *[_p(a) for a in arrs], ctypes.byref(m), _p(offsets), _p(tile),
-                           _p(gid), _p(flags))
+                           *[_p(a) for a in arrs], mo.ref(), ctypes.byref(m), _p(offsets),
+                           _p(tile), _p(gid), _p(flags))
     tile, gid, flags = tile[:total], gid[:total], flags[:total]
     depth = pre["depth"][gid]
     order = np.argsort(depth, kind="stable")
@@ -289,7 +324,7 @@ def blend_backward(cam, pre, lists, dL_dimage, bg=(0.0, 0.0, 0.0)):
 
 
 def zero_grads(params):
-    return {k: np.zeros(np.shape(params[k]), np.float64) for k in PARAM_NAMES}
+    return {k: np.zeros(np.shape(params[k]), np.float64) for k in names_of(params)}
 
 
 def preprocess_backward(cam, params, screen_grads, sh_degree=3, grads=None):
@@ -299,12 +334,15 @@ def preprocess_backward(cam, params, screen_grads, sh_degree=3, grads=None):
     n = arrs[0].shape[0]
     if grads is None:
         grads = zero_grads(params)
-    c = _cam_struct(cam)
+    c, mo = _cam_struct(cam), _MotionArrays(params)
+    dyn = is_dynamic(params)
     lib.orc_preprocess_backward(ctypes.byref(c), ctypes.c_int64(n), ctypes.c_int(sh_degree),
                                 *[_p(a) for a in arrs], _p(screen_grads["xy"]),
                                 _p(screen_grads["conic"]), _p(screen_grads["opacity"]),
                                 _p(screen_grads["rgb"]),
-                                *[_p(grads[k]) for k in PARAM_NAMES])
+                                *[_p(grads[k]) for k in PARAM_NAMES], mo.ref(),
+                                _p(grads["velocity"]) if dyn else None,
+                                _p(grads["t0"]) if dyn else None)
     return grads
 
 
@@ -337,8 +375,10 @@ def adam(p, g, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15):
 
 
 # learning rates of Suppl. A in the order of PARAM_NAMES (means at its
-# initial value; the decay and scene-scale factor are host scalars)
-DEFAULT_LR = (1.6e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 1.25e-4)
+# initial value; the decay and scene-scale factor are host scalars), then
+# velocity and temporal centre of dynamic Gaussians (not given in the paper:
+# the means' rate and 1e-3)
+DEFAULT_LR = (1.6e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 1.25e-4, 1.6e-4, 1e-3)
 
 
 def render(cam, params, sh_degree=3, bg=(0.0, 0.0, 0.0), margins: Margins = NO_MARGINS):
@@ -370,8 +410,10 @@ def train_step(cams, params, targets, moments=None, step=1, sh_degree=3, lam=0.2
         moments = (zero_grads(params), zero_grads(params))
     m, v = moments
     new = {}
-    for k, lr_k in zip(PARAM_NAMES, lr):
+    for k, lr_k in zip(names_of(params), lr):
         p = np.asarray(params[k], np.float64).copy()
         adam(p, grads[k], m[k], v[k], lr_k, step)
         new[k] = p
+    if is_dynamic(params):
+        new["sigma_t"] = params["sigma_t"]
     return total, images, grads, new, (m, v)

@@ -45,7 +45,18 @@ typedef struct {
     int32_t width, height;
     double near_plane;
     double cam_pos[3];  /* camera centre in world space (for SH directions) */
+    double time;        /* timestamp of the view (dynamic Gaussians) */
 } orc_camera;
+
+/* Dynamic Gaussians (Sec. 3.4, the conditional Gaussian in its
+ * linear-velocity form): at time t the mean is mu + v (t - t0) and the
+ * opacity is multiplied by the temporal marginal exp(-(t - t0)^2 /
+ * (2 sigma_t^2)).  NULL (or velocity NULL) for static Gaussians. */
+typedef struct {
+    const double *velocity;  /* [n,3] */
+    const double *t0;        /* [n] */
+    double sigma_t;
+} orc_motion;
 
 /* Decision margins used to flag results that float32 may legitimately
  * decide the other way (all zero = pure FP64 decisions, nothing flagged). */
@@ -198,7 +209,10 @@ typedef struct {
     double detd;
     double conic[3];
     double xy[2];
-    double o;
+    double o;             /* opacity at the view's time */
+    double obase;         /* sigmoid of the logit (o without the temporal factor) */
+    double dtime;         /* t - t0 (dynamic Gaussians; 0 otherwise) */
+    double vel[3];        /* velocity (dynamic Gaussians; 0 otherwise) */
     double k;             /* 2 ln(255 o) */
     double ext[2];        /* half extents sqrt(k * covd_ii) */
     int rect[4];          /* pixel rect u0, v0, u1, v1 (inclusive) */
@@ -218,10 +232,20 @@ typedef struct {
 static void gauss_forward(const orc_camera *cam, int sh_degree, int64_t i,
                           const double *means, const double *log_scales, const double *quats,
                           const double *opacity_logits, const double *sh_dc, const double *sh_rest,
-                          const orc_margins *mg, orc_gauss *g)
+                          const orc_motion *mo, const orc_margins *mg, orc_gauss *g)
 {
     memset(g, 0, sizeof(*g));
-    const double mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+    double mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+    double ptime = 1.0;  /* temporal marginal */
+    if (mo && mo->velocity) {
+        /* conditional mean mu + v (t - t0) and marginal exp(-(t - t0)^2 / (2 sigma_t^2)) */
+        g->dtime = cam->time - mo->t0[i];
+        for (int a = 0; a < 3; ++a) {
+            g->vel[a] = mo->velocity[3 * i + a];
+            mu[a] += g->vel[a] * g->dtime;
+        }
+        ptime = exp(-0.5 * g->dtime * g->dtime / (mo->sigma_t * mo->sigma_t));
+    }
     const double *R = cam->R;
     int marginal = 0;
     int visible = 1;
@@ -293,8 +317,10 @@ static void gauss_forward(const orc_camera *cam, int sh_degree, int64_t i,
     g->xy[0] = cam->fx * tx / tz + cam->cx;
     g->xy[1] = cam->fy * ty / tz + cam->cy;
 
-    /* opacity activation; a Gaussian with o < tau_alpha can never reach it */
-    g->o = sigmoid((double)opacity_logits[i]);
+    /* opacity activation (times the temporal marginal); a Gaussian with
+     * o < tau_alpha can never reach it */
+    g->obase = sigmoid((double)opacity_logits[i]);
+    g->o = g->obase * ptime;
     if (near_threshold(g->o, ORC_ALPHA_MIN, mg->rel)) marginal = 1;
     if (g->o < ORC_ALPHA_MIN) visible = 0;
     if (g->o <= ORC_ALPHA_MIN * (1.0 - mg->rel)) { g->ok = 0; g->visible = 0; g->marginal = marginal; return; }
@@ -459,7 +485,7 @@ static int tile_decision(const orc_camera *cam, const orc_gauss *g, const orc_ma
  * clamped[3n], depth[n], rect[4n] (pixel rect, inclusive), status[n]
  * (ORC_VISIBLE | ORC_MARGINAL), aux[8n] = (tz, qnorm, det2, o, k, ext_x,
  * ext_y, detd). */
-int orc_preprocess(const orc_camera *cam, int64_t n, int sh_degree, const double *means, const double *log_scales, const double *quats, const double *opacity_logits, const double *sh_dc, const double *sh_rest, const orc_margins *mg, double *xy,
+int orc_preprocess(const orc_camera *cam, int64_t n, int sh_degree, const double *means, const double *log_scales, const double *quats, const double *opacity_logits, const double *sh_dc, const double *sh_rest, const orc_motion *mo, const orc_margins *mg, double *xy,
                    double *conic, double *opac, double *rgb, uint8_t *clamped, double *depth,
                    int32_t *rect, int32_t *status, double *aux)
 {
@@ -468,7 +494,7 @@ int orc_preprocess(const orc_camera *cam, int64_t n, int sh_degree, const double
     for (int64_t i = 0; i < n; ++i) {
         orc_gauss g;
         gauss_forward(cam, sh_degree, i, means, log_scales, quats, opacity_logits, sh_dc, sh_rest,
-                      mg, &g);
+                      mo, mg, &g);
         xy[2 * i] = g.xy[0]; xy[2 * i + 1] = g.xy[1];
         for (int a = 0; a < 3; ++a) {
             conic[3 * i + a] = g.conic[a];
@@ -493,7 +519,7 @@ int orc_preprocess(const orc_camera *cam, int64_t n, int sh_degree, const double
 
 /* Number of candidate (Gaussian, tile) instances per Gaussian: every kept
  * instance plus every instance a float32 evaluation could keep. */
-int orc_count_instances(const orc_camera *cam, int64_t n, int sh_degree, const double *means, const double *log_scales, const double *quats, const double *opacity_logits, const double *sh_dc, const double *sh_rest, const orc_margins *mg,
+int orc_count_instances(const orc_camera *cam, int64_t n, int sh_degree, const double *means, const double *log_scales, const double *quats, const double *opacity_logits, const double *sh_dc, const double *sh_rest, const orc_motion *mo, const orc_margins *mg,
                         int64_t *counts)
 {
     const int tiles_x = (cam->width + ORC_TILE - 1) / ORC_TILE;
@@ -502,7 +528,7 @@ int orc_count_instances(const orc_camera *cam, int64_t n, int sh_degree, const d
     for (int64_t i = 0; i < n; ++i) {
         orc_gauss g;
         gauss_forward(cam, sh_degree, i, means, log_scales, quats, opacity_logits, sh_dc, sh_rest,
-                      mg, &g);
+                      mo, mg, &g);
         int64_t cnt = 0;
         if (g.ok && (g.visible || g.marginal)) {
             for (int ty = g.rect_wide[1] / ORC_TILE; ty <= g.rect_wide[3] / ORC_TILE; ++ty)
@@ -516,7 +542,7 @@ int orc_count_instances(const orc_camera *cam, int64_t n, int sh_degree, const d
 
 /* Emits the candidates at offsets[i] in ascending Gaussian id, tiles
  * row-major inside the rectangle: tile id, Gaussian id and flags. */
-int orc_emit_instances(const orc_camera *cam, int64_t n, int sh_degree, const double *means, const double *log_scales, const double *quats, const double *opacity_logits, const double *sh_dc, const double *sh_rest, const orc_margins *mg,
+int orc_emit_instances(const orc_camera *cam, int64_t n, int sh_degree, const double *means, const double *log_scales, const double *quats, const double *opacity_logits, const double *sh_dc, const double *sh_rest, const orc_motion *mo, const orc_margins *mg,
                        const int64_t *offsets, int32_t *tile, int32_t *gid, uint8_t *flags)
 {
     const int tiles_x = (cam->width + ORC_TILE - 1) / ORC_TILE;
@@ -524,7 +550,7 @@ int orc_emit_instances(const orc_camera *cam, int64_t n, int sh_degree, const do
     for (int64_t i = 0; i < n; ++i) {
         orc_gauss g;
         gauss_forward(cam, sh_degree, i, means, log_scales, quats, opacity_logits, sh_dc, sh_rest,
-                      mg, &g);
+                      mo, mg, &g);
         if (!(g.ok && (g.visible || g.marginal))) continue;
         int64_t o = offsets[i];
         for (int ty = g.rect_wide[1] / ORC_TILE; ty <= g.rect_wide[3] / ORC_TILE; ++ty)
@@ -875,7 +901,8 @@ int orc_blend_backward(int32_t width, int32_t height, int64_t n_inst, const int6
 int orc_preprocess_backward(const orc_camera *cam, int64_t n, int sh_degree, const double *means, const double *log_scales, const double *quats, const double *opacity_logits, const double *sh_dc, const double *sh_rest, const double *dxy, const double *dconic,
                             const double *dopac, const double *drgb, double *g_means,
                             double *g_log_scales, double *g_quats, double *g_opacity,
-                            double *g_sh_dc, double *g_sh_rest)
+                            double *g_sh_dc, double *g_sh_rest, const orc_motion *mo,
+                            double *g_velocity, double *g_t0)
 {
     const orc_margins none = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1};
     const double *R = cam->R;
@@ -883,14 +910,16 @@ int orc_preprocess_backward(const orc_camera *cam, int64_t n, int sh_degree, con
     for (int64_t i = 0; i < n; ++i) {
         orc_gauss g;
         gauss_forward(cam, sh_degree, i, means, log_scales, quats, opacity_logits, sh_dc, sh_rest,
-                      &none, &g);
+                      mo, &none, &g);
         if (!g.visible) continue;
         const double tx = g.t[0], ty = g.t[1], tz = g.t[2];
         double dmu[3] = {0.0, 0.0, 0.0};
         double dt[3] = {0.0, 0.0, 0.0};
 
-        /* opacity: o = sigmoid(w) */
-        g_opacity[i] += dopac[i] * g.o * (1.0 - g.o);
+        /* opacity: o = sigmoid(w) p(t): do/dw = o (1 - sigmoid(w)),
+         * do/dt0 = o (t - t0) / sigma_t^2 */
+        g_opacity[i] += dopac[i] * g.o * (1.0 - g.obase);
+        if (mo && mo->velocity) g_t0[i] += dopac[i] * g.o * g.dtime / (mo->sigma_t * mo->sigma_t);
 
         /* colour: rgb = max(0, sum_k Y_k(dir) sh_k + 0.5) */
         {
@@ -963,9 +992,14 @@ int orc_preprocess_backward(const orc_camera *cam, int64_t n, int sh_degree, con
         dt[2] += dJ[0] * (-cam->fx / tz2) + dJ[2] * (2.0 * cam->fx * tx / tz3) +
                  dJ[4] * (-cam->fy / tz2) + dJ[5] * (2.0 * cam->fy * ty / tz3);
 
-        /* t = Rcam mu + tcam */
+        /* t = Rcam mu(t) + tcam; mu(t) = mu + v (t - t0) */
         for (int a = 0; a < 3; ++a) dmu[a] += R[a] * dt[0] + R[3 + a] * dt[1] + R[6 + a] * dt[2];
         for (int a = 0; a < 3; ++a) g_means[3 * i + a] += dmu[a];
+        if (mo && mo->velocity)
+            for (int a = 0; a < 3; ++a) {
+                g_velocity[3 * i + a] += dmu[a] * g.dtime;
+                g_t0[i] -= dmu[a] * g.vel[a];
+            }
 
         /* Sigma = M M^T, M = Rq S: dM = 2 dSigma M (dSigma symmetric) */
         double dM[9];

@@ -18,7 +18,7 @@ from . import build_lib
 
 FGS_TILE = 16
 FGS_MAX_VIEWS = 16
-FGS_NUM_GROUPS = 6
+FGS_NUM_GROUPS = 8
 FGS_F32, FGS_BF16, FGS_F16 = 0, 1, 2
 FGS_FLAG_CAPACITY = 1
 
@@ -52,12 +52,13 @@ class fgs_camera(ctypes.Structure):
                 ("fx", ctypes.c_float), ("fy", ctypes.c_float),
                 ("cx", ctypes.c_float), ("cy", ctypes.c_float),
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32),
-                ("near_plane", ctypes.c_float), ("cam_pos", ctypes.c_float * 3)]
+                ("near_plane", ctypes.c_float), ("cam_pos", ctypes.c_float * 3),
+                ("time", ctypes.c_float)]
 
 
 class fgs_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("data", ctypes.c_void_p * FGS_NUM_GROUPS),
-                ("dtype", ctypes.c_int32 * FGS_NUM_GROUPS)]
+                ("dtype", ctypes.c_int32 * FGS_NUM_GROUPS), ("sigma_t", ctypes.c_float)]
 
 
 class fgs_tuning(ctypes.Structure):
@@ -82,9 +83,9 @@ class fgs_workspace_layout(ctypes.Structure):
 
 class fgs_adam_state(ctypes.Structure):
     _fields_ = [("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
-                ("lr", ctypes.c_float * 6), ("lr_means_final", ctypes.c_float),
+                ("lr", ctypes.c_float * FGS_NUM_GROUPS), ("lr_means_final", ctypes.c_float),
                 ("decay_steps", ctypes.c_int32), ("step", ctypes.c_int32),
-                ("step_size", ctypes.c_float * 6), ("inv_bc2_sqrt", ctypes.c_float),
+                ("step_size", ctypes.c_float * FGS_NUM_GROUPS), ("inv_bc2_sqrt", ctypes.c_float),
                 ("beta1_f", ctypes.c_float), ("beta2_f", ctypes.c_float),
                 ("one_minus_beta1_f", ctypes.c_float), ("one_minus_beta2_f", ctypes.c_float),
                 ("eps_f", ctypes.c_float)]
@@ -201,7 +202,8 @@ def fgs_render_backward_adam(ws, layout, params, sh_degree, cams_host, cams_devi
 
 
 def fgs_adam_step(params, grads, exp_avg, exp_avg_sq, lr, beta1, beta2, eps, step, stream):
-    lr_arr = (ctypes.c_float * 6)(*[float(a) for a in lr])
+    lr = [float(a) for a in lr][:FGS_NUM_GROUPS]
+    lr_arr = (ctypes.c_float * FGS_NUM_GROUPS)(*(lr + [0.0] * (FGS_NUM_GROUPS - len(lr))))
     _check("fgs_adam_step",
            lib().fgs_adam_step(ctypes.byref(params), ctypes.byref(grads), ctypes.byref(exp_avg),
                                ctypes.byref(exp_avg_sq), lr_arr, float(beta1), float(beta2),
@@ -257,13 +259,16 @@ def camera_array(cams):
         a.fx, a.fy, a.cx, a.cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
         a.width, a.height = int(c.width), int(c.height)
         a.near_plane = float(c.near)
+        a.time = float(getattr(c, "time", 0.0))
     return arr
 
 
-def params_struct(n, ptrs, dtypes) -> fgs_params:
+def params_struct(n, ptrs, dtypes, sigma_t=0.0) -> fgs_params:
+    """6 groups (static Gaussians) or 8 (dynamic: velocity and t0 too)."""
     p = fgs_params()
     p.n = int(n)
-    for g in range(FGS_NUM_GROUPS):
+    for g in range(len(ptrs)):
         p.data[g] = int(ptrs[g])
         p.dtype[g] = int(dtypes[g])
+    p.sigma_t = float(sigma_t)
     return p

@@ -22,7 +22,7 @@ __global__ void adam_prepare_kernel(fgs_adam_state* st)
     st->step = t;
     const double bc1 = 1.0 - pow(st->beta1, (double)t);
     const double bc2 = 1.0 - pow(st->beta2, (double)t);
-    for (int g = 0; g < 6; ++g) {
+    for (int g = 0; g < FGS_NUM_GROUPS; ++g) {
         double lr = st->lr[g];
         if (g == 0 && st->lr_means_final > 0.0f && st->decay_steps > 0) {
             const double f = fmin((double)(t - 1) / (double)st->decay_steps, 1.0);

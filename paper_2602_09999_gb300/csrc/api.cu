@@ -56,7 +56,14 @@ cudaError_t launch_preprocess_bwd_adam(int64_t n, int deg, const fgs_params* p, 
                                        const fgs_adam_state* ds, cudaStream_t st);
 bool fused_adam_supported(int sh_dtype, int moment_dtype);
 
-static const int64_t kGroupWidth[FGS_NUM_GROUPS] = {3, 3, 4, 1, 3, 45};
+static const int64_t kGroupWidth[FGS_NUM_GROUPS] = {3, 3, 4, 1, 3, 45, 3, 1};
+static const int kStaticGroups = 6;  // groups 6 and 7 (velocity, t0) are optional
+
+// Groups present: all 8 for dynamic Gaussians (velocity and t0 set), else 6.
+static int groups_of(const fgs_params* p)
+{
+    return p->data[6] ? FGS_NUM_GROUPS : kStaticGroups;
+}
 
 static int check_adam_args(const fgs_params* params, const fgs_params* grads, const fgs_params* m,
                            const fgs_params* v)
@@ -64,13 +71,16 @@ static int check_adam_args(const fgs_params* params, const fgs_params* grads, co
     if (!params || !grads || !m || !v) return FGS_ERR_NULL;
     const int64_t n = params->n;
     if (n < 1 || grads->n != n || m->n != n || v->n != n) return FGS_ERR_SHAPE;
-    for (int g = 0; g < FGS_NUM_GROUPS; ++g) {
+    if ((params->data[6] == nullptr) != (params->data[7] == nullptr)) return FGS_ERR_NULL;
+    const int ng = groups_of(params);
+    for (int g = 0; g < ng; ++g) {
         if (!params->data[g] || !grads->data[g] || !m->data[g] || !v->data[g]) return FGS_ERR_NULL;
         if (grads->dtype[g] != FGS_F32) return FGS_ERR_DTYPE;
         if (m->dtype[g] != v->dtype[g]) return FGS_ERR_DTYPE;
         for (const fgs_params* q : {params, m})
             if (q->dtype[g] != FGS_F32 && q->dtype[g] != FGS_BF16 && q->dtype[g] != FGS_F16)
                 return FGS_ERR_DTYPE;
+        if (g >= kStaticGroups && params->dtype[g] != FGS_F32) return FGS_ERR_DTYPE;
     }
     return FGS_OK;
 }
@@ -206,17 +216,24 @@ template <typename T> static T* slot(void* ws, const fgs_workspace_layout* L, in
     return reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + L->offset[s]);
 }
 
-static int check_params(const fgs_params* p, int64_t n, bool grads)
+// Parameters (or their gradients: like = the parameters, float32 only):
+// groups 0..5 always, 6 and 7 (velocity, t0; float32) both or neither, and a
+// gradient struct has exactly the parameters' groups.
+static int check_params(const fgs_params* p, int64_t n, bool grads, const fgs_params* like = nullptr)
 {
     if (!p) return FGS_ERR_NULL;
     if (p->n != n) return FGS_ERR_SHAPE;
-    for (int g = 0; g < FGS_NUM_GROUPS; ++g) {
+    if ((p->data[6] == nullptr) != (p->data[7] == nullptr)) return FGS_ERR_NULL;
+    if (like && (p->data[6] == nullptr) != (like->data[6] == nullptr)) return FGS_ERR_NULL;
+    const int ng = groups_of(p);
+    for (int g = 0; g < ng; ++g) {
         if (!p->data[g]) return FGS_ERR_NULL;
         const int dt = p->dtype[g];
         if (dt != FGS_F32 && dt != FGS_BF16 && dt != FGS_F16) return FGS_ERR_DTYPE;
-        if ((grads || g < 4) && dt != FGS_F32) return FGS_ERR_DTYPE;
+        if ((grads || g < 4 || g >= kStaticGroups) && dt != FGS_F32) return FGS_ERR_DTYPE;
     }
     if (p->dtype[4] != p->dtype[5]) return FGS_ERR_DTYPE;
+    if (!grads && ng == FGS_NUM_GROUPS && !(p->sigma_t > 0.0f)) return FGS_ERR_ARG;
     return FGS_OK;
 }
 
@@ -346,7 +363,7 @@ int fgs_render_backward(void* ws, const fgs_workspace_layout* L, const fgs_param
     if (!cams_device || !bg || !dl_dimages) return FGS_ERR_NULL;
     if (sh_degree < 0 || sh_degree > 3) return FGS_ERR_SH_DEGREE;
     if ((rc = check_params(params, L->n, false)) != FGS_OK) return rc;
-    if ((rc = check_params(grads, L->n, true)) != FGS_OK) return rc;
+    if ((rc = check_params(grads, L->n, true, params)) != FGS_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     profile_mark(st, "begin");
     if ((rc = backward_blend(ws, L, vt, bg, dl_dimages, st)) != FGS_OK) return rc;
@@ -367,9 +384,9 @@ int fgs_render_backward_adam(void* ws, const fgs_workspace_layout* L, const fgs_
     if (!cams_device || !bg || !dl_dimages || !exp_avg || !exp_avg_sq || !state_device) return FGS_ERR_NULL;
     if (sh_degree < 0 || sh_degree > 3) return FGS_ERR_SH_DEGREE;
     if ((rc = check_params(params, L->n, false)) != FGS_OK) return rc;
-    if (grads && (rc = check_params(grads, L->n, true)) != FGS_OK) return rc;
+    if (grads && (rc = check_params(grads, L->n, true, params)) != FGS_OK) return rc;
     if (exp_avg->n != L->n || exp_avg_sq->n != L->n) return FGS_ERR_SHAPE;
-    for (int g = 0; g < FGS_NUM_GROUPS; ++g) {
+    for (int g = 0; g < groups_of(params); ++g) {
         if (!exp_avg->data[g] || !exp_avg_sq->data[g]) return FGS_ERR_NULL;
         if (exp_avg->dtype[g] != exp_avg->dtype[0] || exp_avg_sq->dtype[g] != exp_avg->dtype[0])
             return FGS_ERR_DTYPE;
@@ -386,7 +403,7 @@ int fgs_render_backward_adam(void* ws, const fgs_workspace_layout* L, const fgs_
 }
 
 int fgs_adam_step(const fgs_params* params, const fgs_params* grads, const fgs_params* exp_avg,
-                  const fgs_params* exp_avg_sq, const float lr[6], double beta1, double beta2,
+                  const fgs_params* exp_avg_sq, const float lr[8], double beta1, double beta2,
                   double eps, int32_t step, void* stream)
 {
     int rc = check_adam_args(params, grads, exp_avg, exp_avg_sq);
@@ -396,7 +413,7 @@ int fgs_adam_step(const fgs_params* params, const fgs_params* grads, const fgs_p
     const double bc1 = 1.0 - pow(beta1, (double)step);
     const double bc2 = 1.0 - pow(beta2, (double)step);
     profile_mark((cudaStream_t)stream, "begin");
-    for (int g = 0; g < FGS_NUM_GROUPS; ++g) {
+    for (int g = 0; g < groups_of(params); ++g) {
         const float step_size = (float)((double)lr[g] / bc1);
         const float inv_bc2_sqrt = (float)(1.0 / sqrt(bc2));
         const cudaError_t e = launch_adam_group(params->n * kGroupWidth[g], params->dtype[g],
@@ -418,7 +435,7 @@ int fgs_adam_step_device(const fgs_params* params, const fgs_params* grads, cons
     cudaStream_t st = (cudaStream_t)stream;
     profile_mark(st, "begin");
     if (launch_adam_prepare(state_device, st) != cudaSuccess) return FGS_ERR_CUDA;
-    for (int g = 0; g < FGS_NUM_GROUPS; ++g) {
+    for (int g = 0; g < groups_of(params); ++g) {
         const cudaError_t e = launch_adam_group(params->n * kGroupWidth[g], params->dtype[g],
                                                 exp_avg->dtype[g], params->data[g],
                                                 (const float*)grads->data[g], exp_avg->data[g],

@@ -62,6 +62,20 @@ struct alignas(16) TileRect {
 // d^T conic d <= k = 2 ln(255 o).  Preprocess, duplication and the blend
 // masks all derive k from the stored opacity with this one expression, so
 // their tile decisions agree bit for bit.
+// Dynamic Gaussians (Sec. 3.4, linear-velocity form of the conditional
+// Gaussian): at time t the mean is mu + v (t - t0) and the opacity is
+// scaled by the temporal marginal exp(-(t - t0)^2 / (2 sigma_t^2)).
+struct Motion {
+    const float* vel;  // [n,3] or nullptr (static Gaussians)
+    const float* t0;   // [n]
+    float inv_var;     // 1 / sigma_t^2
+};
+
+__device__ __forceinline__ float temporal_weight(float dt, float inv_var)
+{
+    return expf(-0.5f * dt * dt * inv_var);
+}
+
 __device__ __forceinline__ float opacity_k(float o)
 {
     return fmaxf(2.0f * __logf(255.0f * o), 0.0f);
@@ -92,7 +106,7 @@ __host__ __device__ inline int view_of_tile(const ViewTable& vt, int tile)
 }
 
 struct Cam {
-    float R[9], t[3], fx, fy, cx, cy, near_plane, pos[3];
+    float R[9], t[3], fx, fy, cx, cy, near_plane, pos[3], time;
     int width, height;
 };
 
@@ -112,6 +126,7 @@ __device__ inline Cam load_cam(const fgs_camera* cams, int v)
     k.cx = __ldg(&c->cx);
     k.cy = __ldg(&c->cy);
     k.near_plane = __ldg(&c->near_plane);
+    k.time = __ldg(&c->time);
     k.width = __ldg(&c->width);
     k.height = __ldg(&c->height);
     return k;

@@ -181,12 +181,12 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
                       const SHT* __restrict__ sh_rest, const fgs_camera* __restrict__ cams,
                       ViewTable vt, Screen* __restrict__ screen, TileRect* __restrict__ rects,
                       uint32_t* __restrict__ local_off, uint32_t* __restrict__ block_sum,
-                      int nblk)
+                      int nblk, Motion mo)
 {
     __shared__ uint32_t warp_tot[kPreBlock / 32];
     const int64_t i = (int64_t)blockIdx.x * kPreBlock + threadIdx.x;
     const bool valid = i < n;
-    float mu[3] = {0.f, 0.f, 0.f}, M[9], o = 0.f;
+    float mu[3] = {0.f, 0.f, 0.f}, M[9], o = 0.f, vel[3] = {0.f, 0.f, 0.f}, t0 = 0.f;
     bool ok = false;
     if (valid) {
         mu[0] = means[3 * i];
@@ -206,14 +206,26 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
             M[3 * r + 2] = Rq[3 * r + 2] * s2;
         }
         o = 1.0f / (1.0f + __expf(-opac[i]));
-        ok = qn >= kQNormMin && o >= kAlphaMin;
+        ok = qn >= kQNormMin;
+        if (mo.vel) {
+            vel[0] = mo.vel[3 * i]; vel[1] = mo.vel[3 * i + 1]; vel[2] = mo.vel[3 * i + 2];
+            t0 = mo.t0[i];
+        }
     }
     const int ncoef = (sh_degree + 1) * (sh_degree + 1);
     for (int v = 0; v < vt.n_views; ++v) {
         const Cam cam = load_cam(cams, v);
+        // the Gaussian at this view's time (static ones: as stored)
+        float mv[3] = {mu[0], mu[1], mu[2]}, ov = o;
+        if (mo.vel) {
+            const float dt = cam.time - t0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) mv[a] = mu[a] + vel[a] * dt;
+            ov = o * temporal_weight(dt, mo.inv_var);
+        }
         Geo g;
         g.ntiles = 0;
-        if (ok) project(cam, mu, M, o, g);
+        if (ok && ov >= kAlphaMin) project(cam, mv, M, ov, g);
         const bool has = g.ntiles > 0;
         uint32_t keep;
         const uint32_t count = count_tiles(g, has, cam.width, cam.height, keep);
@@ -230,7 +242,7 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
                                   (unsigned short)(g.tx0 + g.tw - 1),
                                   (unsigned short)(g.ty0 + g.ntiles / g.tw - 1));
             // SH colour from the view direction, streamed from memory
-            float d0 = mu[0] - cam.pos[0], d1 = mu[1] - cam.pos[1], d2 = mu[2] - cam.pos[2];
+            float d0 = mv[0] - cam.pos[0], d1 = mv[1] - cam.pos[1], d2 = mv[2] - cam.pos[2];
             const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
             d0 *= il; d1 *= il; d2 *= il;
             float Y[16];
@@ -252,7 +264,7 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
             if (r1 < 0.f) { bits |= 2u; r1 = 0.f; }
             if (r2 < 0.f) { bits |= 4u; r2 = 0.f; }
             rec.q0 = make_float4(g.mx, g.my, g.e.lb, g.e.ls);
-            rec.q1 = make_float4(g.e.c, g.e.s, o, g.depth);
+            rec.q1 = make_float4(g.e.c, g.e.s, ov, g.depth);
             rec.q2 = make_float4(r0, r1, r2, __uint_as_float(bits));
         }
         const int64_t vi = (int64_t)v * n + i;
@@ -471,9 +483,9 @@ __device__ __forceinline__ void view_colour_grad(const Cam& cam, const float mu[
 // "Fusing Backward and Optimizer"); the parameters alias the ones the
 // gradient pass reads, so neither is declared __restrict__.
 struct AdamArgs {
-    void* p[6];
-    void* m[6];
-    void* v[6];
+    void* p[8];
+    void* m[8];
+    void* v[8];
     const fgs_adam_state* st;
 };
 
@@ -592,11 +604,12 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
                       const Screen* __restrict__ screen, const ScreenGrad* __restrict__ sgrad,
                       float* __restrict__ g_means, float* __restrict__ g_scales,
                       float* __restrict__ g_quats, float* __restrict__ g_opac,
-                      float* __restrict__ g_dc, float* __restrict__ g_rest, AdamArgs aa)
+                      float* __restrict__ g_dc, float* __restrict__ g_rest, float* __restrict__ g_vel,
+                      float* __restrict__ g_t0, Motion mo, AdamArgs aa)
 {
     __shared__ __align__(16) float s_rest[kBwdBlock * 45];
     // FUSED: gradients of the small groups, one contiguous slice per group
-    constexpr int kSmall = FUSED ? kBwdBlock * 14 : 1;
+    constexpr int kSmall = FUSED ? kBwdBlock * 18 : 1;
     __shared__ __align__(16) float s_small[kSmall];
     const int64_t i0 = (int64_t)blockIdx.x * kBwdBlock;
     const int64_t i = i0 + threadIdx.x;
@@ -604,6 +617,7 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
     float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
     float gw = 0.f;
     float gdc[3] = {0.f, 0.f, 0.f};
+    float gvel[3] = {0.f, 0.f, 0.f}, gt0 = 0.f;  // dynamic Gaussians
     uint32_t vis_mask = 0;
     if (valid)
         for (int v = 0; v < vt.n_views; ++v)
@@ -632,6 +646,14 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
         float dM_acc[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) dM_acc[a] = 0.f;
+        // dynamic Gaussians: velocity, temporal centre and the opacity before
+        // the temporal factor
+        float vel[3] = {0.f, 0.f, 0.f}, t0 = 0.f, obase = 0.f;
+        if (mo.vel) {
+            vel[0] = mo.vel[3 * i]; vel[1] = mo.vel[3 * i + 1]; vel[2] = mo.vel[3 * i + 2];
+            t0 = mo.t0[i];
+            obase = 1.0f / (1.0f + __expf(-opac[i]));
+        }
         for (int v = 0; v < vt.n_views; ++v) {
             if (!(vis_mask >> v & 1u)) continue;
             const int64_t vi = (int64_t)v * n + i;
@@ -639,21 +661,26 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
             const uint32_t bits = __float_as_uint(rec.q2.w);
             const ScreenGrad g = sgrad[vi];
             const Cam cam = load_cam(cams, v);
-            const float o = rec.q1.z;
+            const float o = rec.q1.z;  // the opacity this view saw
+            // the mean at this view's time
+            const float dtime = mo.vel ? cam.time - t0 : 0.f;
+            const float mv[3] = {mu[0] + vel[0] * dtime, mu[1] + vel[1] * dtime, mu[2] + vel[2] * dtime};
             float t[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
-                t[r] = cam.R[3 * r] * mu[0] + cam.R[3 * r + 1] * mu[1] + cam.R[3 * r + 2] * mu[2] + cam.t[r];
+                t[r] = cam.R[3 * r] * mv[0] + cam.R[3 * r + 1] * mv[1] + cam.R[3 * r + 2] * mv[2] + cam.t[r];
             const float iz = 1.0f / t[2], iz2 = iz * iz;
             float dmu[3] = {0.f, 0.f, 0.f}, dt[3] = {0.f, 0.f, 0.f};
 
-            // opacity: o = sigmoid(w)
-            gw += g.g1.y * o * (1.0f - o);
+            // opacity: o = sigmoid(w) (times the temporal factor p for dynamic
+            // Gaussians: do/dw = p sigmoid' = o (1 - sigmoid), do/dt0 = o (t - t0) / sigma^2)
+            gw += g.g1.y * o * (1.0f - (mo.vel ? obase : o));
+            if (mo.vel) gt0 += g.g1.y * o * dtime * mo.inv_var;
 
             // colour -> view direction -> mean
             {
                 float d[3], il, grgb[3];
-                view_colour_grad(cam, mu, bits, g, d, il, grgb);
+                view_colour_grad(cam, mv, bits, g, d, il, grgb);
                 float coef[16];
 #pragma unroll
                 for (int kk = 0; kk < 16; ++kk) coef[kk] = 0.f;
@@ -734,10 +761,14 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
             dt[1] += -dj12 * cam.fy * iz2;
             dt[2] += -dj00 * cam.fx * iz2 + 2.0f * dj02 * cam.fx * t[0] * iz2 * iz -
                      dj11 * cam.fy * iz2 + 2.0f * dj12 * cam.fy * t[1] * iz2 * iz;
-            // t = Rcam mu + tcam
+            // t = Rcam mu(t) + tcam; mu(t) = mu + v (t - t0)
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-                gmu[a] += dmu[a] + cam.R[a] * dt[0] + cam.R[3 + a] * dt[1] + cam.R[6 + a] * dt[2];
+            for (int a = 0; a < 3; ++a) {
+                const float dmv = dmu[a] + cam.R[a] * dt[0] + cam.R[3 + a] * dt[1] + cam.R[6 + a] * dt[2];
+                gmu[a] += dmv;
+                gvel[a] += dmv * dtime;
+                gt0 -= dmv * vel[a];
+            }
         }
         // M = Rq S: dS, dRq -> log-scales and the quaternion
 #pragma unroll
@@ -763,14 +794,17 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
     }
     if (FUSED) {
         // slices: means [0, 384), log-scales [384, 768), quats [768, 1280),
-        // opacity [1280, 1408), sh_dc [1408, 1792)
+        // opacity [1280, 1408), sh_dc [1408, 1792), velocity [1792, 2176),
+        // t0 [2176, 2304)
         const int t = threadIdx.x;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             s_small[3 * t + a] = gmu[a];
             s_small[3 * kBwdBlock + 3 * t + a] = gls[a];
             s_small[11 * kBwdBlock + 3 * t + a] = gdc[a];
+            s_small[14 * kBwdBlock + 3 * t + a] = gvel[a];
         }
+        s_small[17 * kBwdBlock + t] = gt0;
 #pragma unroll
         for (int a = 0; a < 4; ++a) s_small[6 * kBwdBlock + 4 * t + a] = gq[a];
         s_small[10 * kBwdBlock + t] = gw;
@@ -788,6 +822,12 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
                             resolve(AdamScalars{}, aa.st, 4));
         adam_slice<SHT, MT>(aa.p[5], aa.m[5], aa.v[5], s_rest, g_rest, 45 * i0, 45 * nb,
                             resolve(AdamScalars{}, aa.st, 5));
+        if (mo.vel) {
+            adam_slice<float, MT>(aa.p[6], aa.m[6], aa.v[6], s_small + 14 * kBwdBlock, g_vel, 3 * i0, 3 * nb,
+                                  resolve(AdamScalars{}, aa.st, 6));
+            adam_slice<float, MT>(aa.p[7], aa.m[7], aa.v[7], s_small + 17 * kBwdBlock, g_t0, i0, nb,
+                                  resolve(AdamScalars{}, aa.st, 7));
+        }
         return;
     }
     if (valid) {
@@ -804,6 +844,11 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
             for (int a = 0; a < 4; ++a) g_quats[4 * i + a] = gq[a];
         }
         g_opac[i] = gw;
+        if (mo.vel) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) g_vel[3 * i + a] = gvel[a];
+            g_t0[i] = gt0;
+        }
     }
     __syncthreads();
     // coalesced copy of the block's sh_rest gradients (128 * 45 floats)
@@ -822,6 +867,17 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+static Motion motion_of(const fgs_params* p)
+{
+    Motion m{nullptr, nullptr, 0.f};
+    if (p->data[6] && p->data[7]) {
+        m.vel = (const float*)p->data[6];
+        m.t0 = (const float*)p->data[7];
+        m.inv_var = 1.0f / (p->sigma_t * p->sigma_t);
+    }
+    return m;
+}
+
 template <typename SHT>
 static cudaError_t launch_pre_fwd_t(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
                                     const ViewTable& vt, Screen* screen, TileRect* rects,
@@ -831,7 +887,7 @@ static cudaError_t launch_pre_fwd_t(int64_t n, int deg, const fgs_params* p, con
     preprocess_fwd_kernel<SHT><<<nblk, kPreBlock, 0, st>>>(
         n, deg, (const float*)p->data[0], (const float*)p->data[1], (const float*)p->data[2],
         (const float*)p->data[3], (const SHT*)p->data[4], (const SHT*)p->data[5], cams, vt, screen,
-        rects, local_off, block_sum, nblk);
+        rects, local_off, block_sum, nblk, motion_of(p));
     profile_mark(st, "preprocess_fwd");
     return cudaGetLastError();
 }
@@ -903,7 +959,8 @@ static cudaError_t launch_pre_bwd_t(int64_t n, int deg, const fgs_params* p, con
         n, deg, (const float*)p->data[0], (const float*)p->data[1], (const float*)p->data[2],
         (const float*)p->data[3], (const SHT*)p->data[4], (const SHT*)p->data[5], cams, vt, screen,
         sgrad, (float*)g->data[0], (float*)g->data[1], (float*)g->data[2], (float*)g->data[3],
-        (float*)g->data[4], (float*)g->data[5], AdamArgs{});
+        (float*)g->data[4], (float*)g->data[5], (float*)g->data[6], (float*)g->data[7], motion_of(p),
+        AdamArgs{});
     profile_mark(st, "preprocess_bwd");
     return cudaGetLastError();
 }
@@ -930,19 +987,19 @@ static cudaError_t launch_pre_bwd_adam_t(int64_t n, int deg, const fgs_params* p
 {
     const int grid = (int)((n + kBwdBlock - 1) / kBwdBlock);
     AdamArgs aa;
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < FGS_NUM_GROUPS; ++k) {
         aa.p[k] = p->data[k];
         aa.m[k] = m->data[k];
         aa.v[k] = v->data[k];
     }
     aa.st = ds;
-    float* gp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    float* gp[FGS_NUM_GROUPS] = {};
     if (g)
-        for (int k = 0; k < 6; ++k) gp[k] = (float*)g->data[k];
+        for (int k = 0; k < FGS_NUM_GROUPS; ++k) gp[k] = (float*)g->data[k];
     preprocess_bwd_kernel<SHT, MT, true><<<grid, kBwdBlock, 0, st>>>(
         n, deg, (const float*)p->data[0], (const float*)p->data[1], (const float*)p->data[2],
         (const float*)p->data[3], (const SHT*)p->data[4], (const SHT*)p->data[5], cams, vt, screen,
-        sgrad, gp[0], gp[1], gp[2], gp[3], gp[4], gp[5], aa);
+        sgrad, gp[0], gp[1], gp[2], gp[3], gp[4], gp[5], gp[6], gp[7], motion_of(p), aa);
     profile_mark(st, "preprocess_bwd_adam");
     return cudaGetLastError();
 }

@@ -41,6 +41,7 @@ class Camera:
     height: int
     near: float = NEAR_PLANE
     cam_pos: np.ndarray = field(default_factory=lambda: np.zeros(3, np.float32))
+    time: float = 0.0      # timestamp of the view (dynamic Gaussians)
 
     @property
     def tiles(self):

@@ -27,10 +27,14 @@ import torch
 from . import binding as B
 
 GROUPS = ("means", "log_scales", "quats", "opacity", "sh_dc", "sh_rest")
+# dynamic Gaussians add a velocity and a temporal centre (and a scalar sigma_t)
+MOTION_GROUPS = ("velocity", "t0")
 WIDTH = {"means": (3,), "log_scales": (3,), "quats": (4,), "opacity": (), "sh_dc": (3,),
-         "sh_rest": (15, 3)}
+         "sh_rest": (15, 3), "velocity": (3,), "t0": ()}
 # Suppl. A learning rates (means at its initial value)
 DEFAULT_LR = (1.6e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 1.25e-4)
+# velocity and temporal centre (no value in the paper: the means' rate and 1e-3)
+MOTION_LR = (1.6e-4, 1e-3)
 ADAM_BETAS = (0.9, 0.999)
 ADAM_EPS = 1e-15
 _DTYPE = {torch.float32: B.FGS_F32, torch.bfloat16: B.FGS_BF16, torch.float16: B.FGS_F16}
@@ -40,15 +44,24 @@ def current_stream() -> int:
     return torch.cuda.current_stream().cuda_stream
 
 
+def groups_of(t) -> tuple:
+    """Parameter groups a dict holds: the six static ones, plus velocity and
+    t0 for dynamic Gaussians."""
+    return GROUPS + MOTION_GROUPS if "velocity" in t else GROUPS
+
+
 def params_struct(t: Dict[str, torch.Tensor]) -> B.fgs_params:
+    """fgs_params over the tensors of t (and its scalar sigma_t, if any)."""
     n = t["means"].shape[0]
-    for k in GROUPS:
+    gs = groups_of(t)
+    for k in gs:
         x = t[k]
         if not x.is_cuda or not x.is_contiguous():
             raise ValueError(f"{k} must be a contiguous CUDA tensor")
         if tuple(x.shape) != (n,) + WIDTH[k]:
             raise ValueError(f"{k} has shape {tuple(x.shape)}, expected {(n,) + WIDTH[k]}")
-    return B.params_struct(n, [t[k].data_ptr() for k in GROUPS], [_DTYPE[t[k].dtype] for k in GROUPS])
+    return B.params_struct(n, [t[k].data_ptr() for k in gs], [_DTYPE[t[k].dtype] for k in gs],
+                           float(t.get("sigma_t", 0.0)))
 
 
 class Views:
@@ -184,11 +197,13 @@ class RasterizeFn(torch.autograd.Function):
 
 def to_device_params(params, device="cuda", sh_dtype=torch.float32):
     out = {}
-    for k in GROUPS:
+    for k in groups_of(params):
         x = torch.as_tensor(np.ascontiguousarray(params[k])) if isinstance(params[k], np.ndarray) \
             else params[k]
         dt = sh_dtype if k in ("sh_dc", "sh_rest") else torch.float32
         out[k] = x.to(device=device, dtype=dt).contiguous()
+    if "sigma_t" in params:
+        out["sigma_t"] = float(params["sigma_t"])
     return out
 
 
@@ -215,11 +230,12 @@ class Trainer:
         self.store_grads = bool(store_grads)
         self.params = to_device_params(params, device, sh_dtype)
         self.n = self.params["means"].shape[0]
-        self.grads = {k: torch.zeros(self.params[k].shape, device=device) for k in GROUPS}
+        self.groups = groups_of(self.params)
+        self.grads = {k: torch.zeros(self.params[k].shape, device=device) for k in self.groups}
         self.exp_avg = {k: torch.zeros(self.params[k].shape, device=device, dtype=moment_dtype)
-                        for k in GROUPS}
+                        for k in self.groups}
         self.exp_avg_sq = {k: torch.zeros(self.params[k].shape, device=device, dtype=moment_dtype)
-                           for k in GROUPS}
+                           for k in self.groups}
         self.views = Views(cams, device)
         self.rast = Rasterizer(self.n, self.views, k_max, device)
         P = self.views.total_pixels
@@ -229,7 +245,8 @@ class Trainer:
         self.loss = torch.zeros(1, device=device)
         self.sh_degree, self.lam, self.bg = int(sh_degree), float(lam), tuple(float(b) for b in bg)
         st = B.fgs_adam_state()
-        for g in range(6):
+        lr = tuple(lr) + (MOTION_LR if len(lr) == len(GROUPS) else ())
+        for g in range(len(lr)):
             st.lr[g] = float(lr[g])
         st.lr_means_final = float(lr_means_final)
         st.decay_steps = int(decay_steps)
