@@ -232,3 +232,54 @@ def small_scene(n, seed, spread=1.0, log_scale_mean=-2.5, log_scale_std=0.4,
     dc, rest = _sh(rng, n)
     return dict(means=means, log_scales=log_scales, quats=quats, opacity=opacity, sh_dc=dc,
                 sh_rest=rest)
+
+
+# ---------------------------------------------------------------------------
+# dynamic (4D) workload: Gaussians with a linear velocity and a temporal
+# centre (the linear-velocity form of the conditional Gaussian, Sec. 3.4)
+# ---------------------------------------------------------------------------
+DYN_TIMESTAMPS = 150
+DYN_SIGMA_T = 0.1
+
+
+def dynamic_scene(n=600_000, seed=5, radius=1.5):
+    """Object-centred dynamic scene (shaped like the synthetic objects the
+    paper's 4D experiments use): means N(0, 0.5^2 I) inside a ball of
+    `radius`, log-scales N(-4.5, 0.6), opacity logits N(-1, 1.5), SH as
+    elsewhere; velocity N(0, 0.05^2 I), temporal centre U(0, 1),
+    sigma_t = 0.1."""
+    rng = np.random.default_rng(seed)
+    means = rng.normal(0.0, 0.5, (n, 3))
+    r = np.linalg.norm(means, axis=1, keepdims=True)
+    means = np.where(r > radius, means * (radius / np.maximum(r, 1e-12)), means).astype(np.float32)
+    log_scales = rng.normal(-4.5, 0.6, (n, 3)).astype(np.float32)
+    quats = _unit_quats(rng, n)
+    opacity = rng.normal(-1.0, 1.5, n).astype(np.float32)
+    dc, rest = _sh(rng, n)
+    velocity = rng.normal(0.0, 0.05, (n, 3)).astype(np.float32)
+    t0 = rng.uniform(0.0, 1.0, n).astype(np.float32)
+    return dict(means=means, log_scales=log_scales, quats=quats, opacity=opacity, sh_dc=dc,
+                sh_rest=rest, velocity=velocity, t0=t0, sigma_t=DYN_SIGMA_T)
+
+
+def dynamic_cameras(count=6, seed=6, radius=4.0, min_size=(800, 800), max_size=(1352, 1014),
+                    timestamps=DYN_TIMESTAMPS, sizes=None):
+    """Views of the dynamic scene: on a sphere of `radius` around the object
+    (azimuth U(0, 2pi), elevation U(-20, 40) degrees), each at a random one of
+    `timestamps` evenly spaced times in [0, 1] and, unless `sizes` is given,
+    a random resolution between min_size and max_size."""
+    rng = np.random.default_rng(seed)
+    cams = []
+    for i in range(count):
+        az = rng.uniform(0.0, 2.0 * np.pi)
+        el = np.deg2rad(rng.uniform(-20.0, 40.0))
+        eye = radius * np.array([np.cos(el) * np.sin(az), -np.sin(el), np.cos(el) * np.cos(az)])
+        if sizes is not None:
+            w, h = sizes[i % len(sizes)]
+        else:
+            w = int(rng.integers(min_size[0], max_size[0] + 1))
+            h = int(rng.integers(min_size[1], max_size[1] + 1))
+        cam = look_at(eye, (0.0, 0.0, 0.0), w, h)
+        cam.time = float(rng.integers(0, timestamps)) / (timestamps - 1)
+        cams.append(cam)
+    return cams

@@ -182,16 +182,17 @@ def gpu_grads(params, cams, targets, masks=None, lam=0.2, bg=(0.0, 0.0, 0.0), sh
         for v, m in enumerate(masks):
             view = views.split(dl)[v]
             view[:, torch.from_numpy(m).cuda()] = 0.0
-    grads = {k: torch.zeros(t[k].shape, device="cuda") for k in T.GROUPS}
+    grads = {k: torch.zeros(t[k].shape, device="cuda") for k in T.groups_of(t)}
     rast.backward(T.params_struct(t), sh_degree, bg, dl, T.params_struct(grads))
     torch.cuda.synchronize()
     return float(loss.item()), {k: v.cpu().numpy() for k, v in grads.items()}, rast
 
 
 def grad_errors(gg, go, exclude=None):
-    """Relative L2 error per tensor over the Gaussians not excluded."""
+    """Relative L2 error per tensor over the Gaussians not excluded (every
+    group both sides hold: six, or eight for dynamic Gaussians)."""
     out = {}
-    for k in T.GROUPS:
+    for k in [k for k in T.GROUPS + T.MOTION_GROUPS if k in gg and k in go]:
         a, b = np.asarray(gg[k], np.float64), np.asarray(go[k], np.float64)
         if exclude is not None and exclude.any():
             a, b = a[~exclude], b[~exclude]
