@@ -54,6 +54,8 @@ def parse_args():
                     help="views per step of the batched variants")
     ap.add_argument("--no-tune", action="store_true", help="default launch configuration")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-dynamic", action="store_true",
+                    help="skip the dynamic (4D) workload: 600k Gaussians, 6 views per step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
@@ -513,13 +515,97 @@ def run_ours(args, dist):
         batched.append(entry)
         del tb
 
+    dynamic = None if args.no_dynamic else run_dynamic(args, dist, stream, profile_pass, per_step_ms)
+
     return dict(tuned=list(tuned[0]) if tuned else None, tuning_ms=tuned[1] if tuned else None,
                 ms_per_step=ms_per_step, views_per_s=views_per_s, elapsed_ms=max_ms,
                 phase_ms=phase_ms, launches_per_step=launches_per_step,
                 launches=(None if launches_per_step is None
                           else int(round(launches_per_step * args.steps))),
-                roofline=roofline, clocks=clocks, e2e=e2e, batched=batched,
+                roofline=roofline, clocks=clocks, e2e=e2e, batched=batched, dynamic=dynamic,
                 k_max=k_max, instances_last=inst_last, visible_last=visible_est, n=n)
+
+
+# ---------------------------------------------------------------------------
+# the dynamic (4D) workload
+# ---------------------------------------------------------------------------
+def run_dynamic(args, dist, stream, profile_pass, per_step_ms, n=600_000, views=6, pool=25):
+    """Dynamic Gaussians (velocity and temporal centre): 600k Gaussians, 6
+    views per step at random timestamps (150 of them) and poses, full step
+    with the velocity and t0 gradients, captured as a CUDA graph.  The
+    graph needs fixed view sizes, so the 6 resolutions (800x800 to 1352x1014)
+    are drawn once; every step takes new poses and times from a pool of
+    camera sets."""
+    import torch
+
+    from paper_2602_09999_gb300 import binding as B
+    from paper_2602_09999_gb300 import scenes
+    from paper_2602_09999_gb300 import train as T
+
+    torch.cuda.empty_cache()
+    params = scenes.dynamic_scene(n, seed=5)
+    sizes = [(c.width, c.height) for c in scenes.dynamic_cameras(views, seed=6)]
+    sets = [scenes.dynamic_cameras(views, seed=100 + s, sizes=sizes) for s in range(pool)]
+    cam_bytes = ctypes.sizeof(B.fgs_camera) * views
+    table = torch.frombuffer(bytearray(b"".join(bytes(B.camera_array(cs)) for cs in sets)),
+                             dtype=torch.uint8).cuda()
+    targets = [scenes.target_image(w, h, view=i) for i, (w, h) in enumerate(sizes)]
+    # instance capacity from the pool, with margin
+    probe = T.Trainer(params, sets[0], k_max=max(4_000_000, 12 * n * views // 10))
+    kmax_seen = 0
+    for s in range(pool):
+        probe.views.device.copy_(table[s * cam_bytes:(s + 1) * cam_bytes])
+        probe.forward_only()
+        kmax_seen = max(kmax_seen, probe.rast.error(clear=True)[1])
+    del probe
+    torch.cuda.empty_cache()
+    tr = T.Trainer(params, sets[0], k_max=int(kmax_seen * 1.25) + 4096, lam=0.2)
+    tr.set_targets(targets)
+
+    def load(i):
+        s = i % pool
+        tr.views.device.copy_(table[s * cam_bytes:(s + 1) * cam_bytes])
+
+    load(0)
+    tr.capture(warmup=2)
+    for i in range(args.warmup):
+        load(i)
+        tr.replay()
+    torch.cuda.synchronize()
+    if tr.rast.error()[0]:
+        raise RuntimeError("capacity exceeded in the dynamic workload")
+    steps = max(10, args.steps // views)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        load(args.warmup + i)
+        tr.replay()
+    e1.record(stream)
+    e1.synchronize()
+    ms = dist.max(e0.elapsed_time(e1))
+    if tr.rast.error()[0]:
+        raise RuntimeError("capacity exceeded in the dynamic workload")
+    out = {"workload": f"dynamic Gaussians (velocity, temporal centre, sigma_t 0.1), {n} "
+                       f"Gaussians, SH degree 3, {views} views per step at random times "
+                       f"(150 timestamps) and poses, float32, 0.8 L1 + 0.2 D-SSIM, Adam",
+           "views_per_s": round(dist.world * steps * views / (ms / 1000.0), 3),
+           "ms_per_step": round(ms / steps, 4), "views_per_step": views,
+           "resolutions": [f"{w}x{h}" for w, h in sizes],
+           "megapixels_per_s": round(dist.world * steps * sum(w * h for w, h in sizes)
+                                     / (ms / 1000.0) / 1e6, 3),
+           "graph": True, "steps": steps}
+    if not args.no_profile:
+        def eager(i):
+            load(i)
+            tr.step()
+        ph, _ = profile_pass(eager, args.warmup + steps, 4)
+        out["kernel_ms_per_step"] = per_step_ms(ph, 4)
+    del tr
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -623,7 +709,7 @@ def main():
                 "data": "synthetic (seeded outdoor-shaped scene, orbit cameras, uniform targets)",
                 "config": config_dict(args, n), "clocks": r["clocks"], "e2e": r["e2e"],
                 "gpu_launches": r["launches"], "roofline": r["roofline"], "cpu_baseline": cpu,
-                "batched": r["batched"], "blend_config": r["tuned"],
+                "batched": r["batched"], "dynamic": r["dynamic"], "blend_config": r["tuned"],
                 "blend_config_ms": r["tuning_ms"], "kernel_ms_per_step": r["phase_ms"],
                 "instances_last_step": r["instances_last"], "k_max": r["k_max"]}
         print(json.dumps(line), flush=True)

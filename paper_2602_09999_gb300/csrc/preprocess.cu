@@ -173,7 +173,7 @@ __device__ __forceinline__ uint32_t count_tiles(const Geo& g, bool has, int widt
 // third of the Gaussians) and wait at the per-view scan, so more, smaller CTAs
 // keep the SM busier -- 0.32 ms per 3M-Gaussian view against 0.39 ms with 3
 // CTAs of 256 threads.
-template <typename SHT>
+template <typename SHT, bool MOTION>
 __global__ void __launch_bounds__(kPreBlock, 8)
 preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
                       const float* __restrict__ log_scales, const float* __restrict__ quats,
@@ -207,7 +207,7 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
         }
         o = 1.0f / (1.0f + __expf(-opac[i]));
         ok = qn >= kQNormMin;
-        if (mo.vel) {
+        if (MOTION) {
             vel[0] = mo.vel[3 * i]; vel[1] = mo.vel[3 * i + 1]; vel[2] = mo.vel[3 * i + 2];
             t0 = mo.t0[i];
         }
@@ -217,7 +217,7 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
         const Cam cam = load_cam(cams, v);
         // the Gaussian at this view's time (static ones: as stored)
         float mv[3] = {mu[0], mu[1], mu[2]}, ov = o;
-        if (mo.vel) {
+        if (MOTION) {
             const float dt = cam.time - t0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) mv[a] = mu[a] + vel[a] * dt;
@@ -596,7 +596,7 @@ __device__ __forceinline__ void adam_slice(void* p, void* m, void* v, const floa
 // SM (104 registers) and 1.19-1.24 ms at 7.
 constexpr int kFusedMinBlocks = 6;
 
-template <typename SHT, typename MT, bool FUSED>
+template <typename SHT, typename MT, bool FUSED, bool MOTION>
 __global__ void __launch_bounds__(kBwdBlock, FUSED ? kFusedMinBlocks : 1)
 preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float* log_scales,
                       const float* quats, const float* opac, const SHT* sh_dc, const SHT* sh_rest,
@@ -649,7 +649,7 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
         // dynamic Gaussians: velocity, temporal centre and the opacity before
         // the temporal factor
         float vel[3] = {0.f, 0.f, 0.f}, t0 = 0.f, obase = 0.f;
-        if (mo.vel) {
+        if (MOTION) {
             vel[0] = mo.vel[3 * i]; vel[1] = mo.vel[3 * i + 1]; vel[2] = mo.vel[3 * i + 2];
             t0 = mo.t0[i];
             obase = 1.0f / (1.0f + __expf(-opac[i]));
@@ -663,8 +663,10 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
             const Cam cam = load_cam(cams, v);
             const float o = rec.q1.z;  // the opacity this view saw
             // the mean at this view's time
-            const float dtime = mo.vel ? cam.time - t0 : 0.f;
-            const float mv[3] = {mu[0] + vel[0] * dtime, mu[1] + vel[1] * dtime, mu[2] + vel[2] * dtime};
+            const float dtime = MOTION ? cam.time - t0 : 0.f;
+            float mv[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) mv[a] = MOTION ? mu[a] + vel[a] * dtime : mu[a];
             float t[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
@@ -674,8 +676,8 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
 
             // opacity: o = sigmoid(w) (times the temporal factor p for dynamic
             // Gaussians: do/dw = p sigmoid' = o (1 - sigmoid), do/dt0 = o (t - t0) / sigma^2)
-            gw += g.g1.y * o * (1.0f - (mo.vel ? obase : o));
-            if (mo.vel) gt0 += g.g1.y * o * dtime * mo.inv_var;
+            gw += g.g1.y * o * (1.0f - (MOTION ? obase : o));
+            if (MOTION) gt0 += g.g1.y * o * dtime * mo.inv_var;
 
             // colour -> view direction -> mean
             {
@@ -766,8 +768,10 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
             for (int a = 0; a < 3; ++a) {
                 const float dmv = dmu[a] + cam.R[a] * dt[0] + cam.R[3 + a] * dt[1] + cam.R[6 + a] * dt[2];
                 gmu[a] += dmv;
-                gvel[a] += dmv * dtime;
-                gt0 -= dmv * vel[a];
+                if (MOTION) {
+                    gvel[a] += dmv * dtime;
+                    gt0 -= dmv * vel[a];
+                }
             }
         }
         // M = Rq S: dS, dRq -> log-scales and the quaternion
@@ -822,7 +826,7 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
                             resolve(AdamScalars{}, aa.st, 4));
         adam_slice<SHT, MT>(aa.p[5], aa.m[5], aa.v[5], s_rest, g_rest, 45 * i0, 45 * nb,
                             resolve(AdamScalars{}, aa.st, 5));
-        if (mo.vel) {
+        if (MOTION) {
             adam_slice<float, MT>(aa.p[6], aa.m[6], aa.v[6], s_small + 14 * kBwdBlock, g_vel, 3 * i0, 3 * nb,
                                   resolve(AdamScalars{}, aa.st, 6));
             adam_slice<float, MT>(aa.p[7], aa.m[7], aa.v[7], s_small + 17 * kBwdBlock, g_t0, i0, nb,
@@ -844,7 +848,7 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
             for (int a = 0; a < 4; ++a) g_quats[4 * i + a] = gq[a];
         }
         g_opac[i] = gw;
-        if (mo.vel) {
+        if (MOTION) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) g_vel[3 * i + a] = gvel[a];
             g_t0[i] = gt0;
@@ -884,10 +888,12 @@ static cudaError_t launch_pre_fwd_t(int64_t n, int deg, const fgs_params* p, con
                                     uint32_t* local_off, uint32_t* block_sum, cudaStream_t st)
 {
     const int nblk = (int)((n + kPreBlock - 1) / kPreBlock);
-    preprocess_fwd_kernel<SHT><<<nblk, kPreBlock, 0, st>>>(
+    const Motion mo = motion_of(p);
+    auto kernel = mo.vel ? preprocess_fwd_kernel<SHT, true> : preprocess_fwd_kernel<SHT, false>;
+    kernel<<<nblk, kPreBlock, 0, st>>>(
         n, deg, (const float*)p->data[0], (const float*)p->data[1], (const float*)p->data[2],
         (const float*)p->data[3], (const SHT*)p->data[4], (const SHT*)p->data[5], cams, vt, screen,
-        rects, local_off, block_sum, nblk, motion_of(p));
+        rects, local_off, block_sum, nblk, mo);
     profile_mark(st, "preprocess_fwd");
     return cudaGetLastError();
 }
@@ -955,11 +961,14 @@ static cudaError_t launch_pre_bwd_t(int64_t n, int deg, const fgs_params* p, con
                                     const ScreenGrad* sgrad, const fgs_params* g, cudaStream_t st)
 {
     const int grid = (int)((n + kBwdBlock - 1) / kBwdBlock);
-    preprocess_bwd_kernel<SHT, float, false><<<grid, kBwdBlock, 0, st>>>(
+    const Motion mo = motion_of(p);
+    auto kernel = mo.vel ? preprocess_bwd_kernel<SHT, float, false, true>
+                         : preprocess_bwd_kernel<SHT, float, false, false>;
+    kernel<<<grid, kBwdBlock, 0, st>>>(
         n, deg, (const float*)p->data[0], (const float*)p->data[1], (const float*)p->data[2],
         (const float*)p->data[3], (const SHT*)p->data[4], (const SHT*)p->data[5], cams, vt, screen,
         sgrad, (float*)g->data[0], (float*)g->data[1], (float*)g->data[2], (float*)g->data[3],
-        (float*)g->data[4], (float*)g->data[5], (float*)g->data[6], (float*)g->data[7], motion_of(p),
+        (float*)g->data[4], (float*)g->data[5], (float*)g->data[6], (float*)g->data[7], mo,
         AdamArgs{});
     profile_mark(st, "preprocess_bwd");
     return cudaGetLastError();
@@ -996,10 +1005,12 @@ static cudaError_t launch_pre_bwd_adam_t(int64_t n, int deg, const fgs_params* p
     float* gp[FGS_NUM_GROUPS] = {};
     if (g)
         for (int k = 0; k < FGS_NUM_GROUPS; ++k) gp[k] = (float*)g->data[k];
-    preprocess_bwd_kernel<SHT, MT, true><<<grid, kBwdBlock, 0, st>>>(
+    const Motion mo = motion_of(p);
+    auto kernel = mo.vel ? preprocess_bwd_kernel<SHT, MT, true, true> : preprocess_bwd_kernel<SHT, MT, true, false>;
+    kernel<<<grid, kBwdBlock, 0, st>>>(
         n, deg, (const float*)p->data[0], (const float*)p->data[1], (const float*)p->data[2],
         (const float*)p->data[3], (const SHT*)p->data[4], (const SHT*)p->data[5], cams, vt, screen,
-        sgrad, gp[0], gp[1], gp[2], gp[3], gp[4], gp[5], gp[6], gp[7], motion_of(p), aa);
+        sgrad, gp[0], gp[1], gp[2], gp[3], gp[4], gp[5], gp[6], gp[7], mo, aa);
     profile_mark(st, "preprocess_bwd_adam");
     return cudaGetLastError();
 }
