@@ -584,13 +584,24 @@ int orc_emit_instances(const orc_camera *cam, int64_t n, int sh_degree, const do
  *    held fixed);
  *  - the order of two blended entries with tied depths: swapping adjacent
  *    entries changes the pixel by T alpha_1 alpha_2 (c_1 - c_2);
- *  - the stop test: always flagged.
+ *  - the stop test, where the tested T (1 - alpha) lies within its float32
+ *    error bound of 1e-4.  That bound is relative and grows along the walk:
+ *    t_rel, plus (alpha slack + rounding) / (1 - alpha) for every blended
+ *    factor 1 - alpha, plus alpha / (1 - alpha) for every uncertain blend
+ *    decision before the test (taking one the other way scales all later T
+ *    by 1 - alpha or its inverse).  Stopping at entry j instead of going on
+ *    loses what the walk blended from j onwards and leaves T_j on the
+ *    background: the oracle knows that change once the walk is done.
+ *    Going on past the oracle's last test instead adds alpha T (c - bg) of
+ *    that entry and at most T (1 - alpha)(1 + bound) times the largest
+ *    |c - bg| of the list's later entries.
  * The 0.99 clamp leaves the value continuous; it is flagged only when every
  * decision is (value_tol = 0), for scenes that must avoid kinks.  More than
- * ORC_MAX_EVENTS blend decisions in one pixel flag it as well.  `hard` marks
- * the flags whose effect is not bounded (stop test, overflow); `allowance`
- * sums the bounded effects. */
+ * ORC_MAX_EVENTS blend decisions or ORC_MAX_STOPS stop tests near the
+ * threshold in one pixel flag it as `hard` (effect not bounded);
+ * `allowance` sums the bounded effects. */
 #define ORC_MAX_EVENTS 64
+#define ORC_MAX_STOPS 16
 typedef struct {
     double C[3];
     double T;
@@ -604,6 +615,13 @@ typedef struct {
 typedef struct {
     double T0, alpha, c[3], C_after[3], T_after;
 } orc_event;
+
+/* a stop test within its error bound: T and C before the entry, its alpha
+ * and colour, whether the walk stopped there, and the bound */
+typedef struct {
+    double T0, alpha, c[3], C_before[3], bound;
+    int stopped;
+} orc_stop;
 
 static double max_abs_diff3(const double *a, const double *b)
 {
@@ -621,8 +639,14 @@ static void pixel_walk(double px, double py, int64_t start, int64_t end, const i
     int64_t pos = 0, n = 0, last = -1;
     int amb = 0, hard = 0;
     double allowance = 0.0;
+    /* relative error bound of T as float32 computes it (zero without margins) */
+    double t_err = 0.0;
+    const double t_unit = mg->t_rel > 0.0 ? 0x1p-23 : 0.0;
     orc_event ev[ORC_MAX_EVENTS];
     int nev = 0;
+    orc_stop st[ORC_MAX_STOPS];
+    int nst = 0;
+    int64_t j_stop = end;      /* the entry the walk stopped before, end if none */
     double prev_depth = -1.0, prev_T = 0.0, prev_alpha = 0.0;
     const double *prev_c = NULL;
     int have_prev = 0;
@@ -659,6 +683,9 @@ static void pixel_walk(double px, double py, int64_t start, int64_t end, const i
         }
         const double alpha = oG < ORC_ALPHA_MAX ? oG : ORC_ALPHA_MAX;
         const int blend = keep && power <= 0.0 && alpha >= ORC_ALPHA_MIN;
+        /* this entry's blend decision taken the other way scales T by 1 - a */
+        const double a_flip = alpha > ORC_ALPHA_MIN ? alpha : ORC_ALPHA_MIN;
+        const double own_flip = uncertain && mg->t_rel > 0.0 ? a_flip / (1.0 - a_flip) : 0.0;
         double test = T;
         if (blend) {
             if (have_prev && fabs(depth[g] - prev_depth) <= mg->depth_rel * fabs(depth[g])) {
@@ -667,9 +694,31 @@ static void pixel_walk(double px, double py, int64_t start, int64_t end, const i
                 if (effect > mg->value_tol || mg->value_tol <= 0.0) amb = 1;
             }
             test = T * (1.0 - alpha);
-            if (fabs(test - ORC_T_MIN) <= ORC_T_MIN * mg->t_rel) amb = hard = 1;
-            if (test < ORC_T_MIN) break;
+            const double eps = (alpha * slack + t_unit) / (1.0 - alpha);
+            const double bound = mg->t_rel + t_err + eps + own_flip;
+            if (fabs(test - ORC_T_MIN) <= ORC_T_MIN * bound) {
+                amb = 1;
+                if (nst == ORC_MAX_STOPS) {
+                    hard = 1;
+                } else {
+                    orc_stop *sp = &st[nst++];
+                    sp->T0 = T;
+                    sp->alpha = alpha;
+                    sp->bound = bound;
+                    sp->stopped = test < ORC_T_MIN;
+                    for (int ch = 0; ch < 3; ++ch) {
+                        sp->c[ch] = rgb[3 * g + ch];
+                        sp->C_before[ch] = C[ch];
+                    }
+                }
+            }
+            if (test < ORC_T_MIN) {
+                j_stop = j;
+                break;
+            }
+            t_err += eps;
         }
+        t_err += own_flip;
         if (uncertain) {
             if (nev == ORC_MAX_EVENTS) {
                 amb = hard = 1;
@@ -703,6 +752,28 @@ static void pixel_walk(double px, double py, int64_t start, int64_t end, const i
         const double effect = e->alpha * e->T0 * max_abs_diff3(e->c, R);
         allowance += effect;
         if (effect > mg->value_tol || mg->value_tol <= 0.0) amb = 1;
+    }
+    /* effect of each stop test near the threshold going the other way */
+    double c_later = -1.0;     /* largest |c - bg| after the stop entry */
+    for (int k = 0; k < nst; ++k) {
+        const orc_stop *sp = &st[k];
+        double effect;
+        if (!sp->stopped) {
+            effect = 0.0;
+            for (int ch = 0; ch < 3; ++ch)
+                effect = fmax(effect, fabs(C[ch] + T * bg[ch] - sp->C_before[ch] - sp->T0 * bg[ch]));
+        } else {
+            if (c_later < 0.0) {
+                c_later = 0.0;
+                for (int64_t j = j_stop + 1; j < end; ++j) {
+                    const uint8_t f = list_flags ? list_flags[j] : ORC_KEEP;
+                    if (f & ORC_KEEP) c_later = fmax(c_later, max_abs_diff3(rgb + 3 * list_gid[j], bg));
+                }
+            }
+            effect = sp->alpha * sp->T0 * max_abs_diff3(sp->c, bg) +
+                     sp->T0 * (1.0 - sp->alpha) * (1.0 + sp->bound) * c_later;
+        }
+        allowance += effect;
     }
     for (int ch = 0; ch < 3; ++ch) out->C[ch] = C[ch];
     out->T = T;
