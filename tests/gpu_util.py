@@ -117,24 +117,33 @@ def dilate_mask(m, r):
     return acc
 
 
-def gradient_mask(out, tol=IMAGE_TOL, dilate=0):
+def gradient_mask(out, target=None, tol=IMAGE_TOL, dilate=0):
     """Pixels whose dL/dC the gradient comparison zeroes on both sides: those
     with a decision float32 may take the other way whose effect on the value
-    is unbounded (the stop test near its threshold) or, summed, above the
+    is unbounded (overflow of the oracle's event lists) or, summed, above the
     image tolerance.  Elsewhere GPU and oracle values differ by at most the
-    tolerance plus a smaller allowance, which moves dL/dC -- here and in the
-    SSIM window around -- too little for the gradient bar, so no dilation is
-    needed."""
-    m = out["hard"].astype(bool) | (out["allowance"] > tol)
+    tolerance plus a smaller allowance, which moves the smooth part of dL/dC
+    -- here and in the SSIM window around -- too little for the gradient bar,
+    so no dilation is needed.  The L1 term is not smooth: its derivative is
+    the sign of (C - target), a decision float32 may take the other way
+    where |C - target| is within that bound; given the target, those pixels
+    are masked too (one flipped sign moves the gradients of the few Gaussians
+    on that pixel by several percent)."""
+    allow = out["allowance"]
+    m = out["hard"].astype(bool) | (allow > tol)
+    if target is not None:
+        near = np.abs(out["image"] - np.asarray(target, np.float64)) <= tol + allow[None]
+        m |= near.any(axis=0)
     return dilate_mask(m, dilate)
 
 
-def ambiguity_masks(cams, params, sh_degree=3, bg=(0.0, 0.0, 0.0), dilate=0):
-    """gradient_mask of the oracle's render of every view."""
+def ambiguity_masks(cams, params, sh_degree=3, bg=(0.0, 0.0, 0.0), dilate=0, targets=None):
+    """gradient_mask of the oracle's render of every view (with the L1 sign
+    decisions when the targets are given)."""
     masks = []
-    for cam in cams:
+    for v, cam in enumerate(cams):
         _, _, out = oracle.render(cam, params, sh_degree, bg, oracle.FP32_MARGINS)
-        masks.append(gradient_mask(out, dilate=dilate))
+        masks.append(gradient_mask(out, None if targets is None else targets[v], dilate=dilate))
     return masks
 
 

@@ -42,7 +42,7 @@ def test_dynamic_forward_matches_oracle(oracle_mod):
 def test_dynamic_gradients_match_oracle(oracle_mod):
     p, cams = _scene()
     targets = [scenes.target_image(c.width, c.height, view=i) for i, c in enumerate(cams)]
-    masks = ambiguity_masks(cams, p)
+    masks = ambiguity_masks(cams, p, targets=targets)
     Lg, gg, _ = gpu_grads(p, cams, targets, masks)
     Lo, go = oracle_grads(cams, p, targets, masks)
     assert Lg == pytest.approx(Lo, rel=1e-5)

@@ -9,7 +9,7 @@ FP64 oracle on the same seeded inputs: every view's image within 2e-4 plus
 the oracle's per-pixel allowance (pixels with an unbounded float32 decision
 excluded and counted), the batch loss, and every gradient tensor within 1e-3
 relative L2 (dL/dC zeroed on both sides where float32 decisions can move the
-value beyond the image tolerance; Gaussians whose footprint dwarfs the image
+value beyond the image tolerance or flip the sign of the L1 term; Gaussians whose footprint dwarfs the image
 excluded and counted).  The Adam update is checked by its first-step closed
 form: with bias correction, step 1 moves each parameter by
 -lr g / (|g| + eps)."""
@@ -69,7 +69,7 @@ def _oracle_batch(params, cams, targets):
         pre, lists, out = oracle.render(cam, params, 3, (0.0, 0.0, 0.0), oracle.FP32_MARGINS)
         L, dL = oracle.loss(out["image"], tgt, LAM, grad_scale=1.0 / len(cams))
         total += L / len(cams)
-        m = gradient_mask(out)
+        m = gradient_mask(out, tgt)
         dL[:, m] = 0.0
         sg = oracle.blend_backward(cam, pre, lists, dL)
         oracle.preprocess_backward(cam, params, sg, 3, grads)

@@ -51,7 +51,7 @@ def test_reduced_storage_render_and_gradients(oracle_mod, name, n):
     cams = crop_cameras(scenes.uneven_cameras())
     targets = [scenes.target_image(64, 64, view=i) for i in range(len(cams))]
     q = quantised(params, dt)
-    masks = ambiguity_masks(cams, q)
+    masks = ambiguity_masks(cams, q, targets=targets)
     tr = T.Trainer(params, cams, k_max=max(600_000, 4 * n), sh_dtype=dt, moment_dtype=dt)
     tr.set_targets(targets)
     tr.rast.forward(tr.p_s, 3, tr.bg, tr.images)
