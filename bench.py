@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-dynamic", action="store_true",
                     help="skip the dynamic (4D) workload: 600k Gaussians, 6 views per step")
+    ap.add_argument("--no-morton", action="store_true",
+                    help="keep the scene's generated order (default: z-order the Gaussians once "
+                         "before the timed steps, Sec. 3.3 locality-preserving densification)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
@@ -221,12 +224,14 @@ BLEND_FLOPS = {"blend_fwd": (12, 9), "blend_bwd": (12, 50)}
 
 
 # DRAM bytes per launch measured with ncu at the default workload (3M
-# Gaussians, one 1237x822 view; profiles/dram_outdoor_3M_1237x822.md), for
-# the roofline's "traffic" field.  Reported only for that workload and
-# launch configuration; a change to one of these kernels must refresh or drop
-# its entry.
-PROFILED_DRAM_BYTES = {"preprocess_bwd_adam": 4.644e9}
+# Gaussians in z-order, one 1237x822 view;
+# profiles/dram_outdoor_3M_1237x822.md), for the roofline's "traffic" field.
+# Reported only for that workload, order and launch configuration; a change
+# to one of these kernels must refresh or drop its entry.
+PROFILED_DRAM_BYTES = {}
 PROFILED_WORKLOAD = (3_000_000, 1237, 822)
+# the paper re-applies the z-order every 5000 iterations (Sec. 3.3)
+MORTON_PERIOD = 5000
 
 
 def fp32_peak_tflops(sm_count, sm_mhz):
@@ -281,6 +286,7 @@ def run_ours(args, dist):
 
     tr = T.Trainer(params, [cams[0]], k_max=k_max, lam=0.2)
     stream = torch.cuda.current_stream()
+    morton = None if args.no_morton else reorder_once(tr, stream)
     tuned = None
     if not args.no_tune:
         from paper_2602_09999_gb300 import tune
@@ -410,7 +416,8 @@ def run_ours(args, dist):
         elif alg is not None:
             achieved = alg / (avg_ms / 1000.0) / 1e9
             traffic = None
-            if (n, W, H) == PROFILED_WORKLOAD and dom in PROFILED_DRAM_BYTES:
+            if ((n, W, H) == PROFILED_WORKLOAD and not args.no_morton
+                    and dom in PROFILED_DRAM_BYTES):
                 traffic = PROFILED_DRAM_BYTES[dom]
             roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
                         "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
@@ -466,6 +473,8 @@ def run_ours(args, dist):
         tb = T.Trainer(params, cams[:Bv], k_max=int(k_max * Bv), lam=0.2,
                        sh_dtype=torch.bfloat16, moment_dtype=torch.bfloat16)
         tb.targets.copy_(targets[:Bv].reshape(-1)[:tb.targets.numel()])
+        if not args.no_morton:
+            reorder_once(tb, stream)
         tb_tuned = None
         if not args.no_tune:
             from paper_2602_09999_gb300 import tune
@@ -523,7 +532,27 @@ def run_ours(args, dist):
                 launches=(None if launches_per_step is None
                           else int(round(launches_per_step * args.steps))),
                 roofline=roofline, clocks=clocks, e2e=e2e, batched=batched, dynamic=dynamic,
-                k_max=k_max, instances_last=inst_last, visible_last=visible_est, n=n)
+                k_max=k_max, instances_last=inst_last, visible_last=visible_est, n=n,
+                morton=morton)
+
+
+def reorder_once(tr, stream):
+    """z-orders the trainer's Gaussians (the paper repeats this every few
+    thousand steps; here it is done once before the timed steps).  Returns
+    its device time, taken on a second call (the first one also allocates
+    the temporaries), and the time amortised over the paper's period."""
+    import torch
+    tr.reorder()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tr.reorder()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"reorder_ms": round(ms, 4), "ms_per_million": round(ms * 1e6 / tr.n, 4),
+            "period_steps": MORTON_PERIOD,
+            "amortised_ms_per_step": round(ms / MORTON_PERIOD, 6)}
 
 
 # ---------------------------------------------------------------------------
@@ -561,6 +590,8 @@ def run_dynamic(args, dist, stream, profile_pass, per_step_ms, n=600_000, views=
     torch.cuda.empty_cache()
     tr = T.Trainer(params, sets[0], k_max=int(kmax_seen * 1.25) + 4096, lam=0.2)
     tr.set_targets(targets)
+    if not args.no_morton:
+        reorder_once(tr, stream)
 
     def load(i):
         s = i % pool
@@ -651,6 +682,8 @@ def config_dict(args, n):
             "gaussians": n, "sh_degree": 3, "views_per_step": 1,
             "resolution": f"{args.width}x{args.height}",
             "l2": "inputs larger than L2: parameters + Adam state 2.8 GB vs 129 MB L2",
+            "gaussian_order": ("generated (random) order" if args.no_morton else
+                               "z-order (Sec. 3.3), applied once before the timed steps"),
             "parallelism": "replicas" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "single GPU"}
 
 
@@ -711,7 +744,8 @@ def main():
                 "gpu_launches": r["launches"], "roofline": r["roofline"], "cpu_baseline": cpu,
                 "batched": r["batched"], "dynamic": r["dynamic"], "blend_config": r["tuned"],
                 "blend_config_ms": r["tuning_ms"], "kernel_ms_per_step": r["phase_ms"],
-                "instances_last_step": r["instances_last"], "k_max": r["k_max"]}
+                "instances_last_step": r["instances_last"], "k_max": r["k_max"],
+                "morton": r["morton"]}
         print(json.dumps(line), flush=True)
         if args.phase_report:
             with open(args.phase_report, "w") as f:

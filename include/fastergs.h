@@ -319,6 +319,41 @@ int fgs_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t 
 #define FGS_STATIC_SORT_MAX_PAIRS (1 << 20)
 int fgs_sort_pairs_static(uint64_t *keys, uint32_t *vals, int64_t n, int32_t bits, void *stream);
 
+/* Locality-preserving order (Sec. 3.3 "Locality-preserving
+ * densification"): the z-order (Morton) permutation of the Gaussians, so
+ * that Gaussians close in 3D sit close in the parameter buffers.  The paper
+ * applies it every few thousand iterations; apply the permutation to every
+ * buffer indexed by Gaussian (parameters, Adam moments) with
+ * fgs_permute_params.
+ *
+ * means: [n,3] float32 (device), finite.  The bounding box [lo, hi] of the
+ * means is found on the device; each coordinate maps to 10 bits,
+ *   q_a = min(1023, floor((x_a - lo_a) * s_a)),  s_a = 1024 / (hi_a - lo_a)
+ * (s_a = 0 when hi_a == lo_a), evaluated in float32 with round-to-nearest
+ * and no fused multiply-add, so that the codes are reproducible bit for
+ * bit.  The code interleaves the bits: bit 3b + a of the code is bit b of
+ * q_a (a = 0, 1, 2 for x, y, z), 30 bits in all.
+ * order: [n] uint32 (device, output): order[i] is the index of the Gaussian
+ * at position i of the stable sort of the codes (equal codes keep index
+ * order).  codes: [n] uint32 (device, output) receiving the sorted codes,
+ * or NULL.  scratch: device buffer of fgs_morton_scratch_bytes(n) bytes,
+ * 256-byte aligned.  n == 0 is a no-op; n > 2^31 - 1 is FGS_ERR_SHAPE. */
+size_t fgs_morton_scratch_bytes(int64_t n);
+int fgs_morton_order(const float *means, int64_t n, uint32_t *order, uint32_t *codes,
+                     void *scratch, size_t scratch_bytes, void *stream);
+
+/* Gathers every group present in *src into *dst by a permutation:
+ * row i of each dst group = row order[i] of the src group (order: [n]
+ * uint32, device, a permutation of 0..n-1 as fgs_morton_order writes it),
+ * or row i itself when order is NULL (a plain copy).  Works for parameters
+ * and for Adam moments alike: any storage type, groups 0..5 always, 6 and 7
+ * both or neither; *dst must hold the same n, groups and types, and no dst
+ * group may share memory with its src group.  Rows of an index outside
+ * 0..n-1 are left unwritten (a bad order is the caller's bug; nothing
+ * faults). */
+int fgs_permute_params(const fgs_params *src, const fgs_params *dst, const uint32_t *order,
+                       void *stream);
+
 /* Synchronises `stream`, then reads the workspace header: sticky device
  * flags (FGS_FLAG_*) and the instance count of the last forward.  Either
  * output pointer may be NULL.  clear != 0 resets the flags afterwards. */

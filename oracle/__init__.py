@@ -417,3 +417,48 @@ def train_step(cams, params, targets, moments=None, step=1, sh_degree=3, lam=0.2
     if is_dynamic(params):
         new["sigma_t"] = params["sigma_t"]
     return total, images, grads, new, (m, v)
+
+
+# ---------------------------------------------------------------------------
+# Locality-preserving order (Sec. 3.3 "Locality-preserving densification"):
+# the z-order (Morton) permutation of the Gaussians' means.  An integer
+# result decided in floating point: the quantisation is taken in float32,
+# one rounding per operation, the precision the kernel decides it in (the
+# paper fixes none).  The means must be finite.
+# ---------------------------------------------------------------------------
+MORTON_BITS = 10
+
+
+def morton_quantise(means):
+    """Per axis a: q_a = min(1023, floor((x_a - lo_a) * s_a)) with
+    s_a = 1024 / (hi_a - lo_a) (0 when the box is flat along a), lo and hi
+    the bounding box of the means; every operation in float32."""
+    m = np.asarray(means, np.float32).reshape(-1, 3)
+    q = np.zeros(m.shape, np.int64)
+    if m.shape[0] == 0:
+        return q
+    top = (1 << MORTON_BITS) - 1
+    for a in range(3):
+        lo, hi = np.float32(m[:, a].min()), np.float32(m[:, a].max())
+        ext = np.float32(hi - lo)
+        s = np.float32(np.float32(1 << MORTON_BITS) / ext) if ext > 0 else np.float32(0.0)
+        v = (m[:, a] - lo) * s                         # float32 difference, then product
+        q[:, a] = np.clip(np.floor(v.astype(np.float64)), 0, top).astype(np.int64)
+    return q
+
+
+def morton_codes(means):
+    """The z-order code: bit b of q_x, q_y, q_z goes to bit 3b, 3b + 1 and
+    3b + 2 of the code (30 bits)."""
+    q = morton_quantise(means)
+    code = np.zeros(q.shape[0], np.int64)
+    for b in range(MORTON_BITS):
+        for a in range(3):
+            code |= ((q[:, a] >> b) & 1) << (3 * b + a)
+    return code.astype(np.uint32)
+
+
+def morton_order(means):
+    """Indices of the Gaussians in z-order; equal codes keep index order
+    (numpy's stable sort is the library sort step)."""
+    return np.argsort(morton_codes(means), kind="stable").astype(np.uint32)

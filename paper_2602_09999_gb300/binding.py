@@ -36,7 +36,8 @@ FGS_STATIC_SORT_MAX_PAIRS = 1 << 20
 EXPORTED = ("fgs_workspace_size", "fgs_render_forward", "fgs_loss_l1_dssim",
             "fgs_render_backward", "fgs_render_backward_adam", "fgs_adam_step",
             "fgs_adam_step_device",
-            "fgs_sort_scratch_bytes", "fgs_sort_pairs", "fgs_sort_pairs_static", "fgs_get_error",
+            "fgs_sort_scratch_bytes", "fgs_sort_pairs", "fgs_sort_pairs_static",
+            "fgs_morton_scratch_bytes", "fgs_morton_order", "fgs_permute_params", "fgs_get_error",
             "fgs_profile_attach",
             "fgs_profile_count", "fgs_strerror")
 
@@ -123,13 +124,18 @@ def lib():
             L.fgs_sort_scratch_bytes.restype = SZ
             L.fgs_sort_pairs.argtypes = [P, P, P, P, I64, I32, P, SZ, P, P]
             L.fgs_sort_pairs_static.argtypes = [P, P, I64, I32, P]
+            L.fgs_morton_scratch_bytes.argtypes = [I64]
+            L.fgs_morton_scratch_bytes.restype = SZ
+            L.fgs_morton_order.argtypes = [P, I64, P, P, P, SZ, P]
+            L.fgs_permute_params.argtypes = [P, P, P, P]
             L.fgs_get_error.argtypes = [P, P, P, I32, P]
             L.fgs_profile_attach.argtypes = [P, P, I32]
             L.fgs_profile_count.argtypes = []
             L.fgs_strerror.argtypes = [ctypes.c_int]
             L.fgs_strerror.restype = ctypes.c_char_p
             for name in EXPORTED:
-                if name not in ("fgs_sort_scratch_bytes", "fgs_strerror"):
+                if name not in ("fgs_sort_scratch_bytes", "fgs_morton_scratch_bytes",
+                                "fgs_strerror"):
                     getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -234,6 +240,23 @@ def fgs_sort_pairs_static(keys, vals, n, bits, stream):
     """In-place sort with the library's own scratch (no allocation)."""
     _check("fgs_sort_pairs_static",
            lib().fgs_sort_pairs_static(keys, vals, int(n), int(bits), stream))
+
+
+def fgs_morton_scratch_bytes(n) -> int:
+    return int(lib().fgs_morton_scratch_bytes(int(n)))
+
+
+def fgs_morton_order(means, n, order, codes, scratch, scratch_bytes, stream):
+    """z-order permutation of the means into `order` (and the sorted codes
+    into `codes`, unless it is None)."""
+    _check("fgs_morton_order",
+           lib().fgs_morton_order(means, int(n), order, codes, scratch, int(scratch_bytes), stream))
+
+
+def fgs_permute_params(src, dst, order, stream):
+    """dst rows = src rows taken in `order` (None: a plain copy)."""
+    _check("fgs_permute_params",
+           lib().fgs_permute_params(_ref(src), _ref(dst), order, stream))
 
 
 def fgs_get_error(ws, clear=False, stream=None):

@@ -309,6 +309,15 @@ int radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t*
                                   depth ? kDepthSortLabels : kSortLabels);
 }
 
+// 32-bit keys with the caller's profiling labels (the z-order sort).
+int radix_sort_u32_labeled(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                           int64_t n_max, const uint32_t* n_dev, int bits, uint32_t* hist,
+                           const char* const labels[3], cudaStream_t st, cudaError_t* err)
+{
+    return radix_sort_t<uint32_t>(keys, vals, keys_alt, vals_alt, n_max, n_dev, bits, hist, st, err,
+                                  labels);
+}
+
 cudaError_t launch_tile_ranges(const uint32_t* keys, const uint32_t* n_dev, int64_t n_max,
                                uint2* ranges, int total_tiles, cudaStream_t st)
 {

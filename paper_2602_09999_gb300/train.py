@@ -289,6 +289,27 @@ class Trainer:
         self.rast.loss(self.images, self.targets, self.lam, self.loss, self.dl)
         self.rast.backward(self.p_s, self.sh_degree, self.bg, self.dl, self.g_s)
 
+    def reorder(self) -> torch.Tensor:
+        """Puts the Gaussians in z-order (Sec. 3.3 "Locality-preserving
+        densification"; the paper repeats it every few thousand steps):
+        parameters, both Adam moments and the gradient buffers are permuted
+        in place, through a temporary and back, so every buffer keeps its
+        address and a captured graph stays valid.  Returns the order
+        (device int32): order[i] is the previous index of the Gaussian now
+        at i."""
+        s = current_stream()
+        n = self.n
+        order = torch.empty(n, dtype=torch.int32, device=self.device)
+        sb = B.fgs_morton_scratch_bytes(n)
+        scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
+        B.fgs_morton_order(self.params["means"].data_ptr(), n, order.data_ptr(), None,
+                           scratch.data_ptr(), sb, s)
+        for d in (self.params, self.exp_avg, self.exp_avg_sq, self.grads):
+            tmp = {k: torch.empty_like(d[k]) for k in self.groups}
+            B.fgs_permute_params(params_struct(d), params_struct(tmp), order.data_ptr(), s)
+            B.fgs_permute_params(params_struct(tmp), params_struct(d), None, s)
+        return order
+
     def adam_step_count(self) -> int:
         st = B.fgs_adam_state.from_buffer_copy(bytes(self.adam_state.cpu().numpy()))
         return int(st.step)

@@ -118,3 +118,43 @@ def test_null_pointer_checks_before_any_launch(lib):
         B.fgs_render_backward_adam(None, L, B.fgs_params(), 3, cam, None, (0, 0, 0), None,
                                    B.fgs_params(), B.fgs_params(), None, None, None)
     assert e.value.code == -1
+
+
+def _fake_params(n, base, dtypes=None, groups=6):
+    """fgs_params over fake, never dereferenced device addresses."""
+    ptrs = [base + (g << 32) for g in range(groups)]
+    return B.params_struct(n, ptrs, dtypes or [B.FGS_F32] * groups)
+
+
+def test_morton_and_permute_argument_checks(lib):
+    """Host checks of the z-order entry points, before any CUDA call."""
+    P = ctypes.c_void_p
+    sb = B.fgs_morton_scratch_bytes(1000)
+    assert sb >= 3 * 4 * 1000
+    assert lib.fgs_morton_order(None, 0, None, None, None, 0, None) == 0      # n = 0: no-op
+    assert lib.fgs_morton_order(None, -1, None, None, None, 0, None) == -2
+    assert lib.fgs_morton_order(None, 1000, None, None, None, sb, None) == -1
+    assert lib.fgs_morton_order(P(4096), 1000, P(8192), None, P(1 << 20), sb - 1, None) == -4
+    assert lib.fgs_morton_order(P(4096), 1000, P(8192), None, P((1 << 20) + 16), sb, None) == -8
+    src = _fake_params(10, 1 << 40)
+    dst = _fake_params(10, 1 << 44)
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_permute_params(B.params_struct(10, [0] * 6, [B.FGS_F32] * 6), dst, None, None)
+    assert e.value.code == -1
+    bad = _fake_params(10, 1 << 44, [B.FGS_F32] * 4 + [B.FGS_BF16] * 2)
+    with pytest.raises(B.FGSError) as e:                      # storage types differ
+        B.fgs_permute_params(src, bad, None, None)
+    assert e.value.code == -5
+    with pytest.raises(B.FGSError) as e:                      # dst overlaps src
+        B.fgs_permute_params(src, src, None, None)
+    assert e.value.code == -9
+    extra = _fake_params(10, 1 << 44, [B.FGS_F32] * 8, groups=8)
+    with pytest.raises(B.FGSError) as e:                      # dst has groups src lacks
+        B.fgs_permute_params(src, extra, None, None)
+    assert e.value.code == -9
+    short = _fake_params(9, 1 << 44)
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_permute_params(src, short, None, None)
+    assert e.value.code == -2
+    empty_src, empty_dst = _fake_params(0, 1 << 40), _fake_params(0, 1 << 44)
+    B.fgs_permute_params(empty_src, empty_dst, None, None)    # n = 0: no-op
