@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--no-morton", action="store_true",
                     help="keep the scene's generated order (default: z-order the Gaussians once "
                          "before the timed steps, Sec. 3.3 locality-preserving densification)")
+    ap.add_argument("--no-per-gaussian", action="store_true",
+                    help="skip timing the per-Gaussian blend backward (Sec. 3.2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
@@ -463,6 +465,48 @@ def run_ours(args, dist):
                "h2d_bytes_per_step": 3 * W * H * 4 + cam_bytes, "d2h_bytes_per_step": 4,
                "steps": steps_e2e}
 
+    # the per-Gaussian blend backward (Sec. 3.2), on the same workload and
+    # camera sequence: a second trainer whose workspace holds its bucket
+    # states, with the same launch choice
+    per_gaussian = None
+    if not args.no_per_gaussian:
+        tp = T.Trainer(params, [cams[0]], k_max=k_max, lam=0.2, per_gaussian=True)
+        if not args.no_morton:
+            reorder_once(tp, stream)
+        if tuned:
+            from paper_2602_09999_gb300 import tune
+            tune.apply(tp.rast.layout, tuned[0])
+
+        def pg_step(i):
+            tp.views.device.copy_(cam_table[(i % len(cams)) * cam_bytes:((i % len(cams)) + 1) * cam_bytes])
+            tp.targets.copy_(targets[i % n_targets])
+            tp.step()
+
+        for i in range(args.warmup):
+            pg_step(i)
+        pg_steps = min(args.steps, 100)
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        dist.barrier()
+        torch.cuda.synchronize()
+        q0.record(stream)
+        for i in range(pg_steps):
+            pg_step(args.warmup + i)
+        q1.record(stream)
+        q1.synchronize()
+        pg_ms = dist.max(q0.elapsed_time(q1)) / pg_steps
+        if tp.rast.error()[0]:
+            raise RuntimeError("capacity exceeded with the per-Gaussian backward")
+        per_gaussian = {"ms_per_step": round(pg_ms, 4),
+                        "views_per_s": round(dist.world * 1000.0 / pg_ms, 3),
+                        "per_pixel_ms_per_step": round(ms_per_step, 4),
+                        "ratio_vs_per_pixel": round(ms_per_step / pg_ms, 4), "steps": pg_steps}
+        if not args.no_profile:
+            ph, _ = profile_pass(pg_step, args.warmup + pg_steps, 20)
+            per_gaussian["kernel_ms_per_step"] = per_step_ms(ph, 20)
+        del tp
+        torch.cuda.empty_cache()
+
     # batched variants: B views per step, CUDA graph, bf16 SH and moments
     batched = []
     if not args.no_batched:
@@ -533,7 +577,7 @@ def run_ours(args, dist):
                           else int(round(launches_per_step * args.steps))),
                 roofline=roofline, clocks=clocks, e2e=e2e, batched=batched, dynamic=dynamic,
                 k_max=k_max, instances_last=inst_last, visible_last=visible_est, n=n,
-                morton=morton)
+                morton=morton, per_gaussian=per_gaussian)
 
 
 def reorder_once(tr, stream):
@@ -745,7 +789,7 @@ def main():
                 "batched": r["batched"], "dynamic": r["dynamic"], "blend_config": r["tuned"],
                 "blend_config_ms": r["tuning_ms"], "kernel_ms_per_step": r["phase_ms"],
                 "instances_last_step": r["instances_last"], "k_max": r["k_max"],
-                "morton": r["morton"]}
+                "morton": r["morton"], "per_gaussian_backward": r["per_gaussian"]}
         print(json.dumps(line), flush=True)
         if args.phase_report:
             with open(args.phase_report, "w") as f:

@@ -143,6 +143,15 @@ enum fgs_ws_slot {
     FGS_WS_DEPTH_VALS_ALT,
     FGS_WS_SORTED_OFF,  /* uint32 [n_views*n]: instance offsets in depth order (CTA-local) */
     FGS_WS_SORTED_BLOCK, /* uint32 [ceil(n_views*n/512)+1]: prefix of those CTA totals */
+    /* per-Gaussian backward only (FGS_WS_PER_GAUSSIAN; empty otherwise).  A bucket is 32
+       consecutive entries of one tile's list; buckets are numbered tile by tile. */
+    FGS_WS_BUCKET_OFF,   /* uint32 [total_tiles+1]: first bucket of each tile; the last entry
+                            holds the number of buckets */
+    FGS_WS_BUCKET_TILE,  /* uint32 [k_max/32 + total_tiles]: tile of each bucket */
+    FGS_WS_BUCKET_STATE, /* float4 [256 per bucket]: (T, C.r, C.g, C.b) of each pixel of the
+                            tile in front of the bucket's first entry, written by the forward
+                            for the pixels still blending there (pixel ly*16 + lx) */
+    FGS_WS_PIXEL_FINAL,  /* float4 [total_pixels]: output colour C + T bg of each pixel */
     FGS_WS_NUM_SLOTS
 };
 
@@ -151,13 +160,29 @@ enum fgs_ws_slot {
  * list entries staged per shared-memory batch (64, 128 or 256).  Supported
  * pairs: (1,256) (2,128) (2,256) (4,64) (4,128) (4,256).  fgs_workspace_size
  * fills the defaults; an autotuner may overwrite them in the layout before
- * the calls that use it. */
+ * the calls that use it.  The forward and the backward that share a
+ * workspace must run with the same choices. */
 typedef struct fgs_tuning {
     int32_t blend_pixels_per_thread;
     int32_t blend_batch;
     int32_t blend_schedule;  /* FGS_SCHEDULE_QUEUE (default) or FGS_SCHEDULE_GRID */
-    int32_t reserved[5];
+    int32_t blend_backward;  /* FGS_BACKWARD_PER_PIXEL (default) or FGS_BACKWARD_PER_GAUSSIAN */
+    int32_t reserved[4];
 } fgs_tuning;
+
+/* Order of the blend backward (the same gradients up to float32 rounding).
+ * PER_PIXEL: one thread per pixel walks its tile's list back to front,
+ * recovering T by division; per-fragment gradients are summed over the warp
+ * and the CTA before one set of atomics per (entry, CTA).  PER_GAUSSIAN
+ * (Sec. 3.2 "Per-Gaussian Backward", after Mallick et al.): the list is cut
+ * into buckets of 32 entries, one warp per bucket and one lane per entry;
+ * starting from each pixel's (T, C) in front of the bucket, stored by the
+ * forward, the lanes replay the blend front to back, passing the state from
+ * lane to lane with shuffles, and each lane adds its entry's gradient with
+ * one set of atomics per bucket.  Pixel states are staged per warp in
+ * shared memory, 32 at a time (the paper's refinement).  Needs a workspace
+ * made with FGS_WS_PER_GAUSSIAN. */
+enum { FGS_BACKWARD_PER_PIXEL = 0, FGS_BACKWARD_PER_GAUSSIAN = 1 };
 
 /* How the blend kernels visit tiles.  QUEUE: one resident CTA set per SM
  * (SMs x occupancy CTAs) takes tiles from a work queue, longest list first
@@ -176,6 +201,7 @@ typedef struct fgs_workspace_layout {
     int64_t total_pixels;
     int32_t sort_bits;       /* tile-id bits the tile sort orders (the depth sort: 32) */
     int32_t sorted_in_alt;   /* 1: the tile-sorted keys/values end in the *_ALT slots */
+    int32_t flags;           /* the FGS_WS_* options the layout was made with */
     fgs_tuning tuning;       /* launch choices (defaults filled in) */
 } fgs_workspace_layout;
 
@@ -190,6 +216,14 @@ typedef struct fgs_workspace_layout {
  * outside 1..65535, k_max outside 0..2^31-1). */
 int fgs_workspace_size(int64_t n, const fgs_camera *cams_host, int32_t n_views, int64_t k_max,
                        fgs_workspace_layout *out_host);
+
+/* The same with options: flags & FGS_WS_PER_GAUSSIAN also reserves the
+ * buffers of the per-Gaussian backward (4 KB of pixel states per bucket of
+ * 32 instances: about 128 k_max + 4096 total_tiles bytes more).
+ * fgs_workspace_size(...) is fgs_workspace_size_ex(..., 0, ...). */
+enum { FGS_WS_PER_GAUSSIAN = 1 };
+int fgs_workspace_size_ex(int64_t n, const fgs_camera *cams_host, int32_t n_views, int64_t k_max,
+                          int32_t flags, fgs_workspace_layout *out_host);
 
 /* Forward pass for layout->n_views views (Eq. 1-4; Sec. 3.2 bounds, culling and
  * sorting; Suppl. B.1 clamp, early stop and degeneracy tests):

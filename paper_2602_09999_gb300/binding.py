@@ -26,14 +26,16 @@ FGS_FLAG_CAPACITY = 1
  FGS_WS_VALS, FGS_WS_KEYS_ALT, FGS_WS_VALS_ALT, FGS_WS_SORT_HIST, FGS_WS_RANGES, FGS_WS_T_FINAL,
  FGS_WS_N_CONTRIB, FGS_WS_SCREEN_GRAD, FGS_WS_LOSS_MAPS, FGS_WS_LOSS_PART, FGS_WS_N_BLENDED,
  FGS_WS_TILE_QUEUE, FGS_WS_DEPTH_KEYS, FGS_WS_DEPTH_VALS, FGS_WS_DEPTH_KEYS_ALT,
- FGS_WS_DEPTH_VALS_ALT, FGS_WS_SORTED_OFF, FGS_WS_SORTED_BLOCK, FGS_WS_NUM_SLOTS) = range(25)
+ FGS_WS_DEPTH_VALS_ALT, FGS_WS_SORTED_OFF, FGS_WS_SORTED_BLOCK, FGS_WS_BUCKET_OFF,
+ FGS_WS_BUCKET_TILE, FGS_WS_BUCKET_STATE, FGS_WS_PIXEL_FINAL, FGS_WS_NUM_SLOTS) = range(29)
+FGS_WS_PER_GAUSSIAN = 1
 
 STATUS = {0: "FGS_OK", -1: "FGS_ERR_NULL", -2: "FGS_ERR_SHAPE", -3: "FGS_ERR_SH_DEGREE",
           -4: "FGS_ERR_WORKSPACE", -5: "FGS_ERR_DTYPE", -6: "FGS_ERR_CUDA", -7: "FGS_ERR_VIEWS",
           -8: "FGS_ERR_ALIGN", -9: "FGS_ERR_ARG", -10: "FGS_ERR_TOO_LARGE"}
 FGS_STATIC_SORT_MAX_PAIRS = 1 << 20
 
-EXPORTED = ("fgs_workspace_size", "fgs_render_forward", "fgs_loss_l1_dssim",
+EXPORTED = ("fgs_workspace_size", "fgs_workspace_size_ex", "fgs_render_forward", "fgs_loss_l1_dssim",
             "fgs_render_backward", "fgs_render_backward_adam", "fgs_adam_step",
             "fgs_adam_step_device",
             "fgs_sort_scratch_bytes", "fgs_sort_pairs", "fgs_sort_pairs_static",
@@ -64,12 +66,14 @@ class fgs_params(ctypes.Structure):
 
 class fgs_tuning(ctypes.Structure):
     _fields_ = [("blend_pixels_per_thread", ctypes.c_int32), ("blend_batch", ctypes.c_int32),
-                ("blend_schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("blend_schedule", ctypes.c_int32), ("blend_backward", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 BLEND_CONFIGS = ((1, 256), (2, 128), (2, 256), (4, 64), (4, 128), (4, 256))
 FGS_SCHEDULE_QUEUE, FGS_SCHEDULE_GRID = 0, 1
 BLEND_SCHEDULES = (FGS_SCHEDULE_QUEUE, FGS_SCHEDULE_GRID)
+FGS_BACKWARD_PER_PIXEL, FGS_BACKWARD_PER_GAUSSIAN = 0, 1
 
 
 class fgs_workspace_layout(ctypes.Structure):
@@ -79,7 +83,8 @@ class fgs_workspace_layout(ctypes.Structure):
                 ("n", ctypes.c_int64), ("k_max", ctypes.c_int64),
                 ("n_views", ctypes.c_int32), ("total_tiles", ctypes.c_int32),
                 ("total_pixels", ctypes.c_int64), ("sort_bits", ctypes.c_int32),
-                ("sorted_in_alt", ctypes.c_int32), ("tuning", fgs_tuning)]
+                ("sorted_in_alt", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("tuning", fgs_tuning)]
 
 
 class fgs_adam_state(ctypes.Structure):
@@ -113,6 +118,7 @@ def lib():
             L = ctypes.CDLL(path)
             P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
             L.fgs_workspace_size.argtypes = [I64, P, I32, I64, P]
+            L.fgs_workspace_size_ex.argtypes = [I64, P, I32, I64, I32, P]
             L.fgs_render_forward.argtypes = [P, P, P, I32, P, P, P, P, P]
             L.fgs_loss_l1_dssim.argtypes = [P, P, P, P, P, ctypes.c_float, P, P, P]
             L.fgs_render_backward.argtypes = [P, P, P, I32, P, P, P, P, P, P]
@@ -172,6 +178,14 @@ def fgs_workspace_size(n, cams_host, n_views, k_max) -> fgs_workspace_layout:
     out = fgs_workspace_layout()
     _check("fgs_workspace_size",
            lib().fgs_workspace_size(int(n), cams_host, int(n_views), int(k_max), ctypes.byref(out)))
+    return out
+
+
+def fgs_workspace_size_ex(n, cams_host, n_views, k_max, flags) -> fgs_workspace_layout:
+    out = fgs_workspace_layout()
+    _check("fgs_workspace_size_ex",
+           lib().fgs_workspace_size_ex(int(n), cams_host, int(n_views), int(k_max), int(flags),
+                                       ctypes.byref(out)))
     return out
 
 

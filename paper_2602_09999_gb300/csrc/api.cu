@@ -36,7 +36,14 @@ cudaError_t launch_tile_order(const uint2* ranges, int total_tiles, uint32_t* qu
 cudaError_t launch_blend_fwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                              const Screen* screen, const float bg[3], float* images, float* T_final,
                              uint32_t* n_contrib, uint32_t* n_blended, uint32_t* queue, int ppt, int batch,
-                             int schedule, cudaStream_t st);
+                             int schedule, uint32_t* pg_bucket_off, uint32_t* pg_bucket_tile,
+                             float4* pg_state, float4* pg_pixel_final, int64_t pg_max_buckets,
+                             cudaStream_t st);
+cudaError_t launch_blend_bwd_pg(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
+                                const Screen* screen, const float* dL_dimg, const uint32_t* n_contrib,
+                                uint32_t* pg_bucket_off, uint32_t* pg_bucket_tile, float4* pg_state,
+                                float4* pg_pixel_final, int64_t pg_max_buckets, ScreenGrad* sgrad,
+                                cudaStream_t st);
 cudaError_t launch_blend_bwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                              const Screen* screen, const float bg[3], const float* dL_dimg,
                              const float* T_final, const uint32_t* n_contrib, ScreenGrad* sgrad,
@@ -138,12 +145,20 @@ static int sort_bits_for(int64_t total_tiles)
 // The depth sort orders all 32 bits of the (positive) float depths.
 static const int kDepthBits = 32;
 
-static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_max,
+// Buckets of 32 list entries the per-Gaussian backward can meet: every
+// instance in one, plus a partial bucket per tile.
+static int64_t max_buckets_for(int64_t k_max, int64_t total_tiles)
+{
+    return (k_max + 31) / 32 + total_tiles;
+}
+
+static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_max, int32_t flags,
                        fgs_workspace_layout* L, ViewTable* vt)
 {
     if (!L) return FGS_ERR_NULL;
     if (n < 1 || n > 0x7fffffffll) return FGS_ERR_SHAPE;
     if (k_max < 0 || k_max > 0x7fffffffll) return FGS_ERR_ARG;
+    if (flags & ~FGS_WS_PER_GAUSSIAN) return FGS_ERR_ARG;
     const int rc = build_views(cams, nv, vt);
     if (rc != FGS_OK) return rc;
     memset(L, 0, sizeof(*L));
@@ -174,6 +189,12 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     sz[FGS_WS_DEPTH_VALS_ALT] = sizeof(uint32_t) * (size_t)vn;
     sz[FGS_WS_SORTED_OFF] = sizeof(uint32_t) * (size_t)vn;
     sz[FGS_WS_SORTED_BLOCK] = sizeof(uint32_t) * (size_t)(count_scan_blocks(vn) + 1);
+    const bool pg = flags & FGS_WS_PER_GAUSSIAN;
+    const int64_t mb = max_buckets_for(k_max, vt->total_tiles);
+    sz[FGS_WS_BUCKET_OFF] = pg ? sizeof(uint32_t) * ((size_t)vt->total_tiles + 1) : 0;
+    sz[FGS_WS_BUCKET_TILE] = pg ? sizeof(uint32_t) * (size_t)mb : 0;
+    sz[FGS_WS_BUCKET_STATE] = pg ? sizeof(float4) * (size_t)kTilePixels * (size_t)mb : 0;
+    sz[FGS_WS_PIXEL_FINAL] = pg ? sizeof(float4) * (size_t)vt->total_pixels : 0;
     size_t off = 0;
     for (int s = 0; s < FGS_WS_NUM_SLOTS; ++s) {
         L->offset[s] = off;
@@ -188,6 +209,7 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     L->total_pixels = vt->total_pixels;
     L->sort_bits = sort_bits_for(vt->total_tiles);
     L->sorted_in_alt = ((L->sort_bits + 7) / 8) & 1;
+    L->flags = flags;
     L->tuning.blend_pixels_per_thread = kDefaultPPT;
     L->tuning.blend_batch = kDefaultBatch;
     L->tuning.blend_schedule = FGS_SCHEDULE_QUEUE;
@@ -200,7 +222,7 @@ static int check_layout(void* ws, const fgs_workspace_layout* L, const fgs_camer
     if (!ws || !L || !cams) return FGS_ERR_NULL;
     if ((uintptr_t)ws % 256 != 0) return FGS_ERR_ALIGN;
     fgs_workspace_layout mine;
-    const int rc = layout_impl(L->n, cams, L->n_views, L->k_max, &mine, vt);
+    const int rc = layout_impl(L->n, cams, L->n_views, L->k_max, L->flags, &mine, vt);
     if (rc != FGS_OK) return rc;
     if (memcmp(mine.offset, L->offset, sizeof(mine.offset)) != 0 || mine.total_bytes != L->total_bytes)
         return FGS_ERR_WORKSPACE;
@@ -208,6 +230,11 @@ static int check_layout(void* ws, const fgs_workspace_layout* L, const fgs_camer
         return FGS_ERR_ARG;
     if (L->tuning.blend_schedule != FGS_SCHEDULE_QUEUE && L->tuning.blend_schedule != FGS_SCHEDULE_GRID)
         return FGS_ERR_ARG;
+    if (L->tuning.blend_backward != FGS_BACKWARD_PER_PIXEL &&
+        L->tuning.blend_backward != FGS_BACKWARD_PER_GAUSSIAN)
+        return FGS_ERR_ARG;
+    if (L->tuning.blend_backward == FGS_BACKWARD_PER_GAUSSIAN && !(L->flags & FGS_WS_PER_GAUSSIAN))
+        return FGS_ERR_WORKSPACE;
     return FGS_OK;
 }
 
@@ -249,7 +276,14 @@ int fgs_workspace_size(int64_t n, const fgs_camera* cams_host, int32_t n_views, 
                        fgs_workspace_layout* out_host)
 {
     ViewTable vt;
-    return layout_impl(n, cams_host, n_views, k_max, out_host, &vt);
+    return layout_impl(n, cams_host, n_views, k_max, 0, out_host, &vt);
+}
+
+int fgs_workspace_size_ex(int64_t n, const fgs_camera* cams_host, int32_t n_views, int64_t k_max,
+                          int32_t flags, fgs_workspace_layout* out_host)
+{
+    ViewTable vt;
+    return layout_impl(n, cams_host, n_views, k_max, flags, out_host, &vt);
 }
 
 int fgs_render_forward(void* ws, const fgs_workspace_layout* L, const fgs_params* params,
@@ -310,12 +344,18 @@ int fgs_render_forward(void* ws, const fgs_workspace_layout* L, const fgs_params
     if (L->tuning.blend_schedule == FGS_SCHEDULE_QUEUE &&
         (rc = cuda_rc(launch_tile_order(ranges, vt.total_tiles, queue, st))) != FGS_OK)
         return rc;
+    const bool pg = L->tuning.blend_backward == FGS_BACKWARD_PER_GAUSSIAN;
     return cuda_rc(launch_blend_fwd(vt, n, ranges, svals, screen, bg, images,
                                     slot<float>(ws, L, FGS_WS_T_FINAL),
                                     slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB),
                                     slot<uint32_t>(ws, L, FGS_WS_N_BLENDED), queue,
                                     L->tuning.blend_pixels_per_thread, L->tuning.blend_batch,
-                                    L->tuning.blend_schedule, st));
+                                    L->tuning.blend_schedule,
+                                    pg ? slot<uint32_t>(ws, L, FGS_WS_BUCKET_OFF) : nullptr,
+                                    pg ? slot<uint32_t>(ws, L, FGS_WS_BUCKET_TILE) : nullptr,
+                                    pg ? slot<float4>(ws, L, FGS_WS_BUCKET_STATE) : nullptr,
+                                    pg ? slot<float4>(ws, L, FGS_WS_PIXEL_FINAL) : nullptr,
+                                    max_buckets_for(L->k_max, vt.total_tiles), st));
 }
 
 int fgs_loss_l1_dssim(void* ws, const fgs_workspace_layout* L, const fgs_camera* cams_host,
@@ -344,6 +384,14 @@ static int backward_blend(void* ws, const fgs_workspace_layout* L, const ViewTab
     ScreenGrad* sgrad = slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD);
     if (cudaMemsetAsync(sgrad, 0, L->bytes[FGS_WS_SCREEN_GRAD], st) != cudaSuccess) return FGS_ERR_CUDA;
     profile_mark(st, "zero_screen_grads");
+    if (L->tuning.blend_backward == FGS_BACKWARD_PER_GAUSSIAN)
+        return cuda_rc(launch_blend_bwd_pg(vt, n, slot<uint2>(ws, L, FGS_WS_RANGES), svals, screen, dl_dimages,
+                                           slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB),
+                                           slot<uint32_t>(ws, L, FGS_WS_BUCKET_OFF),
+                                           slot<uint32_t>(ws, L, FGS_WS_BUCKET_TILE),
+                                           slot<float4>(ws, L, FGS_WS_BUCKET_STATE),
+                                           slot<float4>(ws, L, FGS_WS_PIXEL_FINAL),
+                                           max_buckets_for(L->k_max, vt.total_tiles), sgrad, st));
     return cuda_rc(launch_blend_bwd(vt, n, slot<uint2>(ws, L, FGS_WS_RANGES), svals, screen, bg, dl_dimages,
                                     slot<float>(ws, L, FGS_WS_T_FINAL),
                                     slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB), sgrad,

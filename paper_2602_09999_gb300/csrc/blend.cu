@@ -21,6 +21,19 @@
 // per-fragment gradients are summed over the warp with shuffles, over the
 // CTA with shared-memory atomics, and leave the CTA as one set of global
 // vector atomics per (instance, CTA).
+//
+// Per-Gaussian backward (Sec. 3.2 "Per-Gaussian Backward" and its details in
+// the supplement, after Mallick et al.), selected by fgs_tuning: each tile's
+// list is cut into buckets of 32 entries.  The forward also stores, for every
+// pixel still blending there, (T, C) in front of each bucket's first entry.
+// The backward runs one warp per bucket, lane j holding entry j: the lanes
+// replay the blend front to back as a pipeline over the tile's pixels that
+// are still active at the bucket (at step s lane j works on pixel s - j and
+// hands (T, C) to lane j + 1 with shuffles); the colour behind entry j is
+// R_j = (C_pixel - C_{<=j}) / T_{j+1}, and each lane sums its entry's
+// gradients over the pixels in registers, then adds them with one set of
+// atomics per bucket.  Per-pixel inputs are staged in shared memory 32
+// pixels at a time by the whole warp (the paper's refinement).
 #include "fgs_common.cuh"
 
 namespace fgs {
@@ -135,6 +148,42 @@ __device__ __forceinline__ bool eval_frag(float px, float py, const Entry& e, Fr
     return f.alpha >= kAlphaMin;
 }
 
+// Adds the screen-space gradients of one blended fragment to d[9]: dL/dmu2D
+// (2), dL/dSigma2D (H00, H01, H11 of the full symmetric gradient), dL/do and
+// dL/drgb, given dL/dalpha, wT = alpha T and the pixel's dL/dC.
+__device__ __forceinline__ void frag_grads(const Entry& e, const Frag& f, float u, float w, float dalpha,
+                                           float wT, float g0, float g1, float g2, float d[9])
+{
+    d[6] += wT * g0;
+    d[7] += wT * g1;
+    d[8] += wT * g2;
+    if (!f.clamped) {
+        // power = -q/2 with q = d^T C d; C d = ls u e + lb w e_perp from
+        // the eigen form (no cancellation) = 2 ln 2 (vx, vy) below
+        const float dpow = dalpha * f.alpha;  // alpha = o G here
+        const float vx = e.coef.x * u - e.coef.w * w;
+        const float vy = e.coef.y * u + e.coef.z * w;
+        d[5] += dalpha * f.G;
+        const float dk = dpow * kTwoLn2;
+        d[0] += dk * vx;  // dL/dmu = dpow C d
+        d[1] += dk * vy;
+        // dL/dSigma (full symmetric) = -C (dL/dC) C = dpow (C d)(C d)^T / 2
+        const float hx = dpow * (0.5f * kTwoLn2 * kTwoLn2) * vx;
+        d[2] += hx * vx;
+        d[3] += hx * vy;
+        d[4] += dpow * (0.5f * kTwoLn2 * kTwoLn2) * vy * vy;
+    }
+}
+
+// Buffers of the per-Gaussian backward (state == nullptr: not in use).
+struct PgBuffers {
+    const uint32_t* bucket_off;  // [total_tiles + 1]
+    uint32_t* bucket_tile;       // [max_buckets]
+    float4* state;               // [max_buckets * 256]
+    float4* pixel_final;         // [total_pixels]: the pixel's output colour (C + T bg)
+    int64_t max_buckets;
+};
+
 // Tile scheduling.  With a queue (head != nullptr) the CTAs of a resident
 // grid take the next entry of `order` (tiles by descending list length) until
 // it is exhausted, and the last CTA out zeroes the counters for the next
@@ -206,13 +255,13 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restric
 }
 
 // Forward of one tile (the whole CTA): front-to-back blending of its list.
-template <int PPT, int BATCH>
+template <int PPT, int BATCH, bool CKPT>
 __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, const uint2* __restrict__ ranges,
                                                const uint32_t* __restrict__ gids,
                                                const Screen* __restrict__ screen, float bg0, float bg1,
                                                float bg2, float* __restrict__ images,
                                                float* __restrict__ T_final, uint32_t* __restrict__ n_contrib,
-                                               uint32_t* __restrict__ n_blended, int tile)
+                                               uint32_t* __restrict__ n_blended, const PgBuffers& pg, int tile)
 {
     using Map = TileMap<PPT>;
     __shared__ Entry s_e[BATCH];
@@ -232,6 +281,8 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
         blended[k] = 0;
         done[k] = !tm.inside[k];
     }
+    const int64_t bucket0 = CKPT ? (int64_t)pg.bucket_off[tile] : 0;
+    float4* ckpt = CKPT ? pg.state + bucket0 * kTilePixels : nullptr;
     for (uint32_t start = range.x; start < range.y; start += BATCH) {
         bool all_done = true;
 #pragma unroll
@@ -248,6 +299,14 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
         __syncthreads();
         const int cnt = (int)min((uint32_t)BATCH, range.y - start);
         for (int jj = 0; jj < cnt && !all_done; ++jj) {
+            if (CKPT && (jj & 31) == 0 && bucket0 + ((start - range.x + jj) >> 5) < pg.max_buckets) {
+                // (T, C) in front of a bucket's first entry (BATCH is a multiple of 32)
+                float4* st = ckpt + (int64_t)((start - range.x + jj) >> 5) * kTilePixels;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    if (!done[k])
+                        st[(tm.py[k] - tm.y0) * kTile + (tm.px[k] - tm.x0)] = make_float4(T[k], C0[k], C1[k], C2[k]);
+            }
             const uint32_t wm = ((uint32_t)s_mask[jj] >> (warp * PPT)) & ((1u << PPT) - 1u);
             if (!wm) continue;  // uniform over the warp
             const Entry e = s_e[jj];
@@ -259,15 +318,16 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
                 float u, w;
                 if (((wm >> k) & 1u) &&
                     eval_frag((float)tm.px[k] + 0.5f, (float)tm.py[k] + 0.5f, e, f, u, w)) {
-                    const float test = T[k] * (1.0f - f.alpha);
+                    const float test = __fmul_rn(T[k], __fsub_rn(1.0f, f.alpha));
                     if (test < kTMin) {
                         done[k] = true;
                         continue;
                     }
-                    const float wt = f.alpha * T[k];
-                    C0[k] += wt * e.rgbo.x;
-                    C1[k] += wt * e.rgbo.y;
-                    C2[k] += wt * e.rgbo.z;
+                    // explicit roundings: the per-Gaussian backward replays these exactly
+                    const float wt = __fmul_rn(f.alpha, T[k]);
+                    C0[k] = __fmaf_rn(wt, e.rgbo.x, C0[k]);
+                    C1[k] = __fmaf_rn(wt, e.rgbo.y, C1[k]);
+                    C2[k] = __fmaf_rn(wt, e.rgbo.z, C2[k]);
                     T[k] = test;
                     last[k] = start + jj - range.x + 1;
                     ++blended[k];
@@ -282,27 +342,30 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
     for (int k = 0; k < PPT; ++k) {
         if (!tm.inside[k]) continue;
         const int64_t pix = (int64_t)tm.py[k] * tm.W + tm.px[k];
-        img[pix] = C0[k] + T[k] * bg0;
-        img[P + pix] = C1[k] + T[k] * bg1;
-        img[2 * P + pix] = C2[k] + T[k] * bg2;
+        const float o0 = C0[k] + T[k] * bg0, o1 = C1[k] + T[k] * bg1, o2 = C2[k] + T[k] * bg2;
+        img[pix] = o0;
+        img[P + pix] = o1;
+        img[2 * P + pix] = o2;
+        if (CKPT) pg.pixel_final[vt.pix_off[tm.v] + pix] = make_float4(o0, o1, o2, 0.0f);
         T_final[vt.pix_off[tm.v] + pix] = T[k];
         n_contrib[vt.pix_off[tm.v] + pix] = last[k];
         n_blended[vt.pix_off[tm.v] + pix] = blended[k];
     }
 }
 
-template <int PPT, int BATCH>
+template <int PPT, int BATCH, bool CKPT>
 __global__ void __launch_bounds__(kTilePixels / PPT)
 blend_fwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
                  const uint32_t* __restrict__ gids, const Screen* __restrict__ screen, float bg0,
                  float bg1, float bg2, float* __restrict__ images, float* __restrict__ T_final,
-                 uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ n_blended, TileSched sched)
+                 uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ n_blended, TileSched sched,
+                 PgBuffers pg)
 {
     __shared__ uint32_t s_slot;
     int iter = 0;
     for (int tile; (tile = sched_next(sched, vt.total_tiles, iter, s_slot)) >= 0;)
-        blend_fwd_tile<PPT, BATCH>(vt, n, ranges, gids, screen, bg0, bg1, bg2, images, T_final, n_contrib,
-                                   n_blended, tile);
+        blend_fwd_tile<PPT, BATCH, CKPT>(vt, n, ranges, gids, screen, bg0, bg1, bg2, images, T_final,
+                                         n_contrib, n_blended, pg, tile);
 }
 
 __device__ __forceinline__ float warp_sum(float x)
@@ -434,30 +497,11 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
                 // the colour behind, A <- A + alpha (c - A)
                 const float c0 = e.rgbo.x - A0[k], c1 = e.rgbo.y - A1[k], c2 = e.rgbo.z - A2[k];
                 const float dalpha = Ti * (g0[k] * c0 + g1[k] * c1 + g2[k] * c2);
-                const float wT = f.alpha * Ti;
-                d[6] += wT * g0[k];
-                d[7] += wT * g1[k];
-                d[8] += wT * g2[k];
+                frag_grads(e, f, u, w, dalpha, f.alpha * Ti, g0[k], g1[k], g2[k], d);
                 A0[k] += f.alpha * c0;
                 A1[k] += f.alpha * c1;
                 A2[k] += f.alpha * c2;
                 T[k] = Ti;
-                if (!f.clamped) {
-                    // power = -q/2 with q = d^T C d; C d = ls u e + lb w e_perp from
-                    // the eigen form (no cancellation) = 2 ln 2 (vx, vy) below
-                    const float dpow = dalpha * f.alpha;  // alpha = o G here
-                    const float vx = e.coef.x * u - e.coef.w * w;
-                    const float vy = e.coef.y * u + e.coef.z * w;
-                    d[5] += dalpha * f.G;
-                    const float dk = dpow * kTwoLn2;
-                    d[0] += dk * vx;  // dL/dmu = dpow C d
-                    d[1] += dk * vy;
-                    // dL/dSigma (full symmetric) = -C (dL/dC) C = dpow (C d)(C d)^T / 2
-                    const float hx = dpow * (0.5f * kTwoLn2 * kTwoLn2) * vx;
-                    d[2] += hx * vx;
-                    d[3] += hx * vy;
-                    d[4] += dpow * (0.5f * kTwoLn2 * kTwoLn2) * vy * vy;
-                }
             }
             if (!__any_sync(0xffffffffu, any)) continue;
             // value index of lane l after the scatter: (l >> 2) & 7
@@ -500,6 +544,189 @@ blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
                                    sgrad, tile);
 }
 
+// ---------------------------------------------------------------------------
+// Per-Gaussian backward
+// ---------------------------------------------------------------------------
+constexpr int kBucket = 32;             // entries per bucket (one per lane)
+constexpr int kPgWarps = 8;             // buckets in flight per CTA
+constexpr int kScanThreads = 1024;
+
+// One CTA: bucket_off[t] = sum over tiles u < t of ceil(len_u / 32),
+// bucket_off[total] = the number of buckets, and bucket_tile[b] = the tile
+// of bucket b.  Buckets beyond max_buckets (more instances than the
+// workspace was sized for, which the capacity flag already reports) are
+// dropped by clamping the offsets.
+__global__ void __launch_bounds__(kScanThreads)
+bucket_scan_kernel(const uint2* __restrict__ ranges, int total, uint32_t* __restrict__ bucket_off,
+                   uint32_t* __restrict__ bucket_tile, uint32_t max_buckets)
+{
+    __shared__ uint32_t s_sum[kScanThreads];
+    const int per = (total + kScanThreads - 1) / kScanThreads;
+    const int t0 = threadIdx.x * per, t1 = min(total, t0 + per);
+    uint32_t mine = 0;
+    for (int t = t0; t < t1; ++t) {
+        const uint2 r = ranges[t];
+        mine += (r.y - r.x + kBucket - 1) / kBucket;
+    }
+    s_sum[threadIdx.x] = mine;
+    __syncthreads();
+    // inclusive Hillis-Steele scan of the per-thread totals
+    for (int o = 1; o < kScanThreads; o <<= 1) {
+        const uint32_t add = threadIdx.x >= o ? s_sum[threadIdx.x - o] : 0u;
+        __syncthreads();
+        s_sum[threadIdx.x] += add;
+        __syncthreads();
+    }
+    uint32_t acc = s_sum[threadIdx.x] - mine;
+    for (int t = t0; t < t1; ++t) {
+        const uint2 r = ranges[t];
+        const uint32_t nb = (r.y - r.x + kBucket - 1) / kBucket;
+        bucket_off[t] = min(acc, max_buckets);
+        for (uint32_t b = acc; b < acc + nb && b < max_buckets; ++b) bucket_tile[b] = (uint32_t)t;
+        acc += nb;
+    }
+    if (threadIdx.x == kScanThreads - 1) bucket_off[total] = min(s_sum[kScanThreads - 1], max_buckets);
+}
+
+// Per-warp staging of 32 active pixels: state in front of the bucket, dL/dC,
+// the output colour, last-contributor position and tile-local index.
+struct PgStage {
+    float T[kBucket], C0[kBucket], C1[kBucket], C2[kBucket];
+    float g0[kBucket], g1[kBucket], g2[kBucket];
+    float o0[kBucket], o1[kBucket], o2[kBucket];
+    uint32_t last[kBucket];
+    uint32_t p[kBucket];
+};
+
+__global__ void __launch_bounds__(kPgWarps * 32)
+blend_bwd_pg_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
+                    const uint32_t* __restrict__ gids, const Screen* __restrict__ screen,
+                    const float* __restrict__ dL_dimg, const uint32_t* __restrict__ n_contrib,
+                    PgBuffers pg, ScreenGrad* __restrict__ sgrad)
+{
+    __shared__ PgStage s_stage[kPgWarps][2];
+    __shared__ uint8_t s_list[kPgWarps][kTilePixels];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t full = 0xffffffffu;
+    const uint32_t nb = pg.bucket_off[vt.total_tiles];
+    for (uint32_t b = blockIdx.x * kPgWarps + warp; b < nb; b += gridDim.x * kPgWarps) {
+        const int tile = (int)pg.bucket_tile[b];
+        const uint32_t first = (b - pg.bucket_off[tile]) * kBucket;  // list position of lane 0
+        const int v = view_of_tile(vt, tile);
+        const int lt = tile - vt.tile_off[v];
+        const int x0 = (lt % vt.tiles_x[v]) * kTile, y0 = (lt / vt.tiles_x[v]) * kTile;
+        const int W = vt.width[v], H = vt.height[v];
+        const int64_t P = (int64_t)W * H, poff = vt.pix_off[v];
+        const uint2 range = ranges[tile];
+        const uint32_t j = range.x + first + lane;
+        const bool has = j < range.y;
+        const uint32_t pos = first + lane + 1;  // 1-based list position of this lane's entry
+        Entry e;
+        uint32_t gid = 0, bmask = 0;
+        if (has) {
+            gid = gids[j];
+            const Screen rec = screen[(int64_t)v * n + gid];
+            stage_entry(rec, e);
+            bmask = block_mask(rec, x0, y0);
+        } else {
+            e.xy = make_float2(0.f, 0.f);
+            e.coef = make_float4(0.f, 0.f, 0.f, 0.f);
+            e.rgbo = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // the tile's pixels still blending in front of this bucket
+        int na = 0;
+        for (int c = 0; c < kTilePixels / 32; ++c) {
+            const int p = 32 * c + lane;
+            const int px = x0 + (p & (kTile - 1)), py = y0 + (p >> 4);
+            const bool act = px < W && py < H && n_contrib[poff + (int64_t)py * W + px] > first;
+            const uint32_t bal = __ballot_sync(full, act);
+            if (act) s_list[warp][na + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)p;
+            na += __popc(bal);
+        }
+        __syncwarp();
+        const float4* st = pg.state + (int64_t)b * kTilePixels;
+        float d[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) d[k] = 0.f;
+        float To = 0.f, Co0 = 0.f, Co1 = 0.f, Co2 = 0.f;  // state this lane hands on
+        for (int s = 0; s < na + kBucket - 1; ++s) {
+            if ((s & (kBucket - 1)) == 0 && s < na) {
+                // stage pixels s .. s + 31 (the buffer last read at step s - 2)
+                PgStage& sg = s_stage[warp][(s >> 5) & 1];
+                const int i = s + lane;
+                if (i < na) {
+                    const int p = s_list[warp][i];
+                    const int64_t pix = (int64_t)(y0 + (p >> 4)) * W + x0 + (p & (kTile - 1));
+                    const float4 t4 = st[p];
+                    const float4 o4 = pg.pixel_final[poff + pix];
+                    sg.T[lane] = t4.x;
+                    sg.C0[lane] = t4.y;
+                    sg.C1[lane] = t4.z;
+                    sg.C2[lane] = t4.w;
+                    sg.g0[lane] = dL_dimg[3 * poff + pix];
+                    sg.g1[lane] = dL_dimg[3 * poff + P + pix];
+                    sg.g2[lane] = dL_dimg[3 * poff + 2 * P + pix];
+                    sg.o0[lane] = o4.x;
+                    sg.o1[lane] = o4.y;
+                    sg.o2[lane] = o4.z;
+                    sg.last[lane] = n_contrib[poff + pix];
+                    sg.p[lane] = (uint32_t)p;
+                }
+                __syncwarp();
+            }
+            // the state lane - 1 produced for the pixel this lane takes now
+            float T = __shfl_up_sync(full, To, 1);
+            float C0 = __shfl_up_sync(full, Co0, 1);
+            float C1 = __shfl_up_sync(full, Co1, 1);
+            float C2 = __shfl_up_sync(full, Co2, 1);
+            const int i = s - lane;
+            if (i < 0 || i >= na) continue;
+            const PgStage& sg = s_stage[warp][(i >> 5) & 1];
+            const int k = i & (kBucket - 1);
+            if (lane == 0) {
+                T = sg.T[k];
+                C0 = sg.C0[k];
+                C1 = sg.C1[k];
+                C2 = sg.C2[k];
+            }
+            const int p = (int)sg.p[k];
+            const int lx = p & (kTile - 1), ly = p >> 4;
+            Frag f;
+            float u, w;
+            if (has && pos <= sg.last[k] && ((bmask >> ((lx >> 3) | ((ly >> 2) << 1))) & 1u) &&
+                eval_frag((float)(x0 + lx) + 0.5f, (float)(y0 + ly) + 0.5f, e, f, u, w)) {
+                // the forward's update, rounding for rounding
+                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, f.alpha));
+                const float wT = __fmul_rn(f.alpha, T);
+                C0 = __fmaf_rn(wT, e.rgbo.x, C0);
+                C1 = __fmaf_rn(wT, e.rgbo.y, C1);
+                C2 = __fmaf_rn(wT, e.rgbo.z, C2);
+                // colour behind the entry, normalised by T after it (Tn >= 1e-4)
+                const float iT = __fdividef(1.0f, Tn);
+                const float g0 = sg.g0[k], g1 = sg.g1[k], g2 = sg.g2[k];
+                const float c0 = e.rgbo.x - (sg.o0[k] - C0) * iT;
+                const float c1 = e.rgbo.y - (sg.o1[k] - C1) * iT;
+                const float c2 = e.rgbo.z - (sg.o2[k] - C2) * iT;
+                const float dalpha = T * (g0 * c0 + g1 * c1 + g2 * c2);
+                frag_grads(e, f, u, w, dalpha, wT, g0, g1, g2, d);
+                T = Tn;
+            }
+            To = T;
+            Co0 = C0;
+            Co1 = C1;
+            Co2 = C2;
+        }
+        if (has && (d[0] != 0.f || d[1] != 0.f || d[2] != 0.f || d[3] != 0.f || d[4] != 0.f || d[5] != 0.f ||
+                    d[6] != 0.f || d[7] != 0.f || d[8] != 0.f)) {
+            ScreenGrad* dst = sgrad + (int64_t)v * n + gid;
+            atomicAdd(&dst->g0, make_float4(d[0], d[1], d[2], d[3]));
+            atomicAdd(&dst->g1, make_float4(d[4], d[5], d[6], d[7]));
+            atomicAdd(&dst->g2.x, d[8]);
+        }
+        __syncwarp();  // s_list and the stages are reused by the next bucket
+    }
+}
+
 // Launch configurations the tuner may pick: pixels per thread x batch, and
 // the schedule.  A queue launch is one resident grid: SMs x CTAs per SM.
 static int sm_count()
@@ -528,16 +755,17 @@ static int grid_for(K kernel, int threads, int total_tiles, const TileSched& sch
     return (int)(g < total_tiles ? g : total_tiles);
 }
 
-template <int PPT, int BATCH>
+template <int PPT, int BATCH, bool CKPT>
 static void launch_pair_fwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                             const Screen* screen, const float bg[3], float* images, float* T_final,
                             uint32_t* n_contrib, uint32_t* n_blended, const TileSched& sched,
-                            cudaStream_t st)
+                            const PgBuffers& pg, cudaStream_t st)
 {
     const int threads = kTilePixels / PPT;
-    const int grid = grid_for(blend_fwd_kernel<PPT, BATCH>, threads, vt.total_tiles, sched);
-    blend_fwd_kernel<PPT, BATCH><<<grid, threads, 0, st>>>(vt, n, ranges, gids, screen, bg[0], bg[1], bg[2],
-                                                           images, T_final, n_contrib, n_blended, sched);
+    const int grid = grid_for(blend_fwd_kernel<PPT, BATCH, CKPT>, threads, vt.total_tiles, sched);
+    blend_fwd_kernel<PPT, BATCH, CKPT><<<grid, threads, 0, st>>>(vt, n, ranges, gids, screen, bg[0], bg[1],
+                                                                 bg[2], images, T_final, n_contrib,
+                                                                 n_blended, sched, pg);
 }
 
 template <int PPT, int BATCH>
@@ -581,18 +809,54 @@ static TileSched make_sched(uint32_t* queue, int schedule, bool backward)
     return s;
 }
 
+// pg_* non-null: also store the per-Gaussian backward's bucket states (after
+// computing the bucket offsets).
 cudaError_t launch_blend_fwd(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
                              const Screen* screen, const float bg[3], float* images, float* T_final,
                              uint32_t* n_contrib, uint32_t* n_blended, uint32_t* queue, int ppt, int batch,
-                             int schedule, cudaStream_t st)
+                             int schedule, uint32_t* pg_bucket_off, uint32_t* pg_bucket_tile,
+                             float4* pg_state, float4* pg_pixel_final, int64_t pg_max_buckets,
+                             cudaStream_t st)
 {
     if (vt.total_tiles <= 0) return cudaSuccess;
     const TileSched sched = make_sched(queue, schedule, false);
+    const PgBuffers pg{pg_bucket_off, pg_bucket_tile, pg_state, pg_pixel_final, pg_max_buckets};
+    if (pg_state) {
+        bucket_scan_kernel<<<1, kScanThreads, 0, st>>>(ranges, vt.total_tiles, pg_bucket_off, pg_bucket_tile,
+                                                       (uint32_t)pg_max_buckets);
+        profile_mark(st, "bucket_scan");
 #define FGS_GO(P, Bt) \
-    if (ppt == P && batch == Bt) launch_pair_fwd<P, Bt>(vt, n, ranges, gids, screen, bg, images, T_final, n_contrib, n_blended, sched, st);
-    FGS_BLEND_CONFIGS(FGS_GO)
+        if (ppt == P && batch == Bt) launch_pair_fwd<P, Bt, true>(vt, n, ranges, gids, screen, bg, images, T_final, n_contrib, n_blended, sched, pg, st);
+        FGS_BLEND_CONFIGS(FGS_GO)
 #undef FGS_GO
+    } else {
+#define FGS_GO(P, Bt) \
+        if (ppt == P && batch == Bt) launch_pair_fwd<P, Bt, false>(vt, n, ranges, gids, screen, bg, images, T_final, n_contrib, n_blended, sched, pg, st);
+        FGS_BLEND_CONFIGS(FGS_GO)
+#undef FGS_GO
+    }
     profile_mark(st, "blend_fwd");
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_bwd_pg(const ViewTable& vt, int64_t n, const uint2* ranges, const uint32_t* gids,
+                                const Screen* screen, const float* dL_dimg, const uint32_t* n_contrib,
+                                uint32_t* pg_bucket_off, uint32_t* pg_bucket_tile, float4* pg_state,
+                                float4* pg_pixel_final, int64_t pg_max_buckets, ScreenGrad* sgrad,
+                                cudaStream_t st)
+{
+    if (vt.total_tiles <= 0) return cudaSuccess;
+    const PgBuffers pg{pg_bucket_off, pg_bucket_tile, pg_state, pg_pixel_final, pg_max_buckets};
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_bwd_pg_kernel, kPgWarps * 32, 0) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t need = (pg_max_buckets + kPgWarps - 1) / kPgWarps;
+    const int64_t cap = (int64_t)per_sm * sm_count();
+    const int grid = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+    blend_bwd_pg_kernel<<<grid, kPgWarps * 32, 0, st>>>(vt, n, ranges, gids, screen, dL_dimg, n_contrib, pg,
+                                                        sgrad);
+    profile_mark(st, "blend_bwd_pg");
     return cudaGetLastError();
 }
 

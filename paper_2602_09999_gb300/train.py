@@ -104,10 +104,15 @@ class Views:
 class Rasterizer:
     """Workspace and the forward / loss / backward calls of one batch shape."""
 
-    def __init__(self, n: int, views: Views, k_max: int, device="cuda"):
+    def __init__(self, n: int, views: Views, k_max: int, device="cuda", per_gaussian=False):
+        """per_gaussian: reserve the buffers of the per-Gaussian blend
+        backward and select it (fgs_tuning.blend_backward)."""
         self.n = int(n)
         self.views = views
-        self.layout = B.fgs_workspace_size(self.n, views.host, views.n, int(k_max))
+        flags = B.FGS_WS_PER_GAUSSIAN if per_gaussian else 0
+        self.layout = B.fgs_workspace_size_ex(self.n, views.host, views.n, int(k_max), flags)
+        if per_gaussian:
+            self.layout.tuning.blend_backward = B.FGS_BACKWARD_PER_GAUSSIAN
         self.ws = torch.zeros(self.layout.total_bytes, dtype=torch.uint8, device=device)
         if self.ws.data_ptr() % 256:
             raise RuntimeError("workspace is not 256-byte aligned")
@@ -224,7 +229,7 @@ class Trainer:
     def __init__(self, params, cams: Sequence, k_max: int, sh_degree=3, lam=0.2,
                  bg=(0.0, 0.0, 0.0), lr=DEFAULT_LR, sh_dtype=torch.float32,
                  moment_dtype=torch.float32, lr_means_final=0.0, decay_steps=0, device="cuda",
-                 fused_adam=True, store_grads=False):
+                 fused_adam=True, store_grads=False, per_gaussian=False):
         self.device = device
         self.fused_adam = bool(fused_adam) and (sh_dtype, moment_dtype) in FUSED_PAIRS
         self.store_grads = bool(store_grads)
@@ -237,7 +242,7 @@ class Trainer:
         self.exp_avg_sq = {k: torch.zeros(self.params[k].shape, device=device, dtype=moment_dtype)
                            for k in self.groups}
         self.views = Views(cams, device)
-        self.rast = Rasterizer(self.n, self.views, k_max, device)
+        self.rast = Rasterizer(self.n, self.views, k_max, device, per_gaussian=per_gaussian)
         P = self.views.total_pixels
         self.images = torch.zeros(3 * P, device=device)
         self.targets = torch.zeros(3 * P, device=device)

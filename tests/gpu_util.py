@@ -15,12 +15,12 @@ GRAD_REL_L2 = 1e-3        # relative L2 error per gradient tensor (same source)
 
 
 def gpu_forward(params, cams, k_max=None, sh_degree=3, bg=(0.0, 0.0, 0.0), sh_dtype=torch.float32,
-                tuning=None):
+                tuning=None, per_gaussian=False):
     n = params["means"].shape[0]
     views = T.Views(cams)
     if k_max is None:
         k_max = max(4096, 64 * n * len(cams))
-    rast = T.Rasterizer(n, views, k_max)
+    rast = T.Rasterizer(n, views, k_max, per_gaussian=per_gaussian)
     if tuning is not None:
         tune.apply(rast.layout, tuning)
     t = T.to_device_params(params, sh_dtype=sh_dtype)
@@ -178,11 +178,11 @@ def oracle_grads(cams, params, targets, masks=None, lam=0.2, bg=(0.0, 0.0, 0.0),
 
 
 def gpu_grads(params, cams, targets, masks=None, lam=0.2, bg=(0.0, 0.0, 0.0), sh_degree=3,
-              sh_dtype=torch.float32, tuning=None, k_max=None):
+              sh_dtype=torch.float32, tuning=None, k_max=None, per_gaussian=False):
     """GPU loss and gradients through the C ABI, with dL/dC zeroed on the
     masked pixels of each view."""
     rast, views, t, images = gpu_forward(params, cams, k_max=k_max, bg=bg, sh_degree=sh_degree,
-                                         sh_dtype=sh_dtype, tuning=tuning)
+                                         sh_dtype=sh_dtype, tuning=tuning, per_gaussian=per_gaussian)
     tg = views.concat([torch.from_numpy(np.asarray(x, np.float32)) for x in targets]).cuda()
     loss = torch.zeros(1, device="cuda")
     dl = torch.zeros_like(images)

@@ -158,3 +158,34 @@ def test_morton_and_permute_argument_checks(lib):
     assert e.value.code == -2
     empty_src, empty_dst = _fake_params(0, 1 << 40), _fake_params(0, 1 << 44)
     B.fgs_permute_params(empty_src, empty_dst, None, None)    # n = 0: no-op
+
+
+def test_per_gaussian_layout_and_checks(lib):
+    """The per-Gaussian buffers exist only with FGS_WS_PER_GAUSSIAN, sized
+    by k_max and the tile count; selecting that backward on a layout made
+    without them, or an unknown backward, is rejected before any launch."""
+    cam = B.camera_array([scenes.look_at((0, 0, 4), (0, 0, 0), 100, 70)])
+    plain = B.fgs_workspace_size(1000, cam, 1, 64_000)
+    pg = B.fgs_workspace_size_ex(1000, cam, 1, 64_000, B.FGS_WS_PER_GAUSSIAN)
+    tiles = 7 * 5
+    for s in (B.FGS_WS_BUCKET_OFF, B.FGS_WS_BUCKET_TILE, B.FGS_WS_BUCKET_STATE, B.FGS_WS_PIXEL_FINAL):
+        assert plain.bytes[s] == 0
+    assert pg.bytes[B.FGS_WS_BUCKET_OFF] == 4 * (tiles + 1)
+    assert pg.bytes[B.FGS_WS_BUCKET_TILE] == 4 * (64_000 // 32 + tiles)
+    assert pg.bytes[B.FGS_WS_BUCKET_STATE] == 16 * 256 * (64_000 // 32 + tiles)
+    assert pg.bytes[B.FGS_WS_PIXEL_FINAL] == 16 * 100 * 70
+    assert pg.flags == B.FGS_WS_PER_GAUSSIAN and plain.flags == 0
+    assert pg.tuning.blend_backward == B.FGS_BACKWARD_PER_PIXEL
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_workspace_size_ex(1000, cam, 1, 64_000, 2)
+    assert e.value.code == -9
+    fake_ws = ctypes.c_void_p(1 << 20)
+    p = B.params_struct(1000, [1 << 40] * 6, [B.FGS_F32] * 6)
+    plain.tuning.blend_backward = B.FGS_BACKWARD_PER_GAUSSIAN
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_render_forward(fake_ws, plain, p, 3, cam, 1 << 30, (0, 0, 0), 1 << 31, None)
+    assert e.value.code == -4
+    pg.tuning.blend_backward = 7
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_render_forward(fake_ws, pg, p, 3, cam, 1 << 30, (0, 0, 0), 1 << 31, None)
+    assert e.value.code == -9
