@@ -38,13 +38,17 @@ radix_upsweep_kernel(const KT* __restrict__ keys, const uint32_t* __restrict__ n
         const int64_t base = (int64_t)b * kSortTile;
         for (int d = threadIdx.x; d < kSortWarps * kRadix; d += kSortThreads) (&h[0][0])[d] = 0;
         __syncthreads();
-#pragma unroll 4
+        // all loads in flight before the first counter update
+        KT k[kSortItems];
+#pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
             const int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
-            if (idx < n) {
-                const uint32_t d = (uint32_t)(keys[idx] >> shift) & dmask;
-                atomicAdd(&h[warp][d], 1u);
-            }
+            k[r] = idx < n ? __ldg(keys + idx) : (KT)0;
+        }
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            const int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
+            if (idx < n) atomicAdd(&h[warp][(uint32_t)(k[r] >> shift) & dmask], 1u);
         }
         __syncthreads();
         for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
@@ -117,12 +121,18 @@ __device__ __forceinline__ void radix_downsweep_tile(DownSmem<KT>& S, const KT* 
     KT k[kSortItems];
     uint32_t val[kSortItems];
     uint32_t dr[kSortItems];  // digit (bits 24..31) | rank within the warp (bits 0..23)
+    // all loads in flight before the ranking (its warp barriers would order them)
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int64_t idx = base + (int64_t)warp * (kSortItems * 32) + r * 32 + lane;
         const bool valid = idx < n;
-        k[r] = valid ? keys_in[idx] : (KT)0;
-        val[r] = valid ? vals_in[idx] : 0u;
+        k[r] = valid ? __ldg(keys_in + idx) : (KT)0;
+        val[r] = valid ? __ldg(vals_in + idx) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t idx = base + (int64_t)warp * (kSortItems * 32) + r * 32 + lane;
+        const bool valid = idx < n;
         const uint32_t d = (uint32_t)(k[r] >> shift) & dmask;
         uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
