@@ -183,7 +183,10 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
                       uint32_t* __restrict__ local_off, uint32_t* __restrict__ block_sum,
                       int nblk, Motion mo)
 {
-    __shared__ uint32_t warp_tot[kPreBlock / 32];
+    // two buffers, alternating by view: a warp still reading view v's totals
+    // cannot be overtaken by a write of view v + 2 (view v + 1's barriers lie
+    // between them)
+    __shared__ uint32_t warp_tot[2][kPreBlock / 32];
     const int64_t i = (int64_t)blockIdx.x * kPreBlock + threadIdx.x;
     const bool valid = i < n;
     float mu[3] = {0.f, 0.f, 0.f}, M[9], o = 0.f, vel[3] = {0.f, 0.f, 0.f}, t0 = 0.f;
@@ -192,7 +195,8 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
         mu[0] = means[3 * i];
         mu[1] = means[3 * i + 1];
         mu[2] = means[3 * i + 2];
-        const float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+        const float4 q4 = *reinterpret_cast<const float4*>(quats + 4 * i);  // rows are 16-byte aligned
+        const float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
         const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
         const float inv = qn > 0.f ? 1.0f / qn : 0.f;
         float Rq[9];
@@ -274,7 +278,7 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
         }
         // compaction offsets of the rendered (view, Gaussian) pairs
         uint32_t total;
-        const uint32_t excl = block_exclusive_scan(count > 0 ? 1u : 0u, warp_tot, total);
+        const uint32_t excl = block_exclusive_scan(count > 0 ? 1u : 0u, warp_tot[v & 1], total);
         if (valid) local_off[vi] = excl;
         if (threadIdx.x == 0) block_sum[(int64_t)v * nblk + blockIdx.x] = total;
     }
@@ -631,7 +635,8 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
     for (int q = 0; q < 45; ++q) my[q] = 0.f;
     if (vis_mask) {
         mu[0] = means[3 * i]; mu[1] = means[3 * i + 1]; mu[2] = means[3 * i + 2];
-        const float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+        const float4 q4 = *reinterpret_cast<const float4*>(quats + 4 * i);  // rows are 16-byte aligned
+        const float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
         const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
         const float inv = 1.0f / qn;
         const float qh[4] = {qw * inv, qx * inv, qy * inv, qz * inv};
