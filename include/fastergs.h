@@ -23,7 +23,8 @@
  * Gaussian parameters (Sec. 2.1 of the paper; fgs_params.data[] order):
  *   0 means       [n,3]  float32
  *   1 log_scales  [n,3]  float32   (scale = exp, Sec. 2.1 activations)
- *   2 quats       [n,4]  float32   (w,x,y,z; normalised in the kernel)
+ *   2 quats       [n,4]  float32   (w,x,y,z; normalised in the kernel; the
+ *                                    buffer 16-byte aligned, else FGS_ERR_ALIGN)
  *   3 opacity     [n]    float32   (logit; sigmoid in the kernel)
  *   4 sh_dc       [n,3]  float32 / bf16 / fp16 (SH band 0, separate buffer
  *                                               as in Sec. 3.2 "Rasterization

@@ -261,6 +261,7 @@ static int check_params(const fgs_params* p, int64_t n, bool grads, const fgs_pa
     }
     if (p->dtype[4] != p->dtype[5]) return FGS_ERR_DTYPE;
     if (!grads && ng == FGS_NUM_GROUPS && !(p->sigma_t > 0.0f)) return FGS_ERR_ARG;
+    if (!grads && (uintptr_t)p->data[2] % 16 != 0) return FGS_ERR_ALIGN;  // quaternions: one 16-byte load
     return FGS_OK;
 }
 

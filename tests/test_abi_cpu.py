@@ -189,3 +189,15 @@ def test_per_gaussian_layout_and_checks(lib):
     with pytest.raises(B.FGSError) as e:
         B.fgs_render_forward(fake_ws, pg, p, 3, cam, 1 << 30, (0, 0, 0), 1 << 31, None)
     assert e.value.code == -9
+
+
+def test_misaligned_quaternions_rejected(lib):
+    """Quaternion rows are read as one 16-byte vector: a buffer off a
+    16-byte boundary is FGS_ERR_ALIGN before any launch."""
+    cam = B.camera_array([scenes.look_at((0, 0, 4), (0, 0, 0), 64, 64)])
+    L = B.fgs_workspace_size(1000, cam, 1, 64_000)
+    ptrs = [1 << 40, 1 << 41, (1 << 42) + 4, 1 << 43, 1 << 44, 1 << 45]
+    p = B.params_struct(1000, ptrs, [B.FGS_F32] * 6)
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_render_forward(ctypes.c_void_p(1 << 20), L, p, 3, cam, 1 << 30, (0, 0, 0), 1 << 31, None)
+    assert e.value.code == -8
