@@ -14,9 +14,9 @@
 
 namespace fgs {
 
-// One thread: advance the step and derive the step sizes (double precision)
-// with the exponential decay of the means learning rate of Suppl. A.
-__global__ void adam_prepare_kernel(fgs_adam_state* st)
+// Advance the step and derive the step sizes (double precision) with the
+// exponential decay of the means learning rate of Suppl. A (one thread).
+__device__ void adam_prepare(fgs_adam_state* st)
 {
     const int t = st->step + 1;
     st->step = t;
@@ -36,6 +36,20 @@ __global__ void adam_prepare_kernel(fgs_adam_state* st)
     st->one_minus_beta1_f = (float)(1.0 - st->beta1);
     st->one_minus_beta2_f = (float)(1.0 - st->beta2);
     st->eps_f = (float)st->eps;
+}
+
+__global__ void adam_prepare_kernel(fgs_adam_state* st) { adam_prepare(st); }
+
+// Zeroes n4 16-byte words while thread 0 of CTA 0 prepares the Adam step:
+// the double-precision scalars take one thread about as long as the zeroing
+// takes the whole grid, so the two share one launch.
+__global__ void __launch_bounds__(256)
+zero_prepare_kernel(float4* __restrict__ dst, int64_t n4, fgs_adam_state* st)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) adam_prepare(st);
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = z;
 }
 
 template <typename PT, typename MT>
@@ -104,6 +118,20 @@ static cudaError_t launch_m(int mdt, int64_t count, void* p, const float* g, voi
     case FGS_F16: return launch_typed<PT, __half>(count, p, g, m, v, a, ds, grp, st);
     default: return launch_typed<PT, float>(count, p, g, m, v, a, ds, grp, st);
     }
+}
+
+// dst: 16-byte aligned, bytes a multiple of 16.
+cudaError_t launch_zero_and_adam_prepare(void* dst, size_t bytes, fgs_adam_state* ds, cudaStream_t st)
+{
+    const int64_t n4 = (int64_t)(bytes / 16);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t need = (n4 + 255) / 256, cap = (int64_t)sms * 8;
+    const int grid = (int)(need < 1 ? 1 : (need < cap ? need : cap));
+    zero_prepare_kernel<<<grid, 256, 0, st>>>((float4*)dst, n4, ds);
+    profile_mark(st, "zero_screen_grads");
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adam_prepare(fgs_adam_state* ds, cudaStream_t st)

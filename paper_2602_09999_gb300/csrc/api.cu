@@ -57,6 +57,7 @@ cudaError_t launch_adam_group(int64_t count, int pdt, int mdt, void* p, const fl
                               void* v, float step_size, float inv_bc2_sqrt, double b1, double b2,
                               double eps, const fgs_adam_state* ds, int grp, cudaStream_t st);
 cudaError_t launch_adam_prepare(fgs_adam_state* ds, cudaStream_t st);
+cudaError_t launch_zero_and_adam_prepare(void* dst, size_t bytes, fgs_adam_state* ds, cudaStream_t st);
 cudaError_t launch_preprocess_bwd_adam(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
                                        const ViewTable& vt, const Screen* screen, const ScreenGrad* sgrad,
                                        const fgs_params* g, const fgs_params* m, const fgs_params* v,
@@ -375,16 +376,22 @@ int fgs_loss_l1_dssim(void* ws, const fgs_workspace_layout* L, const fgs_camera*
 }
 
 // Blend backward into the screen-gradient records (shared by both backward
-// entry points).
+// entry points).  adam (nullable): also prepare that Adam step, in the launch
+// that zeroes the records.
 static int backward_blend(void* ws, const fgs_workspace_layout* L, const ViewTable& vt, const float bg[3],
-                          const float* dl_dimages, cudaStream_t st)
+                          const float* dl_dimages, fgs_adam_state* adam, cudaStream_t st)
 {
     const int64_t n = L->n;
     const uint32_t* svals = slot<uint32_t>(ws, L, L->sorted_in_alt ? FGS_WS_VALS_ALT : FGS_WS_VALS);
     Screen* screen = slot<Screen>(ws, L, FGS_WS_SCREEN);
     ScreenGrad* sgrad = slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD);
-    if (cudaMemsetAsync(sgrad, 0, L->bytes[FGS_WS_SCREEN_GRAD], st) != cudaSuccess) return FGS_ERR_CUDA;
-    profile_mark(st, "zero_screen_grads");
+    if (adam) {
+        if (launch_zero_and_adam_prepare(sgrad, L->bytes[FGS_WS_SCREEN_GRAD], adam, st) != cudaSuccess)
+            return FGS_ERR_CUDA;
+    } else {
+        if (cudaMemsetAsync(sgrad, 0, L->bytes[FGS_WS_SCREEN_GRAD], st) != cudaSuccess) return FGS_ERR_CUDA;
+        profile_mark(st, "zero_screen_grads");
+    }
     if (L->tuning.blend_backward == FGS_BACKWARD_PER_GAUSSIAN)
         return cuda_rc(launch_blend_bwd_pg(vt, n, slot<uint2>(ws, L, FGS_WS_RANGES), svals, screen, dl_dimages,
                                            slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB),
@@ -415,7 +422,7 @@ int fgs_render_backward(void* ws, const fgs_workspace_layout* L, const fgs_param
     if ((rc = check_params(grads, L->n, true, params)) != FGS_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     profile_mark(st, "begin");
-    if ((rc = backward_blend(ws, L, vt, bg, dl_dimages, st)) != FGS_OK) return rc;
+    if ((rc = backward_blend(ws, L, vt, bg, dl_dimages, nullptr, st)) != FGS_OK) return rc;
     return cuda_rc(launch_preprocess_bwd(L->n, sh_degree, params, cams_device, vt,
                                          slot<Screen>(ws, L, FGS_WS_SCREEN),
                                          slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD), grads, st));
@@ -443,8 +450,7 @@ int fgs_render_backward_adam(void* ws, const fgs_workspace_layout* L, const fgs_
     if (!fused_adam_supported(params->dtype[4], exp_avg->dtype[0])) return FGS_ERR_DTYPE;
     cudaStream_t st = (cudaStream_t)stream;
     profile_mark(st, "begin");
-    if ((rc = backward_blend(ws, L, vt, bg, dl_dimages, st)) != FGS_OK) return rc;
-    if (launch_adam_prepare(state_device, st) != cudaSuccess) return FGS_ERR_CUDA;
+    if ((rc = backward_blend(ws, L, vt, bg, dl_dimages, state_device, st)) != FGS_OK) return rc;
     return cuda_rc(launch_preprocess_bwd_adam(L->n, sh_degree, params, cams_device, vt,
                                               slot<Screen>(ws, L, FGS_WS_SCREEN),
                                               slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD), grads, exp_avg,

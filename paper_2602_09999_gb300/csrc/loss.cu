@@ -15,8 +15,9 @@
 //   ssim_bwd : per 32x16 block and channel: halo block of D0..D2, blur, and
 //              dL/dx = s ((1 - lambda) sign(x - y) - lambda dS/dx) with
 //              s = 1 / (3 H W n_views).
-//   loss_reduce : one CTA sums the per-CTA partials per view in a fixed
-//              order (double precision) and writes the scalar loss.
+//              Its first CTA, before its own block, also sums the per-CTA
+//              partials of ssim_fwd per view in a fixed order (double
+//              precision) and writes the scalar loss.
 // The window weights are computed once on the host (double precision,
 // rounded to float) and passed by value with the CTA grid of the views.
 #include <cmath>
@@ -148,14 +149,48 @@ ssim_fwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
     }
 }
 
+// The scalar loss from the per-CTA partials (256 threads; red: scratch).
+__device__ void reduce_loss(const ViewTable& vt, const LossGrid& lg, const double* __restrict__ partials,
+                            float lambda, float* __restrict__ loss_out, double (*red)[256], int tid)
+{
+    double total = 0.0;
+    for (int v = 0; v < vt.n_views; ++v) {
+        double a = 0.0, b = 0.0;
+        for (int t = lg.cta_off[v] + tid; t < lg.cta_off[v + 1]; t += 256) {
+            a += partials[2 * t];
+            b += partials[2 * t + 1];
+        }
+        red[0][tid] = a;
+        red[1][tid] = b;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (tid < o) {
+                red[0][tid] += red[0][tid + o];
+                red[1][tid] += red[1][tid + o];
+            }
+            __syncthreads();
+        }
+        const double inv = 1.0 / (3.0 * (double)vt.width[v] * (double)vt.height[v]);
+        total += (1.0 - lambda) * red[0][0] * inv + lambda * (1.0 - red[1][0] * inv);
+        __syncthreads();
+    }
+    if (tid == 0) loss_out[0] = (float)(total / vt.n_views);
+}
+
 __global__ void __launch_bounds__(kLX * kLY)
 ssim_bwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
                 const float* __restrict__ targets, const float* __restrict__ maps, float lambda,
-                float* __restrict__ dL)
+                float* __restrict__ dL, const double* __restrict__ partials, float* __restrict__ loss_out)
 {
-    __shared__ float sm[3][kSpanY][kSpanX + 1];
+    __shared__ __align__(16) float sm[3][kSpanY][kSpanX + 1];
     __shared__ float hs[3][kSpanY][kLTW + 1];
+    static_assert(sizeof(sm) >= 2 * 256 * sizeof(double), "room for the loss reduction");
     const int b = blockIdx.x;
+    // the first CTA (scheduled first) sums ssim_fwd's partials, complete
+    // before this kernel started, then takes its own block
+    if (b == 0)
+        reduce_loss(vt, lg, partials, lambda, loss_out, reinterpret_cast<double(*)[256]>(&sm[0][0][0]),
+                    threadIdx.y * kLX + threadIdx.x);
     const int v = view_of_cta(lg, vt.n_views, b);
     const int lb = b - lg.cta_off[v];
     const int W = vt.width[v], H = vt.height[v];
@@ -211,35 +246,6 @@ ssim_bwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
     }
 }
 
-__global__ void __launch_bounds__(256)
-loss_reduce_kernel(ViewTable vt, LossGrid lg, const double* __restrict__ partials, float lambda,
-                   float* __restrict__ loss_out)
-{
-    __shared__ double red[2][256];
-    double total = 0.0;
-    for (int v = 0; v < vt.n_views; ++v) {
-        double a = 0.0, b = 0.0;
-        for (int t = lg.cta_off[v] + threadIdx.x; t < lg.cta_off[v + 1]; t += 256) {
-            a += partials[2 * t];
-            b += partials[2 * t + 1];
-        }
-        red[0][threadIdx.x] = a;
-        red[1][threadIdx.x] = b;
-        __syncthreads();
-        for (int o = 128; o > 0; o >>= 1) {
-            if (threadIdx.x < o) {
-                red[0][threadIdx.x] += red[0][threadIdx.x + o];
-                red[1][threadIdx.x] += red[1][threadIdx.x + o];
-            }
-            __syncthreads();
-        }
-        const double inv = 1.0 / (3.0 * (double)vt.width[v] * (double)vt.height[v]);
-        total += (1.0 - lambda) * red[0][0] * inv + lambda * (1.0 - red[1][0] * inv);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) loss_out[0] = (float)(total / vt.n_views);
-}
-
 static LossGrid loss_grid(const ViewTable& vt)
 {
     LossGrid g;
@@ -266,10 +272,8 @@ cudaError_t launch_loss(const ViewTable& vt, const float* images, const float* t
     const dim3 block(kLX, kLY);
     ssim_fwd_kernel<<<ctas, block, 0, st>>>(vt, lg, images, targets, maps, partials);
     profile_mark(st, "loss_ssim_fwd");
-    ssim_bwd_kernel<<<ctas, block, 0, st>>>(vt, lg, images, targets, maps, lambda, dL);
+    ssim_bwd_kernel<<<ctas, block, 0, st>>>(vt, lg, images, targets, maps, lambda, dL, partials, loss_out);
     profile_mark(st, "loss_ssim_bwd");
-    loss_reduce_kernel<<<1, 256, 0, st>>>(vt, lg, partials, lambda, loss_out);
-    profile_mark(st, "loss_reduce");
     return cudaGetLastError();
 }
 
