@@ -292,28 +292,61 @@ __global__ void __launch_bounds__(1024)
 scan_block_sums_kernel(uint32_t* __restrict__ block_sum, int64_t count, WsHeader* __restrict__ hdr,
                        int64_t k_max, bool instances)
 {
-    __shared__ unsigned long long part[1024];
-    const int t = threadIdx.x;
-    const int64_t chunk = (count + 1023) / 1024;
+    __shared__ unsigned long long wsum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // each thread a run of a multiple of 4 values (16-byte vectors; the
+    // array starts 256-byte aligned)
+    const int64_t chunk = (((count + 1023) / 1024) + 3) & ~(int64_t)3;
     const int64_t b = t * chunk, e = min(count, b + chunk);
     unsigned long long s = 0;
-    for (int64_t j = b; j < e; ++j) s += block_sum[j];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const unsigned long long y = t >= o ? part[t - o] : 0ull;
-        __syncthreads();
-        part[t] += y;
-        __syncthreads();
+#pragma unroll 4
+    for (int64_t j = b; j < e; j += 4) {
+        if (j + 4 <= e) {
+            const uint4 q = *reinterpret_cast<const uint4*>(block_sum + j);
+            s += (unsigned long long)q.x + q.y + q.z + q.w;
+        } else {
+            for (int64_t jj = j; jj < e; ++jj) s += block_sum[jj];
+        }
     }
-    unsigned long long run = part[t] - s;
-    for (int64_t j = b; j < e; ++j) {
-        const uint32_t x = block_sum[j];
-        block_sum[j] = (uint32_t)min(run, 0xffffffffull);
-        run += x;
+    // exclusive scan of the run totals: shuffles within warps, then the warp totals
+    unsigned long long x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    unsigned long long run = x - s + (warp > 0 ? wsum[warp - 1] : 0ull);
+    for (int64_t j = b; j < e; j += 4) {
+        if (j + 4 <= e) {
+            const uint4 q = *reinterpret_cast<const uint4*>(block_sum + j);
+            uint4 o;
+            o.x = (uint32_t)min(run, 0xffffffffull); run += q.x;
+            o.y = (uint32_t)min(run, 0xffffffffull); run += q.y;
+            o.z = (uint32_t)min(run, 0xffffffffull); run += q.z;
+            o.w = (uint32_t)min(run, 0xffffffffull); run += q.w;
+            *reinterpret_cast<uint4*>(block_sum + j) = o;
+        } else {
+            for (int64_t jj = j; jj < e; ++jj) {
+                const uint32_t q = block_sum[jj];
+                block_sum[jj] = (uint32_t)min(run, 0xffffffffull);
+                run += q;
+            }
+        }
     }
     if (t == 1023) {
-        const unsigned long long tot = part[1023];
+        const unsigned long long tot = wsum[31];
         if (instances) {
             hdr->instances = tot;
             hdr->counters[0] = (uint32_t)min(tot, (unsigned long long)k_max);

@@ -67,30 +67,37 @@ __global__ void __launch_bounds__(256)
 radix_scan_kernel(uint32_t* __restrict__ hist, const uint32_t* __restrict__ n_dev, int nb_max,
                   uint32_t* __restrict__ dtot)
 {
-    __shared__ uint32_t part[256];
+    __shared__ uint32_t wsum[8];
     const uint32_t n = *n_dev;
     const int nb = (int)((n + kSortTile - 1) / kSortTile);
     uint32_t* row = hist + (int64_t)blockIdx.x * nb_max;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int chunk = (nb + 255) / 256;
     const int b0 = t * chunk, b1 = min(nb, b0 + chunk);
     uint32_t s = 0;
     for (int j = b0; j < b1; ++j) s += row[j];
-    part[t] = s;
+    // exclusive scan of the 256 run totals: shuffles, then the 8 warp totals
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    for (int o = 1; o < 256; o <<= 1) {
-        const uint32_t y = t >= o ? part[t - o] : 0u;
-        __syncthreads();
-        part[t] += y;
-        __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        before += w < warp ? wsum[w] : 0u;
+        total += wsum[w];
     }
-    uint32_t run = part[t] - s;
+    uint32_t run = before + x - s;
     for (int j = b0; j < b1; ++j) {
-        const uint32_t x = row[j];
+        const uint32_t v = row[j];
         row[j] = run;
-        run += x;
+        run += v;
     }
-    if (t == 255) dtot[blockIdx.x] = part[255];
+    if (t == 255) dtot[blockIdx.x] = total;
 }
 
 template <typename KT> struct DownSmem {
