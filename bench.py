@@ -230,7 +230,7 @@ BLEND_FLOPS = {"blend_fwd": (12, 9), "blend_bwd": (12, 50)}
 # profiles/dram_outdoor_3M_1237x822.md), for the roofline's "traffic" field.
 # Reported only for that workload, order and launch configuration; a change
 # to one of these kernels must refresh or drop its entry.
-PROFILED_DRAM_BYTES = {"preprocess_bwd_adam": 4.492e9}
+PROFILED_DRAM_BYTES = {"preprocess_bwd_adam": 4.492e9, "blend_fwd": 2.28e7, "blend_bwd": 4.81e7}
 PROFILED_WORKLOAD = (3_000_000, 1237, 822)
 # the paper re-applies the z-order every 5000 iterations (Sec. 3.3)
 MORTON_PERIOD = 5000
@@ -432,6 +432,46 @@ def run_ours(args, dist):
                         "avg_launch_ms": round(avg_ms, 5)}
     phase_ms = per_step_ms(phases, prof_steps)
 
+    # The blend kernels against rates measured on this GPU: FP32 FMA, ex2 and
+    # L2 reads (a copy and a GEMM do not bound them), plus their DRAM bytes.
+    blend_roofline = None
+    if phases and "blend_fwd" in phases and "blend_bwd" in phases:
+        peaks = measure_blend_peaks(torch, B, stream, dev)
+        visits = {}
+        for i in range(prof_steps):
+            c = (prof_start + i) % len(cams)
+            visits[c] = visits.get(c, 0) + 1
+        ev = bl = inst = 0.0
+        for c, cnt in visits.items():
+            tr.views.device.copy_(cam_table[c * cam_bytes:(c + 1) * cam_bytes])
+            tr.forward_only()
+            a, b = tr.rast.fragment_counts()
+            k = min(tr.rast.error()[1], tr.rast.k_max)
+            ev, bl, inst = ev + a * cnt, bl + b * cnt, inst + k * cnt
+        ev, bl, inst = ev / prof_steps, bl / prof_steps, inst / prof_steps
+        blend_roofline = {"peaks_measured": peaks, "evaluations_per_launch": int(ev),
+                          "blended_per_launch": int(bl), "instances_per_launch": int(inst)}
+        for name in ("blend_fwd", "blend_bwd"):
+            sec = phases[name][0] / phases[name][1] / 1000.0
+            f_eval, f_blend = BLEND_FLOPS[name]
+            tflops = (f_eval * ev + f_blend * bl) / sec / 1e12
+            l2_bytes = 52 * inst + 20 * W * H   # gathers: id + 48-byte record; per-pixel state
+            entry = {"avg_launch_ms": round(sec * 1000.0, 5),
+                     "fp32": {"achieved_tflops": round(tflops, 3), "peak_tflops": peaks["fp32_tflops"],
+                              "frac": round(tflops / peaks["fp32_tflops"], 4)},
+                     "ex2": {"achieved_per_s": float(f"{ev / sec:.4g}"), "peak_per_s": peaks["ex2_per_s"],
+                             "frac": round(ev / sec / peaks["ex2_per_s"], 4)},
+                     "l2": {"achieved_gbs": round(l2_bytes / sec / 1e9, 1), "peak_gbs": peaks["l2_gbs"],
+                            "frac": round(l2_bytes / sec / 1e9 / peaks["l2_gbs"], 4),
+                            "bytes_per_launch": int(l2_bytes)}}
+            dram = PROFILED_DRAM_BYTES.get(name) if ((n, W, H) == PROFILED_WORKLOAD
+                                                     and not args.no_morton) else None
+            entry["hbm"] = {"achieved_gbs": None if dram is None else round(dram / sec / 1e9, 1),
+                            "peak_gbs": hbm,
+                            "frac": None if dram is None else round(dram / sec / 1e9 / hbm, 4),
+                            "traffic": dram}
+            blend_roofline[name] = entry
+
     # e2e through the public API: target and camera from pinned host memory,
     # loss back to the host, every step
     e2e = None
@@ -568,6 +608,7 @@ def run_ours(args, dist):
         batched.append(entry)
         del tb
 
+    uneven = None if args.no_batched else run_uneven(args, dist, stream, params, views_per_s)
     dynamic = None if args.no_dynamic else run_dynamic(args, dist, stream, profile_pass, per_step_ms)
 
     return dict(tuned=list(tuned[0]) if tuned else None, tuning_ms=tuned[1] if tuned else None,
@@ -577,7 +618,44 @@ def run_ours(args, dist):
                           else int(round(launches_per_step * args.steps))),
                 roofline=roofline, clocks=clocks, e2e=e2e, batched=batched, dynamic=dynamic,
                 k_max=k_max, instances_last=inst_last, visible_last=visible_est, n=n,
-                morton=morton, per_gaussian=per_gaussian)
+                morton=morton, per_gaussian=per_gaussian, blend_roofline=blend_roofline,
+                uneven=uneven)
+
+
+def measure_blend_peaks(torch, B, stream, dev):
+    """FP32 FMA, ex2.approx and L2-read rates of this GPU, each the best of
+    three timed launches after a warm-up (the library's microbenchmarks)."""
+    s = stream.cuda_stream
+    props = torch.cuda.get_device_properties(dev)
+    out = torch.zeros(props.multi_processor_count * 8, device=dev)
+
+    def best_ms(fn, reps=3):
+        fn()
+        best = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            grid = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best, grid
+
+    iters = 4096
+    ms, grid = best_ms(lambda: B.fgs_peak_fma(iters, out.data_ptr(), s))
+    fp32 = grid * 256 * iters * 8 * 2 / (ms / 1000.0) / 1e12
+    iters = 2048
+    ms, grid = best_ms(lambda: B.fgs_peak_ex2(iters, out.data_ptr(), s))
+    ex2 = grid * 256 * iters * 8 / (ms / 1000.0)
+    buf = torch.zeros(64 << 20, dtype=torch.uint8, device=dev)   # 64 MB: stays in the 129 MB L2
+    n4, reps = buf.numel() // 16, 50
+    ms, grid = best_ms(lambda: B.fgs_peak_l2_read(buf.data_ptr(), n4, reps, out.data_ptr(), s))
+    l2 = reps * buf.numel() / (ms / 1000.0) / 1e9
+    del buf
+    return {"fp32_tflops": round(fp32, 2), "ex2_per_s": float(f"{ex2:.4g}"), "l2_gbs": round(l2, 1),
+            "how": "fgs_peak_fma / fgs_peak_ex2 / fgs_peak_l2_read, best of 3 timed launches"}
 
 
 def reorder_once(tr, stream):
@@ -602,6 +680,76 @@ def reorder_once(tr, stream):
 # ---------------------------------------------------------------------------
 # the dynamic (4D) workload
 # ---------------------------------------------------------------------------
+def run_uneven(args, dist, stream, params, plain_views_per_s, pool=25):
+    """The precision variant's batch: four views of uneven sizes (1237x822,
+    960x640, 1600x1064, 640x426) per step, bf16 SH parameters and moments,
+    captured as a CUDA graph; new orbit poses every step from a pool of
+    camera sets.  Reported in views/s and megapixels/s."""
+    import torch
+
+    from paper_2602_09999_gb300 import binding as B
+    from paper_2602_09999_gb300 import scenes
+    from paper_2602_09999_gb300 import train as T
+
+    torch.cuda.empty_cache()
+    sizes = list(scenes.UNEVEN_SIZES)
+    sets = [scenes.uneven_cameras(sizes, seed=200 + s) for s in range(pool)]
+    nv = len(sizes)
+    cam_bytes = ctypes.sizeof(B.fgs_camera) * nv
+    table = torch.frombuffer(bytearray(b"".join(bytes(B.camera_array(cs)) for cs in sets)),
+                             dtype=torch.uint8).cuda()
+    targets = [scenes.target_image(w, h, view=i) for i, (w, h) in enumerate(sizes)]
+    probe = T.Trainer(params, sets[0], k_max=64_000_000, sh_dtype=torch.bfloat16,
+                      moment_dtype=torch.bfloat16)
+    kmax_seen = 0
+    for s in range(pool):
+        probe.views.device.copy_(table[s * cam_bytes:(s + 1) * cam_bytes])
+        probe.forward_only()
+        kmax_seen = max(kmax_seen, probe.rast.error(clear=True)[1])
+    del probe
+    torch.cuda.empty_cache()
+    tr = T.Trainer(params, sets[0], k_max=int(kmax_seen * 1.25) + 4096, lam=0.2,
+                   sh_dtype=torch.bfloat16, moment_dtype=torch.bfloat16)
+    tr.set_targets(targets)
+    if not args.no_morton:
+        reorder_once(tr, stream)
+
+    def load(i):
+        s = i % pool
+        tr.views.device.copy_(table[s * cam_bytes:(s + 1) * cam_bytes])
+
+    load(0)
+    tr.capture(warmup=2)
+    for i in range(args.warmup):
+        load(i)
+        tr.replay()
+    torch.cuda.synchronize()
+    steps = max(10, args.steps // nv)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        load(args.warmup + i)
+        tr.replay()
+    e1.record(stream)
+    e1.synchronize()
+    ms = dist.max(e0.elapsed_time(e1))
+    if tr.rast.error()[0]:
+        raise RuntimeError("capacity exceeded in the uneven batch")
+    mpx = sum(w * h for w, h in sizes) / 1e6
+    vps = dist.world * steps * nv / (ms / 1000.0)
+    out = {"views_per_s": round(vps, 3), "megapixels_per_s": round(vps / nv * mpx, 3),
+           "ms_per_step": round(ms / steps, 4), "views_per_step": nv,
+           "resolutions": [f"{w}x{h}" for w, h in sizes], "graph": True,
+           "storage": "bf16 SH parameters, bf16 Adam moments", "steps": steps,
+           "plain_megapixels_per_s": round(plain_views_per_s * args.width * args.height / 1e6, 3)}
+    del tr
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_dynamic(args, dist, stream, profile_pass, per_step_ms, n=600_000, views=6, pool=25):
     """Dynamic Gaussians (velocity and temporal centre): 600k Gaussians, 6
     views per step at random timestamps (150 of them) and poses, full step
@@ -789,7 +937,8 @@ def main():
                 "batched": r["batched"], "dynamic": r["dynamic"], "blend_config": r["tuned"],
                 "blend_config_ms": r["tuning_ms"], "kernel_ms_per_step": r["phase_ms"],
                 "instances_last_step": r["instances_last"], "k_max": r["k_max"],
-                "morton": r["morton"], "per_gaussian_backward": r["per_gaussian"]}
+                "morton": r["morton"], "per_gaussian_backward": r["per_gaussian"],
+                "blend_roofline": r["blend_roofline"], "batched_uneven": r["uneven"]}
         print(json.dumps(line), flush=True)
         if args.phase_report:
             with open(args.phase_report, "w") as f:

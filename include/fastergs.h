@@ -389,6 +389,20 @@ int fgs_morton_order(const float *means, int64_t n, uint32_t *order, uint32_t *c
 int fgs_permute_params(const fgs_params *src, const fgs_params *dst, const uint32_t *order,
                        void *stream);
 
+/* Microbenchmarks of the rates that bound the blend kernels (measurement
+ * only; the caller times each call with events on `stream`).  Each returns
+ * through *grid_out the number of 256-thread CTAs it launched; out is a
+ * device float[*grid_out] the kernels never write in practice (it keeps
+ * their work from being optimised away).
+ *   fgs_peak_fma:     grid * 256 * iters * 8 FP32 fused multiply-adds.
+ *   fgs_peak_ex2:     grid * 256 * iters * 8 evaluations of ex2.approx.
+ *   fgs_peak_l2_read: reps passes of 16-byte reads over buf (n4 words,
+ *                     16-byte aligned; sized to stay in L2). */
+int fgs_peak_fma(int32_t iters, float *out, int32_t *grid_out, void *stream);
+int fgs_peak_ex2(int32_t iters, float *out, int32_t *grid_out, void *stream);
+int fgs_peak_l2_read(const void *buf, int64_t n4, int32_t reps, float *out, int32_t *grid_out,
+                     void *stream);
+
 /* Synchronises `stream`, then reads the workspace header: sticky device
  * flags (FGS_FLAG_*) and the instance count of the last forward.  Either
  * output pointer may be NULL.  clear != 0 resets the flags afterwards. */

@@ -39,7 +39,8 @@ EXPORTED = ("fgs_workspace_size", "fgs_workspace_size_ex", "fgs_render_forward",
             "fgs_render_backward", "fgs_render_backward_adam", "fgs_adam_step",
             "fgs_adam_step_device",
             "fgs_sort_scratch_bytes", "fgs_sort_pairs", "fgs_sort_pairs_static",
-            "fgs_morton_scratch_bytes", "fgs_morton_order", "fgs_permute_params", "fgs_get_error",
+            "fgs_morton_scratch_bytes", "fgs_morton_order", "fgs_permute_params",
+            "fgs_peak_fma", "fgs_peak_ex2", "fgs_peak_l2_read", "fgs_get_error",
             "fgs_profile_attach",
             "fgs_profile_count", "fgs_strerror")
 
@@ -134,6 +135,9 @@ def lib():
             L.fgs_morton_scratch_bytes.restype = SZ
             L.fgs_morton_order.argtypes = [P, I64, P, P, P, SZ, P]
             L.fgs_permute_params.argtypes = [P, P, P, P]
+            L.fgs_peak_fma.argtypes = [I32, P, P, P]
+            L.fgs_peak_ex2.argtypes = [I32, P, P, P]
+            L.fgs_peak_l2_read.argtypes = [P, I64, I32, P, P, P]
             L.fgs_get_error.argtypes = [P, P, P, I32, P]
             L.fgs_profile_attach.argtypes = [P, P, I32]
             L.fgs_profile_count.argtypes = []
@@ -271,6 +275,26 @@ def fgs_permute_params(src, dst, order, stream):
     """dst rows = src rows taken in `order` (None: a plain copy)."""
     _check("fgs_permute_params",
            lib().fgs_permute_params(_ref(src), _ref(dst), order, stream))
+
+
+def fgs_peak_fma(iters, out, stream) -> int:
+    """Launches the FP32 FMA microbenchmark; returns its grid (CTAs of 256)."""
+    grid = ctypes.c_int32(0)
+    _check("fgs_peak_fma", lib().fgs_peak_fma(int(iters), out, ctypes.byref(grid), stream))
+    return int(grid.value)
+
+
+def fgs_peak_ex2(iters, out, stream) -> int:
+    grid = ctypes.c_int32(0)
+    _check("fgs_peak_ex2", lib().fgs_peak_ex2(int(iters), out, ctypes.byref(grid), stream))
+    return int(grid.value)
+
+
+def fgs_peak_l2_read(buf, n4, reps, out, stream) -> int:
+    grid = ctypes.c_int32(0)
+    _check("fgs_peak_l2_read",
+           lib().fgs_peak_l2_read(buf, int(n4), int(reps), out, ctypes.byref(grid), stream))
+    return int(grid.value)
 
 
 def fgs_get_error(ws, clear=False, stream=None):
