@@ -31,6 +31,7 @@ constexpr int kLTW = 32, kLTH = 16;         // output block of one CTA
 constexpr int kSpanX = kLTW + 2 * kHalo;    // 42
 constexpr int kSpanY = kLTH + 2 * kHalo;    // 26
 constexpr int kLX = 32, kLY = 8;            // CTA shape (threadIdx.x, threadIdx.y)
+constexpr int kSpanXP = 44;                 // even row stride: 8-byte loads of pixel pairs
 
 // The CTA grid over all views and the window, passed by value.
 struct LossGrid {
@@ -66,7 +67,8 @@ ssim_fwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
                 const float* __restrict__ targets, float* __restrict__ maps,
                 double* __restrict__ partials)
 {
-    __shared__ float sx[kSpanY][kSpanX + 1], sy[kSpanY][kSpanX + 1];
+    __shared__ __align__(8) float sx[kSpanY][kSpanXP];
+    __shared__ __align__(8) float sy[kSpanY][kSpanXP];
     __shared__ float hs[5][kSpanY][kLTW + 1];
     __shared__ float red[2][kLY];
     const int b = blockIdx.x;
@@ -93,34 +95,57 @@ ssim_fwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
             }
         }
         __syncthreads();
-        for (int r = ty; r < kSpanY; r += kLY) {
-            float a = 0.f, bb_ = 0.f, aa = 0.f, yy = 0.f, ab = 0.f;
+        // horizontal blur: each thread two adjacent columns of one row, from
+        // the 12 pixels both windows cover (six 8-byte loads per image)
+        for (int r = tid >> 4; r < kSpanY; r += kLX * kLY / 16) {
+            const int c2 = 2 * (tid & 15);
+            float xv[12], yv[12];
 #pragma unroll
-            for (int k = 0; k < 11; ++k) {
-                const float w = lg.w[k];
-                const float xv = sx[r][tx + k], yv = sy[r][tx + k];
-                a += w * xv;
-                bb_ += w * yv;
-                aa += w * xv * xv;
-                yy += w * yv * yv;
-                ab += w * xv * yv;
+            for (int j = 0; j < 6; ++j) {
+                const float2 x2 = *reinterpret_cast<const float2*>(&sx[r][c2 + 2 * j]);
+                const float2 y2 = *reinterpret_cast<const float2*>(&sy[r][c2 + 2 * j]);
+                xv[2 * j] = x2.x; xv[2 * j + 1] = x2.y;
+                yv[2 * j] = y2.x; yv[2 * j + 1] = y2.y;
             }
-            hs[0][r][tx] = a; hs[1][r][tx] = bb_; hs[2][r][tx] = aa; hs[3][r][tx] = yy; hs[4][r][tx] = ab;
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                float a = 0.f, bb_ = 0.f, aa = 0.f, yy = 0.f, ab = 0.f;
+#pragma unroll
+                for (int k = 0; k < 11; ++k) {
+                    const float w = lg.w[k];
+                    const float x = xv[o + k], y = yv[o + k];
+                    a += w * x;
+                    bb_ += w * y;
+                    aa += w * x * x;
+                    yy += w * y * y;
+                    ab += w * x * y;
+                }
+                hs[0][r][c2 + o] = a; hs[1][r][c2 + o] = bb_; hs[2][r][c2 + o] = aa;
+                hs[3][r][c2 + o] = yy; hs[4][r][c2 + o] = ab;
+            }
         }
         __syncthreads();
-        for (int oy = ty; oy < kLTH; oy += kLY) {
+        // vertical blur: each thread two adjacent rows of one column, one
+        // moment at a time from the 12 rows both windows cover
+        float mom[2][5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            float hv[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) hv[k] = hs[m][2 * ty + k][tx];
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 11; ++k) acc += lg.w[k] * hv[o + k];
+                mom[o][m] = acc;
+            }
+        }
+        for (int o = 0; o < 2; ++o) {
+            const int oy = 2 * ty + o;
             const int py = y0 + oy;
             if (!(px < W && py < H)) continue;
-            float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
-#pragma unroll
-            for (int k = 0; k < 11; ++k) {
-                const float w = lg.w[k];
-                mx += w * hs[0][oy + k][tx];
-                my += w * hs[1][oy + k][tx];
-                exx += w * hs[2][oy + k][tx];
-                eyy += w * hs[3][oy + k][tx];
-                exy += w * hs[4][oy + k][tx];
-            }
+            const float mx = mom[o][0], my = mom[o][1], exx = mom[o][2], eyy = mom[o][3], exy = mom[o][4];
             const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
             const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
             const float n1 = 2.f * mx * my + C1, n2 = 2.f * cxy + C2;
