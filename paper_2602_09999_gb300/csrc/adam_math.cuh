@@ -43,12 +43,14 @@ __device__ __forceinline__ AdamScalars resolve(AdamScalars a, const fgs_adam_sta
     return a;
 }
 
+// Every rounding is spelled out (no contraction left to the compiler), so
+// the kernels that inline this take bit-identical steps.
 __device__ __forceinline__ float adam_update(float p, float g, float& m, float& v, const AdamScalars& a)
 {
-    m = m + a.omb1 * (g - m);
-    v = v * a.b2 + a.omb2 * g * g;
-    const float denom = sqrtf(v) * a.inv_bc2_sqrt + a.eps;
-    return p - a.step_size * (m / denom);
+    m = __fmaf_rn(a.omb1, __fsub_rn(g, m), m);
+    v = __fmaf_rn(v, a.b2, __fmul_rn(__fmul_rn(a.omb2, g), g));
+    const float denom = __fmaf_rn(__fsqrt_rn(v), a.inv_bc2_sqrt, a.eps);
+    return __fmaf_rn(-a.step_size, __fdiv_rn(m, denom), p);
 }
 
 }  // namespace fgs

@@ -336,6 +336,68 @@ def test_fused_backward_adam_matches_separate(oracle_mod, sh_dt, m_dt):
         assert zero.any()
 
 
+@pytest.mark.parametrize("dt", ["f32", "f16"])
+def test_fused_adam_nonzero_moments(dt):
+    """With nonzero moments, the fused backward + Adam update equals the
+    separate Adam step of the same gradients bit for bit (both take the
+    same roundings), zero-gradient Gaussians included: whole blocks of 128
+    culled by opacity, the ragged last block, a block seen only by the
+    second camera (which looks away from the scene), and a block with a
+    single rendered Gaussian."""
+    dts = {"f32": torch.float32, "f16": torch.float16}
+    n = 20_000                                      # 156 full blocks + 32
+    params = scenes.outdoor_scene(n, seed=85)
+    op, mu = params["opacity"].copy(), params["means"].copy()
+    culled = np.zeros(n, bool)
+    for b in (3, 10, 11, 12, 13, 14):
+        culled[128 * b:128 * (b + 1)] = True
+    culled[128 * 156:] = True                       # the ragged last block
+    culled[128 * 40 + 1:128 * 41] = True            # all but one Gaussian of block 40
+    op[culled] = -8.0                               # sigmoid < 1/255
+    mu[128 * 40] = (0.05, 0.02, 4.0)                # ... in front of the first camera
+    op[128 * 40] = 2.0
+    rng = np.random.default_rng(3)                  # block 20: seen by the second camera only
+    mu[128 * 20:128 * 21] = np.c_[rng.uniform(-0.3, 0.3, (128, 2)), np.full(128, 12.0)]
+    op[128 * 20:128 * 21] = 2.0
+    params = dict(params, opacity=op, means=mu)
+    cams = [scenes.look_at((0.0, 0.0, 6.0), (0.0, 0.0, 0.0), 128, 96),
+            scenes.look_at((0.0, 0.0, 10.0), (0.0, 0.0, 20.0), 96, 128)]
+    targets = [scenes.target_image(c.width, c.height, view=i) for i, c in enumerate(cams)]
+    kw = dict(k_max=400_000, sh_dtype=dts[dt], moment_dtype=dts[dt])
+    fus = T.Trainer(params, cams, fused_adam=True, store_grads=True, **kw)
+    ref = T.Trainer(params, cams, fused_adam=False, **kw)
+    assert fus.fused_adam
+    g = torch.Generator(device="cpu").manual_seed(4)
+    for k in GROUPS:
+        m = (torch.rand(fus.exp_avg[k].shape, generator=g) - 0.5) * 1e-2
+        v = torch.rand(fus.exp_avg_sq[k].shape, generator=g) * 1e-4 + 1e-6
+        for tr in (fus, ref):
+            tr.exp_avg[k].copy_(m)
+            tr.exp_avg_sq[k].copy_(v)
+    fus.set_targets(targets)
+    before = {k: fus.params[k].clone() for k in GROUPS}
+    fus.step()
+    torch.cuda.synchronize()
+    for k in GROUPS:
+        ref.grads[k].copy_(fus.grads[k])
+    B.fgs_adam_step_device(ref.p_s, ref.g_s, ref.m_s, ref.v_s, ref.adam_state.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    gm = fus.grads["means"].cpu().numpy()
+    dark = np.zeros(n, bool)                        # blocks with nothing rendered
+    for b in (3, 10, 11, 12, 13, 14, 156):
+        dark[128 * b:128 * (b + 1)] = True
+    assert not np.any(gm[dark])
+    assert np.any(gm[128 * 20:128 * 21]) and np.any(gm[128 * 40:128 * 41])
+    for k in GROUPS:
+        moved = (fus.params[k].reshape(n, -1) != before[k].reshape(n, -1)).any(dim=1).cpu().numpy()
+        assert moved[dark].mean() > 0.99, k         # nonzero moments move them too
+        for got, want in ((fus.params[k], ref.params[k]), (fus.exp_avg[k], ref.exp_avg[k]),
+                          (fus.exp_avg_sq[k], ref.exp_avg_sq[k])):
+            diff = (got != want).reshape(n, -1).any(dim=1).cpu().numpy()
+            assert not diff.any(), (k, np.flatnonzero(diff)[:8])
+
+
 def test_graph_replay_matches_eager():
     params = scenes.tiny_scene(4000, seed=51)
     cams = [scenes.tiny_camera(128, 128)]
