@@ -159,16 +159,20 @@ enum fgs_ws_slot {
 /* Launch choices that change speed, never results: pixels each blend thread
  * owns (1, 2 or 4; the CTA of a 16x16 tile has 256 / that many threads) and
  * list entries staged per shared-memory batch (64, 128 or 256).  Supported
- * pairs: (1,256) (2,128) (2,256) (4,64) (4,128) (4,256).  fgs_workspace_size
- * fills the defaults; an autotuner may overwrite them in the layout before
- * the calls that use it.  The forward and the backward that share a
- * workspace must run with the same choices. */
+ * pairs: (1,256) (2,128) (2,256) (4,64) (4,128) (4,256).  The per-pixel
+ * blend backward may take its own pair (backward_pixels_per_thread,
+ * backward_batch; both 0, the default: the forward's pair).
+ * fgs_workspace_size fills the defaults; an autotuner may overwrite them in
+ * the layout before the calls that use it.  The forward and the backward
+ * that share a workspace must run with the same layout. */
 typedef struct fgs_tuning {
     int32_t blend_pixels_per_thread;
     int32_t blend_batch;
     int32_t blend_schedule;  /* FGS_SCHEDULE_QUEUE (default) or FGS_SCHEDULE_GRID */
     int32_t blend_backward;  /* FGS_BACKWARD_PER_PIXEL (default) or FGS_BACKWARD_PER_GAUSSIAN */
-    int32_t reserved[4];
+    int32_t backward_pixels_per_thread;  /* 0: blend_pixels_per_thread */
+    int32_t backward_batch;              /* 0: blend_batch */
+    int32_t reserved[2];
 } fgs_tuning;
 
 /* Order of the blend backward (the same gradients up to float32 rounding).

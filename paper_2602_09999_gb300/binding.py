@@ -68,7 +68,8 @@ class fgs_params(ctypes.Structure):
 class fgs_tuning(ctypes.Structure):
     _fields_ = [("blend_pixels_per_thread", ctypes.c_int32), ("blend_batch", ctypes.c_int32),
                 ("blend_schedule", ctypes.c_int32), ("blend_backward", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("backward_pixels_per_thread", ctypes.c_int32), ("backward_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 BLEND_CONFIGS = ((1, 256), (2, 128), (2, 256), (4, 64), (4, 128), (4, 256))

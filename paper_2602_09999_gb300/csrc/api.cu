@@ -229,6 +229,9 @@ static int check_layout(void* ws, const fgs_workspace_layout* L, const fgs_camer
         return FGS_ERR_WORKSPACE;
     if (!blend_config_supported(L->tuning.blend_pixels_per_thread, L->tuning.blend_batch))
         return FGS_ERR_ARG;
+    if ((L->tuning.backward_pixels_per_thread || L->tuning.backward_batch) &&
+        !blend_config_supported(L->tuning.backward_pixels_per_thread, L->tuning.backward_batch))
+        return FGS_ERR_ARG;
     if (L->tuning.blend_schedule != FGS_SCHEDULE_QUEUE && L->tuning.blend_schedule != FGS_SCHEDULE_GRID)
         return FGS_ERR_ARG;
     if (L->tuning.blend_backward != FGS_BACKWARD_PER_PIXEL &&
@@ -378,6 +381,17 @@ int fgs_loss_l1_dssim(void* ws, const fgs_workspace_layout* L, const fgs_camera*
 // Blend backward into the screen-gradient records (shared by both backward
 // entry points).  adam (nullable): also prepare that Adam step, in the launch
 // that zeroes the records.
+// The per-pixel blend backward's launch pair: its own when set, else the
+// forward's.
+static int backward_ppt(const fgs_tuning& t)
+{
+    return t.backward_pixels_per_thread ? t.backward_pixels_per_thread : t.blend_pixels_per_thread;
+}
+static int backward_batch(const fgs_tuning& t)
+{
+    return t.backward_pixels_per_thread ? t.backward_batch : t.blend_batch;
+}
+
 static int backward_blend(void* ws, const fgs_workspace_layout* L, const ViewTable& vt, const float bg[3],
                           const float* dl_dimages, fgs_adam_state* adam, cudaStream_t st)
 {
@@ -404,7 +418,7 @@ static int backward_blend(void* ws, const fgs_workspace_layout* L, const ViewTab
                                     slot<float>(ws, L, FGS_WS_T_FINAL),
                                     slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB), sgrad,
                                     slot<uint32_t>(ws, L, FGS_WS_TILE_QUEUE),
-                                    L->tuning.blend_pixels_per_thread, L->tuning.blend_batch,
+                                    backward_ppt(L->tuning), backward_batch(L->tuning),
                                     L->tuning.blend_schedule, st));
 }
 

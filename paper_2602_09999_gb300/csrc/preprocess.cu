@@ -630,11 +630,14 @@ __device__ __forceinline__ void adam_slice(void* p, void* m, void* v, const floa
 // The fused kernel is bound by how many bytes the Adam tail keeps in flight,
 // i.e. by resident CTAs: compiled for 6 per SM (80 registers, a few spilled)
 // it ran 1.11 ms per step on the 3M-Gaussian scene against 1.34 ms at 4 per
-// SM (104 registers) and 1.19-1.24 ms at 7.
+// SM (104 registers) and 1.19-1.24 ms at 7; at 5 (96 registers, no spill)
+// 0.91 against 0.87 ms in z-order.  The motion variant spills twice as much
+// at 6 and runs best at 5: 0.364 against 0.428 ms on the dynamic workload.
 constexpr int kFusedMinBlocks = 6;
+constexpr int kFusedMinBlocksMotion = 5;
 
 template <typename SHT, typename MT, bool FUSED, bool MOTION>
-__global__ void __launch_bounds__(kBwdBlock, FUSED ? kFusedMinBlocks : 1)
+__global__ void __launch_bounds__(kBwdBlock, FUSED ? (MOTION ? kFusedMinBlocksMotion : kFusedMinBlocks) : 1)
 preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float* log_scales,
                       const float* quats, const float* opac, const SHT* sh_dc, const SHT* sh_rest,
                       const fgs_camera* __restrict__ cams, ViewTable vt,

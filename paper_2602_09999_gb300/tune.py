@@ -5,7 +5,11 @@ and the tile schedule -- a work queue in longest-list-first order or one CTA
 per tile; see fgs_tuning in include/fastergs.h) change speed only: every
 choice gives bit-identical images and the same gradients up to atomic-add
 order.  The tuner times forward + loss + backward of the caller's own batch
-shape for each supported choice with CUDA events, keeps the fastest, and
+shape for each supported choice with CUDA events, keeps the fastest, then
+times the per-pixel backward with each other (pixels, batch) pair of its own
+with that choice fixed (the backward's best pair can differ from the
+forward's: it sums each entry's gradients over the warp once per entry, so
+more pixels per thread spread that cost over more pixels), keeps the fastest, and
 caches it in a JSON file keyed by GPU name, Gaussian count and pixel count
 (rounded to powers of two), so later runs of the same shape skip the search.
 """
@@ -44,15 +48,23 @@ def _store(table):
 
 
 def apply(layout, choice):
-    """choice = (pixels per thread, batch[, schedule])."""
+    """choice = (pixels per thread, batch[, schedule[, backward pixels per
+    thread, backward batch]]); a backward pair of (0, 0) or none means the
+    forward's pair."""
     layout.tuning.blend_pixels_per_thread = int(choice[0])
     layout.tuning.blend_batch = int(choice[1])
     layout.tuning.blend_schedule = int(choice[2]) if len(choice) > 2 else B.FGS_SCHEDULE_QUEUE
+    bwd = tuple(choice[3:5]) if len(choice) > 4 else (0, 0)
+    layout.tuning.backward_pixels_per_thread = int(bwd[0])
+    layout.tuning.backward_batch = int(bwd[1])
 
 
 def label(choice) -> str:
     sched = "grid" if len(choice) > 2 and choice[2] == B.FGS_SCHEDULE_GRID else "queue"
-    return f"{choice[0]}x{choice[1]}/{sched}"
+    text = f"{choice[0]}x{choice[1]}/{sched}"
+    if len(choice) > 4 and choice[3]:
+        text += f"+bwd{choice[3]}x{choice[4]}"
+    return text
 
 
 def all_choices():
@@ -66,13 +78,14 @@ def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=None):
     configs = all_choices() if configs is None else [tuple(c) for c in configs]
     key = _key(trainer.n, trainer.views.total_pixels)
     table = _load() if use_cache else {}
-    if key in table and len(table[key].get("choice", [])) == 3:
+    if key in table and len(table[key].get("choice", [])) == 5:
         choice = tuple(table[key]["choice"])
         apply(trainer.rast.layout, choice)
         return choice, table[key].get("ms", {})
     timings = {}
     stream = torch.cuda.current_stream()
-    for cfg in configs:
+
+    def time_choice(cfg):
         apply(trainer.rast.layout, cfg)
         trainer.forward_backward()        # warm-up of this configuration
         t0 = torch.cuda.Event(enable_timing=True)
@@ -83,7 +96,17 @@ def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=None):
         t1.record(stream)
         t1.synchronize()
         timings[label(cfg)] = t0.elapsed_time(t1) / reps
+
+    for cfg in configs:
+        time_choice(cfg)
     best = min(configs, key=lambda c: timings[label(c)])
+    best = tuple(best[:3]) + (0, 0)
+    # then the per-pixel backward's own pair, the forward's choice fixed
+    if trainer.rast.layout.tuning.blend_backward == B.FGS_BACKWARD_PER_PIXEL:
+        own = [best[:3] + tuple(pb) for pb in B.BLEND_CONFIGS if tuple(pb) != tuple(best[:2])]
+        for cfg in own:
+            time_choice(cfg)
+        best = min([best] + own, key=lambda c: timings[label(c)])
     apply(trainer.rast.layout, best)
     if use_cache:
         table[key] = {"choice": list(best), "ms": timings}

@@ -189,6 +189,14 @@ def test_per_gaussian_layout_and_checks(lib):
     with pytest.raises(B.FGSError) as e:
         B.fgs_render_forward(fake_ws, pg, p, 3, cam, 1 << 30, (0, 0, 0), 1 << 31, None)
     assert e.value.code == -9
+    # the backward's own launch pair: (0, 0) by default, else a supported pair
+    pg.tuning.blend_backward = B.FGS_BACKWARD_PER_PIXEL
+    assert (pg.tuning.backward_pixels_per_thread, pg.tuning.backward_batch) == (0, 0)
+    for pair in ((4, 32), (0, 128), (3, 128)):
+        pg.tuning.backward_pixels_per_thread, pg.tuning.backward_batch = pair
+        with pytest.raises(B.FGSError) as e:
+            B.fgs_render_forward(fake_ws, pg, p, 3, cam, 1 << 30, (0, 0, 0), 1 << 31, None)
+        assert e.value.code == -9, pair
 
 
 def test_misaligned_quaternions_rejected(lib):

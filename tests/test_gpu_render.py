@@ -439,7 +439,10 @@ def test_blend_configurations_agree(oracle_mod):
     Lo, go = oracle_grads(cams, params, targets, masks)
     ref_img = None
     from paper_2602_09999_gb300 import tune
-    for cfg in tune.all_choices():
+    # and backward pairs of their own (forward pair, schedule, backward pair)
+    mixed = [(2, 128, B.FGS_SCHEDULE_QUEUE, 4, 128), (4, 64, B.FGS_SCHEDULE_GRID, 1, 256),
+             (1, 256, B.FGS_SCHEDULE_QUEUE, 2, 256)]
+    for cfg in tune.all_choices() + mixed:
         L, gg, rast = gpu_grads(params, cams, targets, masks, tuning=cfg)
         Tf, nc = (x.clone() for x in rast.per_pixel())
         if ref_img is None:
@@ -506,7 +509,9 @@ def test_autotuner_picks_a_supported_configuration(tmp_path, monkeypatch):
     tr = T.Trainer(params, [scenes.tiny_camera(128, 96)], k_max=200_000)
     choice, ms = tune.autotune(tr, reps=1)
     assert tuple(choice[:2]) in B.BLEND_CONFIGS and choice[2] in B.BLEND_SCHEDULES
-    assert len(ms) == len(B.BLEND_CONFIGS) * len(B.BLEND_SCHEDULES)
+    assert tuple(choice[3:5]) == (0, 0) or tuple(choice[3:5]) in B.BLEND_CONFIGS
+    # every forward choice, then the backward's other pairs
+    assert len(ms) == len(B.BLEND_CONFIGS) * len(B.BLEND_SCHEDULES) + len(B.BLEND_CONFIGS) - 1
     again, _ = tune.autotune(tr)           # cached
     assert tuple(again) == tuple(choice)
 
@@ -515,6 +520,12 @@ def test_unsupported_configuration_is_rejected():
     params = scenes.tiny_scene(100, seed=73)
     rast, views, t, images = gpu_forward(params, [scenes.tiny_camera(32, 32)])
     rast.layout.tuning.blend_pixels_per_thread = 3
+    with pytest.raises(B.FGSError) as e:
+        rast.forward(T.params_struct(t), 3, (0, 0, 0), images)
+    assert e.value.code == -9
+    rast.layout.tuning.blend_pixels_per_thread = 2
+    rast.layout.tuning.backward_pixels_per_thread = 4
+    rast.layout.tuning.backward_batch = 32       # not a supported pair
     with pytest.raises(B.FGSError) as e:
         rast.forward(T.params_struct(t), 3, (0, 0, 0), images)
     assert e.value.code == -9
