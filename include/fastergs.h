@@ -131,7 +131,9 @@ enum fgs_ws_slot {
     FGS_WS_N_CONTRIB,   /* uint32 [total_pixels]: list position of the last blended entry */
     FGS_WS_SCREEN_GRAD, /* 48-byte records [n_views*n]: float4 (dL/dmu2D, dL/dSigma2D 00, 01),
                            float4 (dL/dSigma2D 11, dL/do, dL/dr, dL/dg), float4 (dL/db, 0, 0, 0);
-                           dL/dSigma2D is the full symmetric gradient */
+                           dL/dSigma2D is the full symmetric gradient.  The backward clears
+                           only the records of 128-Gaussian blocks with a rendered pair in
+                           that view; the others keep whatever they held */
     FGS_WS_LOSS_MAPS,   /* float [9*total_pixels]: SSIM partial-derivative maps */
     FGS_WS_LOSS_PART,   /* double [loss blocks*2]: per-CTA L1 / SSIM sums */
     FGS_WS_N_BLENDED,   /* uint32 [total_pixels]: fragments blended into each pixel */

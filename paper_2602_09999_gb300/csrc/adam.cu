@@ -40,16 +40,31 @@ __device__ void adam_prepare(fgs_adam_state* st)
 
 __global__ void adam_prepare_kernel(fgs_adam_state* st) { adam_prepare(st); }
 
-// Zeroes n4 16-byte words while thread 0 of CTA 0 prepares the Adam step:
-// the double-precision scalars take one thread about as long as the zeroing
-// takes the whole grid, so the two share one launch.
+// Zeroes the screen-gradient records of every (view, 128-Gaussian block)
+// with a rendered pair, one warp per (view, block); thread 0 of CTA 0 also
+// prepares the Adam step (st non-null): the double-precision scalars take
+// one thread about as long as the clear takes the grid, so the two share one
+// launch.  Those records are the only ones the blend backward adds to and
+// the preprocess backward reads (a pair is visible exactly when it is
+// rendered).  block_sum: the forward's exclusive prefixes of rendered pairs
+// per (view, block), view-major; total: their sum.
 __global__ void __launch_bounds__(256)
-zero_prepare_kernel(float4* __restrict__ dst, int64_t n4, fgs_adam_state* st)
+zero_prepare_kernel(float4* __restrict__ dst, const uint32_t* __restrict__ block_sum,
+                    const uint32_t* __restrict__ total, int64_t n, int nv, fgs_adam_state* st)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) adam_prepare(st);
+    if (st && blockIdx.x == 0 && threadIdx.x == 0) adam_prepare(st);
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = z;
+    const int64_t nblk = (n + kPreBlock - 1) / kPreBlock, pairs = nv * nblk;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < pairs; k += nwarps) {
+        const uint32_t end = k + 1 < pairs ? block_sum[k + 1] : *total;
+        if (end == block_sum[k]) continue;
+        const int64_t v = k / nblk, i0 = (k - v * nblk) * kPreBlock;
+        const int64_t words = 3 * min((int64_t)kPreBlock, n - i0);  // three 16-byte words a record
+        float4* base = dst + 3 * (v * n + i0);
+        for (int64_t w = lane; w < words; w += 32) base[w] = z;
+    }
 }
 
 template <typename PT, typename MT>
@@ -120,16 +135,17 @@ static cudaError_t launch_m(int mdt, int64_t count, void* p, const float* g, voi
     }
 }
 
-// dst: 16-byte aligned, bytes a multiple of 16.
-cudaError_t launch_zero_and_adam_prepare(void* dst, size_t bytes, fgs_adam_state* ds, cudaStream_t st)
+// sgrad: the [n_views * n] screen-gradient records; ds nullable.
+cudaError_t launch_zero_and_adam_prepare(ScreenGrad* sgrad, const uint32_t* block_sum, const uint32_t* total,
+                                         int64_t n, int nv, fgs_adam_state* ds, cudaStream_t st)
 {
-    const int64_t n4 = (int64_t)(bytes / 16);
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t need = (n4 + 255) / 256, cap = (int64_t)sms * 8;
+    const int64_t pairs = (int64_t)nv * ((n + kPreBlock - 1) / kPreBlock);
+    const int64_t need = (pairs + 7) / 8, cap = (int64_t)sms * 8;  // 8 warps a CTA
     const int grid = (int)(need < 1 ? 1 : (need < cap ? need : cap));
-    zero_prepare_kernel<<<grid, 256, 0, st>>>((float4*)dst, n4, ds);
+    zero_prepare_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<float4*>(sgrad), block_sum, total, n, nv, ds);
     profile_mark(st, "zero_screen_grads");
     return cudaGetLastError();
 }

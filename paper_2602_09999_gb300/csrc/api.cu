@@ -57,7 +57,8 @@ cudaError_t launch_adam_group(int64_t count, int pdt, int mdt, void* p, const fl
                               void* v, float step_size, float inv_bc2_sqrt, double b1, double b2,
                               double eps, const fgs_adam_state* ds, int grp, cudaStream_t st);
 cudaError_t launch_adam_prepare(fgs_adam_state* ds, cudaStream_t st);
-cudaError_t launch_zero_and_adam_prepare(void* dst, size_t bytes, fgs_adam_state* ds, cudaStream_t st);
+cudaError_t launch_zero_and_adam_prepare(ScreenGrad* sgrad, const uint32_t* block_sum, const uint32_t* total,
+                                         int64_t n, int nv, fgs_adam_state* ds, cudaStream_t st);
 cudaError_t launch_preprocess_bwd_adam(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
                                        const ViewTable& vt, const Screen* screen, const ScreenGrad* sgrad,
                                        const fgs_params* g, const fgs_params* m, const fgs_params* v,
@@ -399,13 +400,12 @@ static int backward_blend(void* ws, const fgs_workspace_layout* L, const ViewTab
     const uint32_t* svals = slot<uint32_t>(ws, L, L->sorted_in_alt ? FGS_WS_VALS_ALT : FGS_WS_VALS);
     Screen* screen = slot<Screen>(ws, L, FGS_WS_SCREEN);
     ScreenGrad* sgrad = slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD);
-    if (adam) {
-        if (launch_zero_and_adam_prepare(sgrad, L->bytes[FGS_WS_SCREEN_GRAD], adam, st) != cudaSuccess)
-            return FGS_ERR_CUDA;
-    } else {
-        if (cudaMemsetAsync(sgrad, 0, L->bytes[FGS_WS_SCREEN_GRAD], st) != cudaSuccess) return FGS_ERR_CUDA;
-        profile_mark(st, "zero_screen_grads");
-    }
+    // clears the records of the (view, block)s with a rendered pair (and
+    // prepares the Adam step of the fused call)
+    if (launch_zero_and_adam_prepare(sgrad, slot<uint32_t>(ws, L, FGS_WS_BLOCK_SUM),
+                                     &slot<WsHeader>(ws, L, FGS_WS_HEADER)->counters[1], n, vt.n_views, adam,
+                                     st) != cudaSuccess)
+        return FGS_ERR_CUDA;
     if (L->tuning.blend_backward == FGS_BACKWARD_PER_GAUSSIAN)
         return cuda_rc(launch_blend_bwd_pg(vt, n, slot<uint2>(ws, L, FGS_WS_RANGES), svals, screen, dl_dimages,
                                            slot<uint32_t>(ws, L, FGS_WS_N_CONTRIB),
