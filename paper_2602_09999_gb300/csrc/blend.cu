@@ -17,7 +17,8 @@
 // from the largest last-contributor position of its pixels; each pixel
 // recovers T_i = T_{i+1} / (1 - alpha_i) and the colour behind it,
 // A_i = alpha_{i+1} c_{i+1} + (1 - alpha_{i+1}) A_{i+1} (A = bg behind the
-// last), so dC/dalpha_i = T_i (c_i - A_i) and dC/dc_i = alpha_i T_i.  The 9
+// last), so dC/dalpha_i = T_i (c_i - A_i) and dC/dc_i = alpha_i T_i; only
+// the scalar g . A_i is kept, g = dL/dC of the pixel.  The 9
 // per-fragment gradients are summed over the warp with shuffles, over the
 // CTA with shared-memory atomics, and leave the CTA as one set of global
 // vector atomics per (instance, CTA).
@@ -428,22 +429,24 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
     const int64_t P = (int64_t)tm.W * tm.H;
     const float* dl = dL_dimg + 3 * vt.pix_off[tm.v];
 
-    float T[PPT], g0[PPT], g1[PPT], g2[PPT], A0[PPT], A1[PPT], A2[PPT];
+    // S = g . A: the colour behind the entry (A, normalised by T after the
+    // entry; bg behind the last) enters the gradients only through its dot
+    // product with the pixel's dL/dC = g, so one scalar replaces A
+    float T[PPT], g0[PPT], g1[PPT], g2[PPT], S[PPT];
     uint32_t last[PPT];
     uint32_t my_max = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         T[k] = 1.0f;
         g0[k] = g1[k] = g2[k] = 0.f;
+        S[k] = 0.f;
         last[k] = 0;
-        A0[k] = bg0;  // colour behind, normalised by T after the entry
-        A1[k] = bg1;
-        A2[k] = bg2;
         if (tm.inside[k]) {
             const int64_t pix = (int64_t)tm.py[k] * tm.W + tm.px[k];
             g0[k] = dl[pix];
             g1[k] = dl[P + pix];
             g2[k] = dl[2 * P + pix];
+            S[k] = g0[k] * bg0 + g1[k] * bg1 + g2[k] * bg2;
             T[k] = T_final[vt.pix_off[tm.v] + pix];
             last[k] = n_contrib[vt.pix_off[tm.v] + pix];
             my_max = max(my_max, last[k]);
@@ -493,14 +496,12 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
                 // transmittance in front of the entry; 1 - alpha >= 0.01, so the
                 // approximate divide (2 ulp) is in range
                 const float Ti = __fdividef(T[k], 1.0f - f.alpha);
-                // colour minus colour behind, shared by dL/dalpha and the update of
-                // the colour behind, A <- A + alpha (c - A)
-                const float c0 = e.rgbo.x - A0[k], c1 = e.rgbo.y - A1[k], c2 = e.rgbo.z - A2[k];
-                const float dalpha = Ti * (g0[k] * c0 + g1[k] * c1 + g2[k] * c2);
+                // g . (c - A), shared by dL/dalpha and the update of the colour
+                // behind, A <- A + alpha (c - A)
+                const float gc = g0[k] * e.rgbo.x + g1[k] * e.rgbo.y + g2[k] * e.rgbo.z - S[k];
+                const float dalpha = Ti * gc;
                 frag_grads(e, f, u, w, dalpha, f.alpha * Ti, g0[k], g1[k], g2[k], d);
-                A0[k] += f.alpha * c0;
-                A1[k] += f.alpha * c1;
-                A2[k] += f.alpha * c2;
+                S[k] += f.alpha * gc;
                 T[k] = Ti;
             }
             if (!__any_sync(0xffffffffu, any)) continue;

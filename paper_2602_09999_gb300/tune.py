@@ -9,7 +9,8 @@ shape for each supported choice with CUDA events, keeps the fastest, then
 times the per-pixel backward with each other (pixels, batch) pair of its own
 with that choice fixed (the backward's best pair can differ from the
 forward's: it sums each entry's gradients over the warp once per entry, so
-more pixels per thread spread that cost over more pixels), keeps the fastest, and
+more pixels per thread spread that cost over more pixels), then the
+forward's other pairs with the backward's fixed, keeps the fastest, and
 caches it in a JSON file keyed by GPU name, Gaussian count and pixel count
 (rounded to powers of two), so later runs of the same shape skip the search.
 """
@@ -107,6 +108,12 @@ def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=None):
         for cfg in own:
             time_choice(cfg)
         best = min([best] + own, key=lambda c: timings[label(c)])
+        # and the forward's pair once more, the backward's pair fixed
+        bwd = tuple(best[3:5]) if best[3] else tuple(best[:2])
+        fwd = [tuple(pb) + (best[2],) + bwd for pb in B.BLEND_CONFIGS if tuple(pb) != tuple(best[:2])]
+        for cfg in fwd:
+            time_choice(cfg)
+        best = min([best] + fwd, key=lambda c: timings[label(c)])
     apply(trainer.rast.layout, best)
     if use_cache:
         table[key] = {"choice": list(best), "ms": timings}

@@ -510,8 +510,8 @@ def test_autotuner_picks_a_supported_configuration(tmp_path, monkeypatch):
     choice, ms = tune.autotune(tr, reps=1)
     assert tuple(choice[:2]) in B.BLEND_CONFIGS and choice[2] in B.BLEND_SCHEDULES
     assert tuple(choice[3:5]) == (0, 0) or tuple(choice[3:5]) in B.BLEND_CONFIGS
-    # every forward choice, then the backward's other pairs
-    assert len(ms) == len(B.BLEND_CONFIGS) * len(B.BLEND_SCHEDULES) + len(B.BLEND_CONFIGS) - 1
+    # every choice, then the backward's other pairs, then the forward's
+    assert len(ms) == len(B.BLEND_CONFIGS) * len(B.BLEND_SCHEDULES) + 2 * (len(B.BLEND_CONFIGS) - 1)
     again, _ = tune.autotune(tr)           # cached
     assert tuple(again) == tuple(choice)
 
