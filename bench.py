@@ -222,7 +222,7 @@ def algorithmic_bytes(label, n, views, instances, pixels, sh_bytes, moment_bytes
 # quadratic form, exp2 argument, o G: 12), and per blended fragment the
 # forward's accumulation (9) or the backward's adjoint (T recovery, dalpha,
 # colour behind, nine gradient terms: 50).
-BLEND_FLOPS = {"blend_fwd": (12, 9), "blend_bwd": (12, 50)}
+BLEND_FLOPS = {"blend_fwd": (12, 9), "blend_bwd": (12, 42)}
 
 
 # DRAM bytes per launch measured with ncu at the default workload (3M
@@ -230,7 +230,7 @@ BLEND_FLOPS = {"blend_fwd": (12, 9), "blend_bwd": (12, 50)}
 # profiles/dram_outdoor_3M_1237x822.md), for the roofline's "traffic" field.
 # Reported only for that workload, order and launch configuration; a change
 # to one of these kernels must refresh or drop its entry.
-PROFILED_DRAM_BYTES = {"preprocess_bwd_adam": 4.492e9, "blend_fwd": 2.28e7, "blend_bwd": 4.81e7}
+PROFILED_DRAM_BYTES = {"preprocess_bwd_adam": 4.492e9, "blend_fwd": 2.27e7, "blend_bwd": 4.80e7}
 PROFILED_WORKLOAD = (3_000_000, 1237, 822)
 # the paper re-applies the z-order every 5000 iterations (Sec. 3.3)
 MORTON_PERIOD = 5000
