@@ -258,7 +258,8 @@ int fgs_loss_l1_dssim(void *ws, const fgs_workspace_layout *layout, const fgs_ca
                       const float *images, const float *targets, float lambda, float *loss_out,
                       float *dl_dimages, void *stream);
 
-/* Backward pass: zero the screen-gradient accumulators, re-traverse every
+/* Backward pass: zero the screen-gradient accumulators of the blocks of
+ * 128 Gaussians with a rendered pair in the forward, re-traverse every
  * tile back to front from each pixel's last contributor (recovering T by
  * division, Suppl. B.1), reduce per-Gaussian gradients across each warp
  * and CTA before global atomics, then the chain rule of the preprocessing
