@@ -40,9 +40,10 @@ def test_library_exports_every_declared_function(lib):
 def test_struct_sizes_match_c(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "fastergs.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(fgs_camera),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(fgs_camera),'
                    ' sizeof(fgs_params), sizeof(fgs_workspace_layout), sizeof(fgs_adam_state),'
-                   ' offsetof(fgs_adam_state, step_size), offsetof(fgs_workspace_layout, tuning));'
+                   ' offsetof(fgs_adam_state, step_size), offsetof(fgs_workspace_layout, tuning),'
+                   ' offsetof(fgs_tuning, backward_pixels_per_thread), offsetof(fgs_tuning, backward_batch));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -52,7 +53,9 @@ def test_struct_sizes_match_c(tmp_path):
                                      ctypes.sizeof(B.fgs_workspace_layout),
                                      ctypes.sizeof(B.fgs_adam_state),
                                      B.fgs_adam_state.step_size.offset,
-                                     B.fgs_workspace_layout.tuning.offset]
+                                     B.fgs_workspace_layout.tuning.offset,
+                                     B.fgs_tuning.backward_pixels_per_thread.offset,
+                                     B.fgs_tuning.backward_batch.offset]
 
 
 def test_workspace_layout(lib):
@@ -209,3 +212,26 @@ def test_misaligned_quaternions_rejected(lib):
     with pytest.raises(B.FGSError) as e:
         B.fgs_render_forward(ctypes.c_void_p(1 << 20), L, p, 3, cam, 1 << 30, (0, 0, 0), 1 << 31, None)
     assert e.value.code == -8
+
+
+def test_tuning_choice_encoding(lib):
+    """The autotuner's choice tuples map onto the layout's launch fields: a
+    backward pair of (0, 0), or none, means the forward's pair; labels name
+    every field that is set, so the three tuning passes never share one."""
+    from paper_2602_09999_gb300 import tune
+    cam = B.camera_array([scenes.tiny_camera(100, 70)])
+    layout = B.fgs_workspace_size(1000, cam, 1, 64_000)
+    t = layout.tuning
+    tune.apply(layout, (4, 64, B.FGS_SCHEDULE_GRID, 2, 256))
+    assert (t.blend_pixels_per_thread, t.blend_batch, t.blend_schedule) == (4, 64, B.FGS_SCHEDULE_GRID)
+    assert (t.backward_pixels_per_thread, t.backward_batch) == (2, 256)
+    tune.apply(layout, (2, 128))
+    assert (t.blend_schedule, t.backward_pixels_per_thread, t.backward_batch) == (B.FGS_SCHEDULE_QUEUE, 0, 0)
+    assert tune.label((2, 128, 0, 0, 0)) == tune.label((2, 128, 0)) == "2x128/queue"
+    assert tune.label((2, 128, 1, 4, 64)) == "2x128/grid+bwd4x64"
+    first = [tuple(c) + (0, 0) for c in tune.all_choices()]
+    best = (2, 128, 0)
+    second = [best + tuple(pb) for pb in B.BLEND_CONFIGS if tuple(pb) != best[:2]]
+    third = [tuple(pb) + (0, 4, 64) for pb in B.BLEND_CONFIGS if tuple(pb) != best[:2]]
+    labels = [tune.label(c) for c in first + second + third]
+    assert len(set(labels)) == len(labels)
