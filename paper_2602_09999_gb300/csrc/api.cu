@@ -379,9 +379,6 @@ int fgs_loss_l1_dssim(void* ws, const fgs_workspace_layout* L, const fgs_camera*
                                (cudaStream_t)stream));
 }
 
-// Blend backward into the screen-gradient records (shared by both backward
-// entry points).  adam (nullable): also prepare that Adam step, in the launch
-// that zeroes the records.
 // The per-pixel blend backward's launch pair: its own when set, else the
 // forward's.
 static int backward_ppt(const fgs_tuning& t)
@@ -393,6 +390,9 @@ static int backward_batch(const fgs_tuning& t)
     return t.backward_pixels_per_thread ? t.backward_batch : t.blend_batch;
 }
 
+// Blend backward into the screen-gradient records (shared by both backward
+// entry points).  adam (nullable): also prepare that Adam step, in the launch
+// that zeroes the records.
 static int backward_blend(void* ws, const fgs_workspace_layout* L, const ViewTable& vt, const float bg[3],
                           const float* dl_dimages, fgs_adam_state* adam, cudaStream_t st)
 {

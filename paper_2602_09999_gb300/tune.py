@@ -76,7 +76,8 @@ def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=None):
     """Picks the fastest blend configuration for `trainer`'s batch shape and
     writes it into its workspace layout.  Runs forward, loss and backward
     only (the parameters are not updated).  Returns (choice, timings_ms)."""
-    configs = all_choices() if configs is None else [tuple(c) for c in configs]
+    configs = all_choices() if configs is None else [
+        (tuple(c) + (B.FGS_SCHEDULE_QUEUE,))[:3] for c in configs]
     key = _key(trainer.n, trainer.views.total_pixels)
     table = _load() if use_cache else {}
     if key in table and len(table[key].get("choice", [])) == 5:
