@@ -177,7 +177,8 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
-# algorithmic bytes per launch of the HBM-bound kernels
+# algorithmic bytes per launch of the HBM-bound kernels: what each must read
+# or write at least once, from the workload's sizes
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(label, n, views, instances, pixels, sh_bytes, moment_bytes, visible):
     """Bytes a kernel must move at least once, per launch."""
@@ -220,8 +221,8 @@ def algorithmic_bytes(label, n, views, instances, pixels, sh_bytes, moment_bytes
 # FP32 operations per unit of the blend kernels (an FMA counts 2): one alpha
 # evaluation per list position up to a pixel's last contributor (offset,
 # quadratic form, exp2 argument, o G: 12), and per blended fragment the
-# forward's accumulation (9) or the backward's adjoint (T recovery, dalpha,
-# colour behind, nine gradient terms: 50).
+# forward's accumulation (9) or the backward's adjoint (T recovery, dalpha
+# through g . (c - A) and the update of g . A, nine gradient terms: 42).
 BLEND_FLOPS = {"blend_fwd": (12, 9), "blend_bwd": (12, 42)}
 
 
