@@ -67,6 +67,7 @@ def parse_args():
     ap.add_argument("--small", action="store_true",
                     help="small case for profiler captures (300k Gaussians)")
     ap.add_argument("--phase-report", default="", help="write per-kernel timings to this file")
+    ap.add_argument("--detail", default="", help="write every result in full to this JSON file")
     ap.add_argument("--kmax", type=int, default=0,
                     help="instance capacity; 0 = probe every camera and add 25%%")
     return ap.parse_args()
@@ -185,9 +186,15 @@ def algorithmic_bytes(label, n, views, instances, pixels, sh_bytes, moment_bytes
     if label == "adam":
         return None  # per group; handled by the caller
     if label == "preprocess_fwd":
-        return n * 44 + visible * 48 * sh_bytes / 4 + views * n * (48 + 8 + 4)
+        # geometry of every Gaussian, the 48 SH coefficients of each rendered
+        # pair, and per (view, Gaussian) the screen record, the tile record and
+        # the compaction offset
+        return n * 44 + visible * 48 * sh_bytes + views * n * (48 + 16 + 4)
     if label == "preprocess_bwd":
-        return n * 44 + views * n * 48 * 2 + visible * 48 * sh_bytes / 4 + n * 236
+        # the 45 sh_rest coefficients of each rendered pair (sh_dc's gradient
+        # needs no coefficient), screen and screen-gradient records, and the
+        # gradient of every parameter
+        return n * 44 + views * n * 48 * 2 + visible * 45 * sh_bytes + n * 236
     if label == "preprocess_bwd_adam":
         # visibility words of every (view, Gaussian), the rest of the screen
         # and screen-gradient records of visible ones, and the Adam step of
@@ -226,11 +233,11 @@ def algorithmic_bytes(label, n, views, instances, pixels, sh_bytes, moment_bytes
 BLEND_FLOPS = {"blend_fwd": (12, 9), "blend_bwd": (12, 42)}
 
 
-# DRAM bytes per launch measured with ncu at the default workload (3M
-# Gaussians in z-order, one 1237x822 view;
-# profiles/dram_outdoor_3M_1237x822.md), for the roofline's "traffic" field.
-# Reported only for that workload, order and launch configuration; a change
-# to one of these kernels must refresh or drop its entry.
+# DRAM bytes per launch measured with ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) at the default workload (3M Gaussians in z-order,
+# one 1237x822 view), for the roofline's "traffic" field.  Reported only for
+# that workload, order and launch configuration; a change to one of these
+# kernels must refresh or drop its entry.
 PROFILED_DRAM_BYTES = {"preprocess_bwd_adam": 4.492e9, "blend_fwd": 2.27e7, "blend_bwd": 4.80e7}
 PROFILED_WORKLOAD = (3_000_000, 1237, 822)
 # the paper re-applies the z-order every 5000 iterations (Sec. 3.3)
@@ -610,6 +617,9 @@ def run_ours(args, dist):
         del tb
 
     uneven = None if args.no_batched else run_uneven(args, dist, stream, params, views_per_s)
+    uneven16 = None if args.no_batched else run_uneven(args, dist, stream, params, views_per_s,
+                                                       dtype="fp16")
+    indoor = None if (args.no_batched or args.small) else run_indoor(args, dist, stream)
     dynamic = None if args.no_dynamic else run_dynamic(args, dist, stream, profile_pass, per_step_ms)
 
     return dict(tuned=list(tuned[0]) if tuned else None, tuning_ms=tuned[1] if tuned else None,
@@ -620,7 +630,7 @@ def run_ours(args, dist):
                 roofline=roofline, clocks=clocks, e2e=e2e, batched=batched, dynamic=dynamic,
                 k_max=k_max, instances_last=inst_last, visible_last=visible_est, n=n,
                 morton=morton, per_gaussian=per_gaussian, blend_roofline=blend_roofline,
-                uneven=uneven)
+                uneven=uneven, uneven_fp16=uneven16, indoor=indoor)
 
 
 def measure_blend_peaks(torch, B, stream, dev):
@@ -681,11 +691,12 @@ def reorder_once(tr, stream):
 # ---------------------------------------------------------------------------
 # the dynamic (4D) workload
 # ---------------------------------------------------------------------------
-def run_uneven(args, dist, stream, params, plain_views_per_s, pool=25):
+def run_uneven(args, dist, stream, params, plain_views_per_s, pool=25, dtype="bf16"):
     """The precision variant's batch: four views of uneven sizes (1237x822,
-    960x640, 1600x1064, 640x426) per step, bf16 SH parameters and moments,
-    captured as a CUDA graph; new orbit poses every step from a pool of
-    camera sets.  Reported in views/s and megapixels/s."""
+    960x640, 1600x1064, 640x426) per step, SH parameters and Adam moments in
+    `dtype` (bf16, or fp16 for the variant's second run), captured as a CUDA
+    graph; new orbit poses every step from a pool of camera sets.  Reported
+    in views/s and megapixels/s."""
     import torch
 
     from paper_2602_09999_gb300 import binding as B
@@ -700,8 +711,8 @@ def run_uneven(args, dist, stream, params, plain_views_per_s, pool=25):
     table = torch.frombuffer(bytearray(b"".join(bytes(B.camera_array(cs)) for cs in sets)),
                              dtype=torch.uint8).cuda()
     targets = [scenes.target_image(w, h, view=i) for i, (w, h) in enumerate(sizes)]
-    probe = T.Trainer(params, sets[0], k_max=64_000_000, sh_dtype=torch.bfloat16,
-                      moment_dtype=torch.bfloat16)
+    tdt = {"bf16": torch.bfloat16, "fp16": torch.float16}[dtype]
+    probe = T.Trainer(params, sets[0], k_max=64_000_000, sh_dtype=tdt, moment_dtype=tdt)
     kmax_seen = 0
     for s in range(pool):
         probe.views.device.copy_(table[s * cam_bytes:(s + 1) * cam_bytes])
@@ -710,10 +721,13 @@ def run_uneven(args, dist, stream, params, plain_views_per_s, pool=25):
     del probe
     torch.cuda.empty_cache()
     tr = T.Trainer(params, sets[0], k_max=int(kmax_seen * 1.25) + 4096, lam=0.2,
-                   sh_dtype=torch.bfloat16, moment_dtype=torch.bfloat16)
+                   sh_dtype=tdt, moment_dtype=tdt)
     tr.set_targets(targets)
     if not args.no_morton:
         reorder_once(tr, stream)
+    if not args.no_tune:
+        from paper_2602_09999_gb300 import tune
+        tune.autotune(tr, reps=2)
 
     def load(i):
         s = i % pool
@@ -744,8 +758,81 @@ def run_uneven(args, dist, stream, params, plain_views_per_s, pool=25):
     out = {"views_per_s": round(vps, 3), "megapixels_per_s": round(vps / nv * mpx, 3),
            "ms_per_step": round(ms / steps, 4), "views_per_step": nv,
            "resolutions": [f"{w}x{h}" for w, h in sizes], "graph": True,
-           "storage": "bf16 SH parameters, bf16 Adam moments", "steps": steps,
-           "plain_megapixels_per_s": round(plain_views_per_s * args.width * args.height / 1e6, 3)}
+           "storage": f"{dtype} SH parameters, {dtype} Adam moments", "steps": steps,
+           "mpx_ratio_vs_plain": round(vps / nv * mpx / (plain_views_per_s * args.width * args.height
+                                                         / 1e6), 4)}
+    del tr
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_indoor(args, dist, stream, n=2_500_000, views=8, pool=12):
+    """The indoor-shaped batched workload: 2.5M Gaussians in a 10x4x8 box
+    (60% near the walls), B = 8 in-room views of 1264x832 per step, float32
+    storage, forward + loss + backward + fused Adam captured as one CUDA
+    graph, blend launch choices from the autotuner.  Every step takes a new
+    set of in-room poses from a pool (the graph fixes only the view sizes)."""
+    import torch
+
+    from paper_2602_09999_gb300 import binding as B
+    from paper_2602_09999_gb300 import scenes
+    from paper_2602_09999_gb300 import train as T
+
+    torch.cuda.empty_cache()
+    params = scenes.indoor_scene(n, seed=0)
+    W, H = 1264, 832
+    sets = [scenes.indoor_cameras(views, W, H, seed=2 + s) for s in range(pool)]
+    cam_bytes = ctypes.sizeof(B.fgs_camera) * views
+    table = torch.frombuffer(bytearray(b"".join(bytes(B.camera_array(cs)) for cs in sets)),
+                             dtype=torch.uint8).cuda()
+    targets = [scenes.target_image(W, H, view=i) for i in range(views)]
+    probe = T.Trainer(params, sets[0], k_max=96_000_000)
+    kmax_seen = 0
+    for s in range(pool):
+        probe.views.device.copy_(table[s * cam_bytes:(s + 1) * cam_bytes])
+        probe.forward_only()
+        kmax_seen = max(kmax_seen, probe.rast.error(clear=True)[1])
+    del probe
+    torch.cuda.empty_cache()
+    tr = T.Trainer(params, sets[0], k_max=int(kmax_seen * 1.25) + 4096, lam=0.2)
+    tr.set_targets(targets)
+    if not args.no_morton:
+        reorder_once(tr, stream)
+    tuned = None
+    if not args.no_tune:
+        from paper_2602_09999_gb300 import tune
+        tuned = tune.autotune(tr, reps=2)
+
+    def load(i):
+        s = i % pool
+        tr.views.device.copy_(table[s * cam_bytes:(s + 1) * cam_bytes])
+
+    load(0)
+    tr.capture(warmup=2)
+    for i in range(args.warmup):
+        load(i)
+        tr.replay()
+    torch.cuda.synchronize()
+    if tr.rast.error()[0]:
+        raise RuntimeError("device flags in the indoor batch")
+    steps = max(10, args.steps // views)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        load(args.warmup + i)
+        tr.replay()
+    e1.record(stream)
+    e1.synchronize()
+    ms = dist.max(e0.elapsed_time(e1))
+    if tr.rast.error()[0]:
+        raise RuntimeError("device flags in the indoor batch")
+    out = {"views_per_s": round(dist.world * steps * views / (ms / 1000.0), 3),
+           "ms_per_step": round(ms / steps, 4), "views_per_step": views, "resolution": f"{W}x{H}",
+           "gaussians": n, "storage": "float32", "graph": True, "steps": steps,
+           "blend_config": list(tuned[0]) if tuned else None}
     del tr
     torch.cuda.empty_cache()
     return out
@@ -934,18 +1021,53 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded outdoor-shaped scene, orbit cameras, uniform targets)",
                 "config": config_dict(args, n), "clocks": r["clocks"], "e2e": r["e2e"],
-                "gpu_launches": r["launches"], "roofline": r["roofline"], "cpu_baseline": cpu,
-                "batched": r["batched"], "dynamic": r["dynamic"], "blend_config": r["tuned"],
-                "blend_config_ms": r["tuning_ms"], "kernel_ms_per_step": r["phase_ms"],
-                "instances_last_step": r["instances_last"], "k_max": r["k_max"],
-                "morton": r["morton"], "per_gaussian_backward": r["per_gaussian"],
-                "blend_roofline": r["blend_roofline"], "batched_uneven": r["uneven"]}
+                "gpu_launches": r["launches"], "roofline": r["roofline"], "cpu_baseline": cpu}
+        line.update(compact_extras(r))
         print(json.dumps(line), flush=True)
+        if args.detail:
+            with open(args.detail, "w") as f:
+                json.dump(dict(r, cpu_baseline=cpu), f, indent=1)
         if args.phase_report:
             with open(args.phase_report, "w") as f:
                 json.dump(r["phase_ms"], f, indent=1)
     dist.close()
     return 0
+
+
+def compact_extras(r):
+    """The variants in short form, the batched ones last, so that the end
+    of the printed line carries the batched ratios (the full results go to
+    --detail)."""
+    def pick(d, keys):
+        return None if d is None else {k: d[k] for k in keys if k in d}
+
+    out = {"blend_config": r["tuned"], "k_max": r["k_max"],
+           "instances_last_step": r["instances_last"],
+           "kernel_ms_per_step": {k: round(v, 4) for k, v in list(r["phase_ms"].items())[:9]}}
+    br = r["blend_roofline"]
+    if br:
+        out["blend_roofline"] = {
+            name: {"ms": br[name]["avg_launch_ms"], "fp32_frac": br[name]["fp32"]["frac"],
+                   "ex2_frac": br[name]["ex2"]["frac"], "l2_frac": br[name]["l2"]["frac"]}
+            for name in ("blend_fwd", "blend_bwd")}
+        out["blend_roofline"]["peaks"] = {k: v for k, v in br["peaks_measured"].items() if k != "how"}
+    out["morton"] = pick(r["morton"], ("reorder_ms", "ms_per_million"))
+    out["per_gaussian_backward"] = pick(r["per_gaussian"], ("ms_per_step", "ratio_vs_per_pixel"))
+    out["dynamic"] = pick(r["dynamic"], ("views_per_s", "ms_per_step", "views_per_step",
+                                         "megapixels_per_s"))
+    batched = {}
+    for e in r["batched"]:
+        batched[f"b{e['views_per_step']}_bf16_graph"] = pick(
+            e, ("views_per_s", "ms_per_step", "blend_config", "ratio_vs_plain"))
+    if r["indoor"]:
+        batched["indoor_b8_f32_graph"] = pick(r["indoor"], ("views_per_s", "ms_per_step",
+                                                            "resolution", "blend_config"))
+    for name, e in (("uneven_b4_bf16_graph", r["uneven"]), ("uneven_b4_fp16_graph", r["uneven_fp16"])):
+        if e:
+            batched[name] = pick(e, ("views_per_s", "megapixels_per_s", "ms_per_step",
+                                     "mpx_ratio_vs_plain"))
+    out["batched"] = batched
+    return out
 
 
 if __name__ == "__main__":

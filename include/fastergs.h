@@ -14,9 +14,9 @@
  *    as long as the view sizes stay the same between replays.
  *  - Return value: FGS_OK (0) or a negative FGS_ERR_* code for an error the
  *    host can see (bad pointer, shape, degree, dtype, workspace size, launch
- *    failure).  Errors found on the device (instance capacity exceeded)
- *    set sticky bits in the workspace header read by fgs_get_error; no
- *    kernel traps.
+ *    failure).  Errors found on the device (instance capacity exceeded,
+ *    non-finite loss or Adam update) set sticky bits in the workspace header
+ *    read by fgs_get_error; no kernel traps.
  *  - Gradients are overwritten, never accumulated.
  *  - Layouts are row-major; a [n,3] array is n consecutive triples.
  *
@@ -69,9 +69,15 @@ enum fgs_status {
     FGS_ERR_TOO_LARGE = -10  /* more pairs than fgs_sort_pairs_static can hold */
 };
 
-/* Sticky bits set on the device, read by fgs_get_error. */
+/* Sticky bits set on the device, read by fgs_get_error.  Setting one never
+ * stops a kernel: the outputs of that call hold whatever the arithmetic gave
+ * (dropped instances, NaN or infinity), and the caller decides. */
 enum fgs_device_flags {
-    FGS_FLAG_CAPACITY = 1u   /* instances exceeded k_max; the extra ones were dropped */
+    FGS_FLAG_CAPACITY = 1u,  /* instances exceeded k_max; the extra ones were dropped */
+    FGS_FLAG_NONFINITE = 2u  /* a NaN or infinity reached the loss (a per-view sum or
+                                dL/dimages, set by fgs_loss_l1_dssim) or an Adam update
+                                (a new parameter or moment, set by the fused
+                                fgs_render_backward_adam) */
 };
 
 enum fgs_dtype { FGS_F32 = 0, FGS_BF16 = 1, FGS_F16 = 2 };
@@ -334,7 +340,9 @@ int fgs_render_backward_adam(void *ws, const fgs_workspace_layout *layout, const
  * radix sort of the combined keys).  keys/vals hold the input; keys_alt /
  * vals_alt are same-sized scratch.  The sorted result ends in keys/vals
  * when *result_in_alt (host) is 0, else in the *_alt buffers.  scratch:
- * device buffer of fgs_sort_scratch_bytes(n) bytes. */
+ * device buffer of fgs_sort_scratch_bytes(n) bytes, 256-byte aligned.
+ * Key buffers must be 8-byte and value buffers 4-byte aligned, else
+ * FGS_ERR_ALIGN before any launch. */
 size_t fgs_sort_scratch_bytes(int64_t n);
 int fgs_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                    int64_t n, int32_t bits, void *scratch, size_t scratch_bytes,
@@ -353,8 +361,12 @@ int fgs_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t 
  * by every GPU that loads the library until the process exits; the call
  * allocates nothing.  n > FGS_STATIC_SORT_MAX_PAIRS returns
  * FGS_ERR_TOO_LARGE before any launch; n == 0 returns FGS_OK.
+ * keys must be 8-byte and vals 4-byte aligned, else FGS_ERR_ALIGN.
  * The first call on a device looks up the array's device address (with that
  * device current), so make it before any stream capture on that device.
+ * The address is cached per device number for the CUDA runtime's primary
+ * context; after cudaDeviceReset, or under another context made current
+ * through the driver API, the cached address is stale and must not be used.
  * Every call uses the same array: calls whose kernels overlap on the GPU
  * (different streams, or different host threads, without ordering between
  * them) race on it and corrupt each other's results. */
@@ -431,6 +443,10 @@ int32_t fgs_profile_count(void);
 
 /* Static description of a status code. */
 const char *fgs_strerror(int code);
+
+/* Static description of one device flag bit (FGS_FLAG_*); "unknown flag"
+ * for any other value, including 0 and combinations of bits. */
+const char *fgs_flag_string(uint32_t flag);
 
 #ifdef __cplusplus
 }

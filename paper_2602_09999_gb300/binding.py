@@ -21,6 +21,7 @@ FGS_MAX_VIEWS = 16
 FGS_NUM_GROUPS = 8
 FGS_F32, FGS_BF16, FGS_F16 = 0, 1, 2
 FGS_FLAG_CAPACITY = 1
+FGS_FLAG_NONFINITE = 2
 
 (FGS_WS_HEADER, FGS_WS_SCREEN, FGS_WS_RECT, FGS_WS_LOCAL_OFF, FGS_WS_BLOCK_SUM, FGS_WS_KEYS,
  FGS_WS_VALS, FGS_WS_KEYS_ALT, FGS_WS_VALS_ALT, FGS_WS_SORT_HIST, FGS_WS_RANGES, FGS_WS_T_FINAL,
@@ -42,7 +43,7 @@ EXPORTED = ("fgs_workspace_size", "fgs_workspace_size_ex", "fgs_render_forward",
             "fgs_morton_scratch_bytes", "fgs_morton_order", "fgs_permute_params",
             "fgs_peak_fma", "fgs_peak_ex2", "fgs_peak_l2_read", "fgs_get_error",
             "fgs_profile_attach",
-            "fgs_profile_count", "fgs_strerror")
+            "fgs_profile_count", "fgs_strerror", "fgs_flag_string")
 
 
 class FGSError(RuntimeError):
@@ -144,9 +145,11 @@ def lib():
             L.fgs_profile_count.argtypes = []
             L.fgs_strerror.argtypes = [ctypes.c_int]
             L.fgs_strerror.restype = ctypes.c_char_p
+            L.fgs_flag_string.argtypes = [ctypes.c_uint32]
+            L.fgs_flag_string.restype = ctypes.c_char_p
             for name in EXPORTED:
                 if name not in ("fgs_sort_scratch_bytes", "fgs_morton_scratch_bytes",
-                                "fgs_strerror"):
+                                "fgs_strerror", "fgs_flag_string"):
                     getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -177,6 +180,10 @@ def fgs_profile_count() -> int:
 
 def fgs_strerror(code: int) -> str:
     return lib().fgs_strerror(int(code)).decode()
+
+
+def fgs_flag_string(flag: int) -> str:
+    return lib().fgs_flag_string(int(flag)).decode()
 
 
 def fgs_workspace_size(n, cams_host, n_views, k_max) -> fgs_workspace_layout:

@@ -1,6 +1,7 @@
 // adam.cu -- fused Adam update (Suppl. A: beta = (0.9, 0.999), eps = 1e-15;
-// Sec. 3.3 "Parameter Updates": one fused kernel that follows PyTorch's
-// Adam step by step).  Per element, in float32:
+// Sec. 3.3 "Parameter Updates": one fused kernel with PyTorch's Adam
+// formula, its roundings spelled out in adam_math.cuh).  Per element, in
+// float32:
 //   m = m + (1 - b1) (g - m)                     (PyTorch forms m with lerp)
 //   v = b2 v + (1 - b2) g^2
 //   p = p - step_size * m / (sqrt(v) / sqrt(1 - b2^t) + eps)

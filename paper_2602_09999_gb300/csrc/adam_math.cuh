@@ -1,7 +1,11 @@
 // adam_math.cuh -- the per-element Adam update shared by the standalone
 // Adam kernels and the fused preprocess-backward + Adam kernel, so both take
-// exactly the same steps (Suppl. A hyper-parameters; PyTorch's order of
-// operations, Sec. 3.3 "Parameter Updates").
+// exactly the same steps (Suppl. A hyper-parameters; Sec. 3.3 "Parameter
+// Updates").  It is PyTorch's formula, not its instruction sequence: the
+// second-moment and parameter updates are fused multiply-adds, and the
+// denominator is sqrt(v) * (1 / sqrt(1 - b2^t)) + eps in one fused step where
+// PyTorch divides by sqrt(1 - b2^t) and then adds eps, so a result can differ
+// from torch.optim.Adam in float32 by a few ulps.
 #pragma once
 #include "fgs_common.cuh"
 

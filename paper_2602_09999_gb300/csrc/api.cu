@@ -52,7 +52,8 @@ bool blend_config_supported(int ppt, int batch);
 
 static const int kDefaultPPT = 2, kDefaultBatch = 128;
 cudaError_t launch_loss(const ViewTable& vt, const float* images, const float* targets, float lambda,
-                        float* maps, double* partials, float* loss_out, float* dL, cudaStream_t st);
+                        float* maps, double* partials, float* loss_out, float* dL, WsHeader* hdr,
+                        cudaStream_t st);
 cudaError_t launch_adam_group(int64_t count, int pdt, int mdt, void* p, const float* g, void* m,
                               void* v, float step_size, float inv_bc2_sqrt, double b1, double b2,
                               double eps, const fgs_adam_state* ds, int grp, cudaStream_t st);
@@ -62,7 +63,7 @@ cudaError_t launch_zero_and_adam_prepare(ScreenGrad* sgrad, const uint32_t* bloc
 cudaError_t launch_preprocess_bwd_adam(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
                                        const ViewTable& vt, const Screen* screen, const ScreenGrad* sgrad,
                                        const fgs_params* g, const fgs_params* m, const fgs_params* v,
-                                       const fgs_adam_state* ds, cudaStream_t st);
+                                       const fgs_adam_state* ds, WsHeader* hdr, cudaStream_t st);
 bool fused_adam_supported(int sh_dtype, int moment_dtype);
 
 static const int64_t kGroupWidth[FGS_NUM_GROUPS] = {3, 3, 4, 1, 3, 45, 3, 1};
@@ -376,7 +377,7 @@ int fgs_loss_l1_dssim(void* ws, const fgs_workspace_layout* L, const fgs_camera*
     profile_mark((cudaStream_t)stream, "begin");
     return cuda_rc(launch_loss(vt, images, targets, lambda, slot<float>(ws, L, FGS_WS_LOSS_MAPS),
                                slot<double>(ws, L, FGS_WS_LOSS_PART), loss_out, dl_dimages,
-                               (cudaStream_t)stream));
+                               slot<WsHeader>(ws, L, FGS_WS_HEADER), (cudaStream_t)stream));
 }
 
 // The per-pixel blend backward's launch pair: its own when set, else the
@@ -468,7 +469,8 @@ int fgs_render_backward_adam(void* ws, const fgs_workspace_layout* L, const fgs_
     return cuda_rc(launch_preprocess_bwd_adam(L->n, sh_degree, params, cams_device, vt,
                                               slot<Screen>(ws, L, FGS_WS_SCREEN),
                                               slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD), grads, exp_avg,
-                                              exp_avg_sq, state_device, st));
+                                              exp_avg_sq, state_device, slot<WsHeader>(ws, L, FGS_WS_HEADER),
+                                              st));
 }
 
 int fgs_adam_step(const fgs_params* params, const fgs_params* grads, const fgs_params* exp_avg,
@@ -529,6 +531,9 @@ int fgs_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t*
     if (bits < 1 || bits > 64) return FGS_ERR_ARG;
     if (scratch_bytes < fgs_sort_scratch_bytes(n)) return FGS_ERR_WORKSPACE;
     if ((uintptr_t)scratch % 256 != 0) return FGS_ERR_ALIGN;
+    if ((uintptr_t)keys % 8 != 0 || (uintptr_t)keys_alt % 8 != 0 || (uintptr_t)vals % 4 != 0 ||
+        (uintptr_t)vals_alt % 4 != 0)
+        return FGS_ERR_ALIGN;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t* n_dev = (uint32_t*)scratch;
     if (launch_set_count(n_dev, (uint32_t)n, st) != cudaSuccess) return FGS_ERR_CUDA;
@@ -588,6 +593,15 @@ const char* fgs_strerror(int code)
     case FGS_ERR_ARG: return "argument out of range";
     case FGS_ERR_TOO_LARGE: return "more pairs than the static sort scratch holds";
     default: return "unknown status";
+    }
+}
+
+const char* fgs_flag_string(uint32_t flag)
+{
+    switch (flag) {
+    case FGS_FLAG_CAPACITY: return "instances exceeded the workspace capacity k_max (extra ones dropped)";
+    case FGS_FLAG_NONFINITE: return "a NaN or infinity reached the loss or an Adam update";
+    default: return "unknown flag";
     }
 }
 

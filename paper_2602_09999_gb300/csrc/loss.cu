@@ -17,7 +17,8 @@
 //              s = 1 / (3 H W n_views).
 //              Its first CTA, before its own block, also sums the per-CTA
 //              partials of ssim_fwd per view in a fixed order (double
-//              precision) and writes the scalar loss.
+//              precision) and writes the scalar loss.  A non-finite loss or
+//              dL/dx sets the workspace's sticky FGS_FLAG_NONFINITE.
 // The window weights are computed once on the host (double precision,
 // rounded to float) and passed by value with the CTA grid of the views.
 #include <cmath>
@@ -176,7 +177,8 @@ ssim_fwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
 
 // The scalar loss from the per-CTA partials (256 threads; red: scratch).
 __device__ void reduce_loss(const ViewTable& vt, const LossGrid& lg, const double* __restrict__ partials,
-                            float lambda, float* __restrict__ loss_out, double (*red)[256], int tid)
+                            float lambda, float* __restrict__ loss_out, double (*red)[256], int tid,
+                            WsHeader* __restrict__ hdr)
 {
     double total = 0.0;
     for (int v = 0; v < vt.n_views; ++v) {
@@ -199,13 +201,18 @@ __device__ void reduce_loss(const ViewTable& vt, const LossGrid& lg, const doubl
         total += (1.0 - lambda) * red[0][0] * inv + lambda * (1.0 - red[1][0] * inv);
         __syncthreads();
     }
-    if (tid == 0) loss_out[0] = (float)(total / vt.n_views);
+    if (tid == 0) {
+        const float loss = (float)(total / vt.n_views);
+        loss_out[0] = loss;
+        if (!isfinite(loss)) set_flag(hdr, FGS_FLAG_NONFINITE);
+    }
 }
 
 __global__ void __launch_bounds__(kLX * kLY)
 ssim_bwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
                 const float* __restrict__ targets, const float* __restrict__ maps, float lambda,
-                float* __restrict__ dL, const double* __restrict__ partials, float* __restrict__ loss_out)
+                float* __restrict__ dL, const double* __restrict__ partials, float* __restrict__ loss_out,
+                WsHeader* __restrict__ hdr)
 {
     __shared__ __align__(16) float sm[3][kSpanY][kSpanX + 1];
     __shared__ float hs[3][kSpanY][kLTW + 1];
@@ -215,7 +222,7 @@ ssim_bwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
     // before this kernel started, then takes its own block
     if (b == 0)
         reduce_loss(vt, lg, partials, lambda, loss_out, reinterpret_cast<double(*)[256]>(&sm[0][0][0]),
-                    threadIdx.y * kLX + threadIdx.x);
+                    threadIdx.y * kLX + threadIdx.x, hdr);
     const int v = view_of_cta(lg, vt.n_views, b);
     const int lb = b - lg.cta_off[v];
     const int W = vt.width[v], H = vt.height[v];
@@ -225,6 +232,7 @@ ssim_bwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int px = x0 + tx;
     const float scale = 1.0f / (3.0f * (float)P * (float)vt.n_views);
+    bool nonfinite = false;
     for (int ch = 0; ch < 3; ++ch) {
         __syncthreads();
         for (int r = ty; r < kSpanY; r += kLY) {
@@ -266,9 +274,12 @@ ssim_bwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
             const float dssim = b0 + 2.f * x * b1 + y * b2;
             const float diff = x - y;
             const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-            dL[off] = scale * ((1.0f - lambda) * sgn - lambda * dssim);
+            const float grad = scale * ((1.0f - lambda) * sgn - lambda * dssim);
+            dL[off] = grad;
+            nonfinite |= !isfinite(grad);
         }
     }
+    if (__syncthreads_or(nonfinite) && threadIdx.x == 0 && threadIdx.y == 0) set_flag(hdr, FGS_FLAG_NONFINITE);
 }
 
 static LossGrid loss_grid(const ViewTable& vt)
@@ -289,7 +300,8 @@ static LossGrid loss_grid(const ViewTable& vt)
 }
 
 cudaError_t launch_loss(const ViewTable& vt, const float* images, const float* targets, float lambda,
-                        float* maps, double* partials, float* loss_out, float* dL, cudaStream_t st)
+                        float* maps, double* partials, float* loss_out, float* dL, WsHeader* hdr,
+                        cudaStream_t st)
 {
     if (vt.total_tiles <= 0) return cudaSuccess;
     const LossGrid lg = loss_grid(vt);
@@ -297,7 +309,8 @@ cudaError_t launch_loss(const ViewTable& vt, const float* images, const float* t
     const dim3 block(kLX, kLY);
     ssim_fwd_kernel<<<ctas, block, 0, st>>>(vt, lg, images, targets, maps, partials);
     profile_mark(st, "loss_ssim_fwd");
-    ssim_bwd_kernel<<<ctas, block, 0, st>>>(vt, lg, images, targets, maps, lambda, dL, partials, loss_out);
+    ssim_bwd_kernel<<<ctas, block, 0, st>>>(vt, lg, images, targets, maps, lambda, dL, partials, loss_out,
+                                                hdr);
     profile_mark(st, "loss_ssim_bwd");
     return cudaGetLastError();
 }

@@ -524,7 +524,15 @@ struct AdamArgs {
     void* m[8];
     void* v[8];
     const fgs_adam_state* st;
+    WsHeader* hdr;  // receives FGS_FLAG_NONFINITE
 };
+
+// True unless all three are finite (v >= 0; a NaN fails the comparison, and
+// a sum beyond the float range counts as non-finite too).
+__device__ __forceinline__ bool adam_nonfinite(float p, float m, float v)
+{
+    return !(fabsf(p) + fabsf(m) + v <= 3.402823466e38f);
+}
 
 // Four consecutive elements of a storage type as one 16-byte (float32) or
 // 8-byte (bf16, fp16) access.
@@ -572,7 +580,7 @@ template <typename T> __device__ __forceinline__ bool aligned_for_pack(const voi
 constexpr int kAdamPacks = 2;
 template <typename PT, typename MT>
 __device__ __forceinline__ void adam_slice(void* p, void* m, void* v, const float* sg, float* g_out,
-                                           int64_t base, int64_t cnt, const AdamScalars& a)
+                                           int64_t base, int64_t cnt, const AdamScalars& a, bool& bad)
 {
     PT* __restrict__ pp = static_cast<PT*>(p) + base;
     MT* __restrict__ mm = static_cast<MT*>(m) + base;
@@ -603,6 +611,7 @@ __device__ __forceinline__ void adam_slice(void* p, void* m, void* v, const floa
             for (int j = 0; j < 4; ++j) {
                 float vf = v_decode<MT>(vvv[u][j]);
                 pv[u][j] = adam_update(pv[u][j], gg[j], mv[u][j], vf, a);
+                bad |= adam_nonfinite(pv[u][j], mv[u][j], vf);
                 vvv[u][j] = v_encode<MT>(vf);
             }
             Pack4<PT>::store(pp + 4 * qs[u], pv[u]);
@@ -615,7 +624,9 @@ __device__ __forceinline__ void adam_slice(void* p, void* m, void* v, const floa
         const float g = sg[e];
         float mf = to_f32(mm[e]);
         float vf = VStore<MT>::load(vv[e]);
-        pp[e] = from_f32<PT>(adam_update(to_f32(pp[e]), g, mf, vf, a));
+        const float pf = adam_update(to_f32(pp[e]), g, mf, vf, a);
+        bad |= adam_nonfinite(pf, mf, vf);
+        pp[e] = from_f32<PT>(pf);
         mm[e] = from_f32<MT>(mf);
         vv[e] = VStore<MT>::store(vf);
         if (go) go[e] = g;
@@ -855,24 +866,26 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
         s_small[10 * kBwdBlock + t] = gw;
         __syncthreads();
         const int64_t nb = min((int64_t)kBwdBlock, n - i0);
+        bool bad = false;
         adam_slice<float, MT>(aa.p[0], aa.m[0], aa.v[0], s_small, g_means, 3 * i0, 3 * nb,
-                              resolve(AdamScalars{}, aa.st, 0));
+                              resolve(AdamScalars{}, aa.st, 0), bad);
         adam_slice<float, MT>(aa.p[1], aa.m[1], aa.v[1], s_small + 3 * kBwdBlock, g_scales, 3 * i0,
-                              3 * nb, resolve(AdamScalars{}, aa.st, 1));
+                              3 * nb, resolve(AdamScalars{}, aa.st, 1), bad);
         adam_slice<float, MT>(aa.p[2], aa.m[2], aa.v[2], s_small + 6 * kBwdBlock, g_quats, 4 * i0,
-                              4 * nb, resolve(AdamScalars{}, aa.st, 2));
+                              4 * nb, resolve(AdamScalars{}, aa.st, 2), bad);
         adam_slice<float, MT>(aa.p[3], aa.m[3], aa.v[3], s_small + 10 * kBwdBlock, g_opac, i0, nb,
-                              resolve(AdamScalars{}, aa.st, 3));
+                              resolve(AdamScalars{}, aa.st, 3), bad);
         adam_slice<SHT, MT>(aa.p[4], aa.m[4], aa.v[4], s_small + 11 * kBwdBlock, g_dc, 3 * i0, 3 * nb,
-                            resolve(AdamScalars{}, aa.st, 4));
+                            resolve(AdamScalars{}, aa.st, 4), bad);
         adam_slice<SHT, MT>(aa.p[5], aa.m[5], aa.v[5], s_rest, g_rest, 45 * i0, 45 * nb,
-                            resolve(AdamScalars{}, aa.st, 5));
+                            resolve(AdamScalars{}, aa.st, 5), bad);
         if (MOTION) {
             adam_slice<float, MT>(aa.p[6], aa.m[6], aa.v[6], s_small + 14 * kBwdBlock, g_vel, 3 * i0, 3 * nb,
-                                  resolve(AdamScalars{}, aa.st, 6));
+                                  resolve(AdamScalars{}, aa.st, 6), bad);
             adam_slice<float, MT>(aa.p[7], aa.m[7], aa.v[7], s_small + 17 * kBwdBlock, g_t0, i0, nb,
-                                  resolve(AdamScalars{}, aa.st, 7));
+                                  resolve(AdamScalars{}, aa.st, 7), bad);
         }
+        if (__syncthreads_or(bad) && threadIdx.x == 0) set_flag(aa.hdr, FGS_FLAG_NONFINITE);
         return;
     }
     if (valid) {
@@ -1033,10 +1046,11 @@ template <typename SHT, typename MT>
 static cudaError_t launch_pre_bwd_adam_t(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
                                          const ViewTable& vt, const Screen* screen, const ScreenGrad* sgrad,
                                          const fgs_params* g, const fgs_params* m, const fgs_params* v,
-                                         const fgs_adam_state* ds, cudaStream_t st)
+                                         const fgs_adam_state* ds, WsHeader* hdr, cudaStream_t st)
 {
     const int grid = (int)((n + kBwdBlock - 1) / kBwdBlock);
     AdamArgs aa;
+    aa.hdr = hdr;
     for (int k = 0; k < FGS_NUM_GROUPS; ++k) {
         aa.p[k] = p->data[k];
         aa.m[k] = m->data[k];
@@ -1063,10 +1077,10 @@ static cudaError_t launch_pre_bwd_adam_t(int64_t n, int deg, const fgs_params* p
 cudaError_t launch_preprocess_bwd_adam(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
                                        const ViewTable& vt, const Screen* screen, const ScreenGrad* sgrad,
                                        const fgs_params* g, const fgs_params* m, const fgs_params* v,
-                                       const fgs_adam_state* ds, cudaStream_t st)
+                                       const fgs_adam_state* ds, WsHeader* hdr, cudaStream_t st)
 {
     const int sht = p->dtype[4], mt = m->dtype[0];
-#define FGS_PB(S, M) launch_pre_bwd_adam_t<S, M>(n, deg, p, cams, vt, screen, sgrad, g, m, v, ds, st)
+#define FGS_PB(S, M) launch_pre_bwd_adam_t<S, M>(n, deg, p, cams, vt, screen, sgrad, g, m, v, ds, hdr, st)
     if (sht == FGS_F32 && mt == FGS_F32) return FGS_PB(float, float);
     if (sht == FGS_BF16 && mt == FGS_F32) return FGS_PB(__nv_bfloat16, float);
     if (sht == FGS_BF16 && mt == FGS_BF16) return FGS_PB(__nv_bfloat16, __nv_bfloat16);

@@ -15,7 +15,10 @@
 // The array's name is a host-side stand-in in host code, never a device
 // address, so this file looks the device address up with
 // cudaGetSymbolAddress once per device (with that device current) and
-// passes that pointer to the kernels.
+// passes that pointer to the kernels.  The address is cached per device
+// number, for the context the CUDA runtime uses there (the primary
+// context): after cudaDeviceReset, or with another context made current
+// through the driver API, the cached address is no longer valid.
 #include <mutex>
 
 #include "fgs_common.cuh"
@@ -73,6 +76,8 @@ extern "C" int fgs_sort_pairs_static(uint64_t* keys, uint32_t* vals, int64_t n, 
     if (bits < 1 || bits > 64) return FGS_ERR_ARG;
     if (n == 0) return FGS_OK;
     if (!keys || !vals) return FGS_ERR_NULL;
+    // 8-byte key and 4-byte value accesses
+    if ((uintptr_t)keys % 8 != 0 || (uintptr_t)vals % 4 != 0) return FGS_ERR_ALIGN;
     if (sort_hist_bytes(n) > kHistBytes) return FGS_ERR_TOO_LARGE;
     unsigned char* base = nullptr;
     const int rc = scratch_on_current_device(&base);

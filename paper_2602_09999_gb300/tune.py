@@ -12,7 +12,8 @@ forward's: it sums each entry's gradients over the warp once per entry, so
 more pixels per thread spread that cost over more pixels), then the
 forward's other pairs with the backward's fixed, keeps the fastest, and
 caches it in a JSON file keyed by GPU name, Gaussian count and pixel count
-(rounded to powers of two), so later runs of the same shape skip the search.
+(rounded to powers of two), view count, backward order and storage types,
+so later runs of the same shape skip the search.
 """
 from __future__ import annotations
 
@@ -27,9 +28,17 @@ from . import binding as B
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
 
 
-def _key(n: int, pixels: int) -> str:
+def _key(trainer) -> str:
+    """Cache key of a trainer's shape: GPU, Gaussian and pixel counts (as
+    powers of two), the number of views, the blend backward's order and the
+    SH parameter and Adam moment storage types."""
     name = torch.cuda.get_device_name().replace(" ", "_")
-    return f"{name}/n2^{round(math.log2(max(n, 1)))}/px2^{round(math.log2(max(pixels, 1)))}"
+    n, pixels = trainer.n, trainer.views.total_pixels
+    order = "pg" if trainer.rast.layout.tuning.blend_backward == B.FGS_BACKWARD_PER_GAUSSIAN else "pp"
+    sh = str(trainer.params["sh_rest"].dtype).replace("torch.", "")
+    mom = str(trainer.exp_avg["means"].dtype).replace("torch.", "")
+    return (f"{name}/n2^{round(math.log2(max(n, 1)))}/px2^{round(math.log2(max(pixels, 1)))}"
+            f"/v{trainer.views.n}/{order}/sh-{sh}/m-{mom}")
 
 
 def _load():
@@ -78,7 +87,7 @@ def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=None):
     only (the parameters are not updated).  Returns (choice, timings_ms)."""
     configs = all_choices() if configs is None else [
         (tuple(c) + (B.FGS_SCHEDULE_QUEUE,))[:3] for c in configs]
-    key = _key(trainer.n, trainer.views.total_pixels)
+    key = _key(trainer)
     table = _load() if use_cache else {}
     if key in table and len(table[key].get("choice", [])) == 5:
         choice = tuple(table[key]["choice"])

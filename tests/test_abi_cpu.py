@@ -98,9 +98,37 @@ def test_bad_camera_size_rejected(lib):
 
 
 def test_strerror(lib):
-    for code in range(-9, 1):
-        assert B.fgs_strerror(code)
+    for code in range(-10, 1):
+        assert B.fgs_strerror(code) != "unknown status"
     assert B.fgs_strerror(-100) == "unknown status"
+
+
+def _header_enum(name):
+    """{member: value} of one enum of the header, read as text."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"enum\s+" + name + r"\s*\{(.*?)\}", text, flags=re.S).group(1)
+    out = {}
+    for item in body.split(","):
+        m = re.match(r"\s*(\w+)\s*=\s*(-?\w+)", item)
+        if m:
+            out[m.group(1)] = int(m.group(2).rstrip("uU"), 0)
+    return out
+
+
+def test_device_flags_and_their_strings(lib):
+    """The sticky device flags: distinct single bits, mirrored by the
+    binding, each with its own description; anything else is unknown."""
+    flags = _header_enum("fgs_device_flags")
+    assert flags == {"FGS_FLAG_CAPACITY": B.FGS_FLAG_CAPACITY,
+                     "FGS_FLAG_NONFINITE": B.FGS_FLAG_NONFINITE}
+    bits = list(flags.values())
+    assert all(b and (b & (b - 1)) == 0 for b in bits) and len(set(bits)) == len(bits)
+    texts = {B.fgs_flag_string(b) for b in bits}
+    assert len(texts) == len(bits) and "unknown flag" not in texts
+    assert "NaN" in B.fgs_flag_string(B.FGS_FLAG_NONFINITE)
+    for other in (0, 4, B.FGS_FLAG_CAPACITY | B.FGS_FLAG_NONFINITE, 0xffffffff):
+        assert B.fgs_flag_string(other) == "unknown flag"
+    assert _header_enum("fgs_status") == {v: k for k, v in B.STATUS.items()}
 
 
 def test_null_pointer_checks_before_any_launch(lib):
@@ -121,6 +149,25 @@ def test_null_pointer_checks_before_any_launch(lib):
         B.fgs_render_backward_adam(None, L, B.fgs_params(), 3, cam, None, (0, 0, 0), None,
                                    B.fgs_params(), B.fgs_params(), None, None, None)
     assert e.value.code == -1
+
+
+def test_sort_alignment_checks_before_any_launch(lib):
+    """Misaligned key (8-byte) or value (4-byte) buffers are rejected on the
+    host; the fake addresses are never dereferenced."""
+    base = 1 << 40
+    sb = B.fgs_sort_scratch_bytes(10)
+    good = dict(keys=base, vals=base + (1 << 32), keys_alt=base + (2 << 32), vals_alt=base + (3 << 32))
+    for name, off in (("keys", 4), ("vals", 2), ("keys_alt", 4), ("vals_alt", 1)):
+        a = dict(good)
+        a[name] += off
+        with pytest.raises(B.FGSError) as e:
+            B.fgs_sort_pairs(a["keys"], a["vals"], a["keys_alt"], a["vals_alt"], 10, 32,
+                             base + (4 << 32), sb, None)
+        assert e.value.code == -8, name
+    for k, v in ((base + 4, base + (1 << 32)), (base, base + (1 << 32) + 2)):
+        with pytest.raises(B.FGSError) as e:
+            B.fgs_sort_pairs_static(k, v, 10, 32, None)
+        assert e.value.code == -8
 
 
 def _fake_params(n, base, dtypes=None, groups=6):

@@ -150,3 +150,40 @@ def test_zero_capacity_flags_and_renders_background():
     img = images.cpu().numpy().reshape(3, 48, 64)
     for ch in range(3):
         assert np.all(img[ch] == np.float32(BG[ch]))
+
+
+def test_nonfinite_flag_from_loss_and_fused_adam():
+    """Non-finite values put into the inputs on the host set the sticky
+    FGS_FLAG_NONFINITE, read through fgs_get_error, without a device fault:
+    a NaN target pixel (the loss and dL/dC), then a NaN parameter of a
+    Gaussian outside the view (its fused Adam update).  A clean step sets
+    nothing, and clearing the flags resets them."""
+    p = scenes.tiny_scene(2000, seed=11)
+    cam = scenes.tiny_camera(64, 48)
+    target = scenes.target_image(64, 48, view=0)
+    tr = T.Trainer(p, [cam], k_max=100_000)
+    tr.set_targets([target])
+    tr.step()
+    flags, _ = tr.rast.error()
+    assert flags == 0
+    bad = target.copy()
+    bad[1, 20, 30] = np.nan
+    tr.set_targets([bad])
+    tr.step()
+    flags, _ = tr.rast.error(clear=True)
+    assert flags & B.FGS_FLAG_NONFINITE and not flags & B.FGS_FLAG_CAPACITY
+    assert not np.isfinite(float(tr.loss.item()))
+    assert B.fgs_flag_string(B.FGS_FLAG_NONFINITE) != "unknown flag"
+    assert tr.rast.error()[0] == 0
+    # the loss is clean again; an invisible Gaussian's NaN reaches only Adam
+    tr2 = T.Trainer(p, [cam], k_max=100_000)
+    tr2.set_targets([target])
+    with torch.no_grad():
+        tr2.params["means"][0] = torch.tensor([0.0, 0.0, 9.0])   # behind the camera at z = 4
+        tr2.params["log_scales"][0, 1] = float("nan")
+    tr2.step()
+    torch.cuda.synchronize()
+    assert np.isfinite(float(tr2.loss.item()))
+    flags, _ = tr2.rast.error()
+    assert flags & B.FGS_FLAG_NONFINITE
+    assert torch.isfinite(tr2.params["log_scales"][1:]).all()
