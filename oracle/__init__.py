@@ -286,6 +286,43 @@ def blend_forward(cam, pre, lists, bg=(0.0, 0.0, 0.0), margins: Margins = NO_MAR
     return out
 
 
+MAX_PATHS = 64
+
+
+def blend_paths(cam, pre, lists, bg=(0.0, 0.0, 0.0), margins: Margins = NO_MARGINS,
+                max_paths=MAX_PATHS):
+    """Admissible results of every pixel (see orc_blend_paths): the results a
+    float32 evaluation may reach when it takes the decisions within the
+    margins either way.  Returns status[H,W] (0: one result, the FP64 one;
+    1: several; 2: more than max_paths, bounded only by the allowance) and,
+    for the status-1 pixels, path_pix[M] (pixel index v W + u, ascending)
+    with path_val[M, 5] = (C + T bg, T, last blended Gaussian or -1)."""
+    lib = _lib_handle()
+    W, H = cam.width, cam.height
+    bg = np.asarray(bg, np.float64)
+    m = _mg_struct(margins)
+    status = np.zeros((H, W), np.uint8)
+    cap = max(1024, 2 * W * H)
+    while True:
+        pix = np.zeros(cap, np.int64)
+        val = np.zeros((cap, 5))
+        n_out = ctypes.c_int64(0)
+        rc = lib.orc_blend_paths(ctypes.c_int32(W), ctypes.c_int32(H), _p(lists["ranges"]),
+                                 _p(lists["gid"]), _p(lists["flags"]), _p(pre["xy"]),
+                                 _p(pre["conic"]), _p(pre["opacity"]), _p(pre["rgb"]),
+                                 _p(pre["depth"]), _p(bg), ctypes.byref(m), ctypes.c_int32(max_paths),
+                                 ctypes.c_int64(cap), _p(status), ctypes.byref(n_out), _p(pix),
+                                 _p(val))
+        if rc != 0:
+            raise MemoryError("orc_blend_paths failed")
+        if n_out.value <= cap:
+            break
+        cap = int(n_out.value)
+    k = int(n_out.value)
+    order = np.argsort(pix[:k], kind="stable")
+    return dict(status=status, path_pix=pix[:k][order], path_val=val[:k][order])
+
+
 def blend_brute(cam, pre, bg=(0.0, 0.0, 0.0)):
     """Tile-free twin: every pixel walks all visible Gaussians in (depth, id)
     order."""
@@ -381,11 +418,18 @@ def adam(p, g, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-15):
 DEFAULT_LR = (1.6e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 1.25e-4, 1.6e-4, 1e-3)
 
 
-def render(cam, params, sh_degree=3, bg=(0.0, 0.0, 0.0), margins: Margins = NO_MARGINS):
-    """Forward for one camera: preprocess, lists, blend."""
+def render(cam, params, sh_degree=3, bg=(0.0, 0.0, 0.0), margins: Margins = NO_MARGINS,
+           paths=None):
+    """Forward for one camera: preprocess, lists, blend.  With paths (by
+    default whenever the margins are not all zero) `out` also holds the
+    admissible results of blend_paths."""
     pre = preprocess(cam, params, sh_degree, margins)
     lists = build_lists(cam, params, pre, sh_degree, margins)
     out = blend_forward(cam, pre, lists, bg, margins)
+    if paths is None:
+        paths = margins.t_rel > 0.0 or margins.rel > 0.0
+    if paths:
+        out.update(blend_paths(cam, pre, lists, bg, margins))
     return pre, lists, out
 
 

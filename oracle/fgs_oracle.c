@@ -630,6 +630,54 @@ static double max_abs_diff3(const double *a, const double *b)
     return m;
 }
 
+/* One list entry at one pixel centre (Eq. 3 with the 3DGS rules): its
+ * exponent, o G, alpha = min(0.99, o G), whether FP64 blends it (a kept
+ * tile, power <= 0, alpha >= 1/255), the relative float32 error of o G
+ * (slack), whether float32 may take the blend decision the other way
+ * (uncertain) and whether o G lies within its error of the 0.99 clamp. */
+typedef struct {
+    double power, oG, alpha, slack;
+    int keep, blend, uncertain, near_clamp;
+} orc_entry;
+
+static void entry_eval(double px, double py, int32_t g, uint8_t f, const double *xy,
+                       const double *conic, const double *opac, const orc_margins *mg,
+                       orc_entry *e)
+{
+    const int keep = f & ORC_KEEP;
+    const double dx = px - xy[2 * g], dy = py - xy[2 * g + 1];
+    const double qa = conic[3 * g] * dx * dx;
+    const double qb = 2.0 * conic[3 * g + 1] * dx * dy;
+    const double qc = conic[3 * g + 2] * dy * dy;
+    const double power = -0.5 * (qa + qb + qc);
+    const double oG = opac[g] * exp(power);
+    /* relative float32 error of o G: opacity and exp rounding, the
+     * rounding of the form (form_error_scale) and the position error of
+     * mu2D */
+    const double pos_err = mg->pos_rel * fmax(1.0, fmax(fabs(xy[2 * g]), fabs(xy[2 * g + 1])));
+    const double grad = fabs(conic[3 * g] * dx + conic[3 * g + 1] * dy) +
+                        fabs(conic[3 * g + 1] * dx + conic[3 * g + 2] * dy);
+    const double mag = mg->q_rel > 0.0
+                           ? form_error_scale(conic[3 * g], conic[3 * g + 1], conic[3 * g + 2], dx, dy)
+                           : 0.0;
+    const double slack = mg->rel + 0.5 * mg->q_rel * mag + pos_err * grad;
+    /* is whether this entry is blended a decision float32 may take the other way? */
+    int uncertain = 0;
+    if (!keep || (f & ORC_IMARGINAL)) uncertain |= oG >= ORC_ALPHA_MIN * (1.0 - slack);
+    if (keep) {
+        uncertain |= fabs(power) <= 0.5 * mg->q_rel * mag + (mg->q_rel > 0.0 ? 1e-12 : 0.0);
+        uncertain |= fabs(oG - ORC_ALPHA_MIN) <= ORC_ALPHA_MIN * slack;
+    }
+    e->power = power;
+    e->oG = oG;
+    e->alpha = oG < ORC_ALPHA_MAX ? oG : ORC_ALPHA_MAX;
+    e->slack = slack;
+    e->keep = keep;
+    e->blend = keep && power <= 0.0 && e->alpha >= ORC_ALPHA_MIN;
+    e->uncertain = uncertain;
+    e->near_clamp = keep && fabs(oG - ORC_ALPHA_MAX) <= ORC_ALPHA_MAX * slack;
+}
+
 static void pixel_walk(double px, double py, int64_t start, int64_t end, const int32_t *list_gid,
                        const uint8_t *list_flags, const double *xy, const double *conic,
                        const double *opac, const double *rgb, const double *depth, const double *bg,
@@ -653,36 +701,16 @@ static void pixel_walk(double px, double py, int64_t start, int64_t end, const i
     for (int64_t j = start; j < end; ++j) {
         const int32_t g = list_gid[j];
         const uint8_t f = list_flags ? list_flags[j] : ORC_KEEP;
-        const int keep = f & ORC_KEEP;
-        if (keep) ++pos;
-        const double dx = px - xy[2 * g], dy = py - xy[2 * g + 1];
-        const double qa = conic[3 * g] * dx * dx;
-        const double qb = 2.0 * conic[3 * g + 1] * dx * dy;
-        const double qc = conic[3 * g + 2] * dy * dy;
-        const double power = -0.5 * (qa + qb + qc);
-        const double oG = opac[g] * exp(power);
-        /* relative float32 error of o G: opacity and exp rounding, the
-         * rounding of the form (form_error_scale) and the position error of
-         * mu2D */
-        const double pos_err = mg->pos_rel * fmax(1.0, fmax(fabs(xy[2 * g]), fabs(xy[2 * g + 1])));
-        const double grad = fabs(conic[3 * g] * dx + conic[3 * g + 1] * dy) +
-                            fabs(conic[3 * g + 1] * dx + conic[3 * g + 2] * dy);
-        const double mag = mg->q_rel > 0.0
-                               ? form_error_scale(conic[3 * g], conic[3 * g + 1], conic[3 * g + 2], dx, dy)
-                               : 0.0;
-        const double slack = mg->rel + 0.5 * mg->q_rel * mag + pos_err * grad;
-        /* is whether this entry is blended a decision float32 may take the other way? */
-        int uncertain = 0;
-        if (!keep || (f & ORC_IMARGINAL)) uncertain |= oG >= ORC_ALPHA_MIN * (1.0 - slack);
-        if (keep) {
-            uncertain |= fabs(power) <= 0.5 * mg->q_rel * mag + (mg->q_rel > 0.0 ? 1e-12 : 0.0);
-            uncertain |= fabs(oG - ORC_ALPHA_MIN) <= ORC_ALPHA_MIN * slack;
-            /* the clamp: no effect on the value, a kink for derivatives; flagged
-             * only when every decision is (value_tol = 0) */
-            if (mg->value_tol <= 0.0 && fabs(oG - ORC_ALPHA_MAX) <= ORC_ALPHA_MAX * slack) amb = 1;
-        }
-        const double alpha = oG < ORC_ALPHA_MAX ? oG : ORC_ALPHA_MAX;
-        const int blend = keep && power <= 0.0 && alpha >= ORC_ALPHA_MIN;
+        orc_entry en;
+        entry_eval(px, py, g, f, xy, conic, opac, mg, &en);
+        if (en.keep) ++pos;
+        const int uncertain = en.uncertain;
+        const double slack = en.slack;
+        /* the clamp: no effect on the value, a kink for derivatives; flagged
+         * only when every decision is (value_tol = 0) */
+        if (mg->value_tol <= 0.0 && en.near_clamp) amb = 1;
+        const double alpha = en.alpha;
+        const int blend = en.blend;
         /* this entry's blend decision taken the other way scales T by 1 - a */
         const double a_flip = alpha > ORC_ALPHA_MIN ? alpha : ORC_ALPHA_MIN;
         const double own_flip = uncertain && mg->t_rel > 0.0 ? a_flip / (1.0 - a_flip) : 0.0;
@@ -814,6 +842,196 @@ int orc_blend_forward(int32_t width, int32_t height, const int64_t *ranges,
         allowance[p] = r.allowance;
     }
     return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Admissible decision paths of a pixel (a float32 evaluation's results)   */
+/* ---------------------------------------------------------------------- */
+
+/* Every result a float32 evaluation of one pixel's walk may legitimately
+ * reach.  The pixel's candidates -- the entries FP64 blends and those whose
+ * blend decision float32 may take the other way (entry_eval) -- are walked
+ * front to back, and the walk branches at each decision float32 may take
+ * either way:
+ *  - an uncertain blend decision: the entry skipped, or blended with its
+ *    FP64 alpha;
+ *  - a stop test whose tested T (1 - alpha) lies within its float32 error
+ *    bound of 1e-4: stopped before the entry, or the entry blended and on;
+ *  - two consecutive candidates with depths tied within depth_rel: both
+ *    orders (the sort may order them either way).
+ * Every other decision is taken as FP64 takes it.  The error bound of the
+ * tested T is pixel_walk's without its flip terms, since each branch takes
+ * its decisions explicitly: t_rel plus (alpha slack + 2^-23) / (1 - alpha)
+ * for every blended factor.  Each end of a walk is one admissible result:
+ * C + T bg, T, and the last blended Gaussian.  One result means every
+ * decision of the pixel is determined.  The walk gives up (overflow) beyond
+ * max_paths results, or at three consecutive tied candidates. */
+typedef struct {
+    int32_t gid;
+    int uncertain;
+    double alpha, slack, depth, c[3];
+} orc_cand;
+
+typedef struct {
+    orc_cand *seq;
+    int64_t m;
+    double bg[3];
+    double t_rel, t_unit, depth_rel;
+    int max_paths, npaths, overflow;
+    double *val;  /* max_paths x 5: C + T bg (3), T, last blended Gaussian (-1: none) */
+} orc_paths;
+
+static void paths_emit(orc_paths *x, const double C[3], double T, int32_t last)
+{
+    if (x->npaths >= x->max_paths) {
+        x->overflow = 1;
+        return;
+    }
+    double *v = x->val + 5 * x->npaths++;
+    for (int ch = 0; ch < 3; ++ch) v[ch] = C[ch] + T * x->bg[ch];
+    v[3] = T;
+    v[4] = (double)last;
+}
+
+static int cand_tied(const orc_paths *x, int64_t a, int64_t b)
+{
+    return x->depth_rel > 0.0 && fabs(x->seq[a].depth - x->seq[b].depth) <= x->depth_rel * fabs(x->seq[a].depth);
+}
+
+static void cand_swap(orc_paths *x, int64_t k)
+{
+    const orc_cand tmp = x->seq[k];
+    x->seq[k] = x->seq[k + 1];
+    x->seq[k + 1] = tmp;
+}
+
+/* Walks candidates k.. from transmittance T, colour C and the accumulated
+ * error bound t_err of T; tie_done: the order of candidates k and k + 1 was
+ * already branched on. */
+static void paths_walk(orc_paths *x, int64_t k, double T, const double C_in[3], double t_err,
+                       int32_t last, int tie_done)
+{
+    double C[3] = {C_in[0], C_in[1], C_in[2]};
+    for (; k < x->m; ++k, tie_done = 0) {
+        if (x->overflow) return;
+        if (!tie_done && k + 1 < x->m && cand_tied(x, k, k + 1)) {
+            if (k + 2 < x->m && (cand_tied(x, k + 1, k + 2) || cand_tied(x, k, k + 2))) {
+                x->overflow = 1;
+                return;
+            }
+            cand_swap(x, k);
+            paths_walk(x, k, T, C, t_err, last, 1);
+            cand_swap(x, k);
+            if (x->overflow) return;
+        }
+        const orc_cand *e = &x->seq[k];
+        if (e->uncertain) {
+            paths_walk(x, k + 1, T, C, t_err, last, 0);  /* the entry skipped */
+            if (x->overflow) return;
+        }
+        /* the entry blended: first the stop test */
+        const double test = T * (1.0 - e->alpha);
+        const double eps = (e->alpha * e->slack + x->t_unit) / (1.0 - e->alpha);
+        const double bound = x->t_rel + t_err + eps;
+        const int near = fabs(test - ORC_T_MIN) <= ORC_T_MIN * bound;
+        if (test < ORC_T_MIN || near) {
+            paths_emit(x, C, T, last);  /* stopped before the entry */
+            if (!near) return;
+        }
+        for (int ch = 0; ch < 3; ++ch) C[ch] += e->alpha * T * e->c[ch];
+        T = test;
+        t_err += eps;
+        last = e->gid;
+    }
+    paths_emit(x, C, T, last);
+}
+
+/* For every pixel of the tile-based forward (inputs as orc_blend_forward):
+ * status[H,W] = 0 when the pixel has one admissible result (every decision
+ * determined), 1 when it has several, 2 when their enumeration overflowed
+ * (then only pixel_walk's allowance bounds the pixel).  The results of the
+ * status-1 pixels are appended to path_pix (pixel index v W + u) and
+ * path_val (5 per result, as paths_emit writes them), up to `cap` results in
+ * all, in no particular order; *n_out receives the number of results there
+ * were (when it exceeds cap, the call must be repeated with a larger cap).
+ * Returns -1 when a scratch allocation fails. */
+int orc_blend_paths(int32_t width, int32_t height, const int64_t *ranges, const int32_t *list_gid,
+                    const uint8_t *list_flags, const double *xy, const double *conic,
+                    const double *opac, const double *rgb, const double *depth, const double *bg,
+                    const orc_margins *mg, int32_t max_paths, int64_t cap, uint8_t *status,
+                    int64_t *n_out, int64_t *path_pix, double *path_val)
+{
+    const int tiles_x = (width + ORC_TILE - 1) / ORC_TILE;
+    const int tiles_y = (height + ORC_TILE - 1) / ORC_TILE;
+    const int64_t npix = (int64_t)width * height;
+    int64_t longest = 1;
+    for (int64_t t = 0; t < (int64_t)tiles_x * tiles_y; ++t)
+        if (ranges[2 * t + 1] - ranges[2 * t] > longest) longest = ranges[2 * t + 1] - ranges[2 * t];
+    int64_t total = 0;
+    int failed = 0;
+#pragma omp parallel
+    {
+        orc_cand *seq = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)longest);
+        double *val = (double *)malloc(sizeof(double) * 5 * (size_t)(max_paths > 0 ? max_paths : 1));
+        if (!seq || !val) {
+#pragma omp atomic write
+            failed = 1;
+        }
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t p = 0; p < npix; ++p) {
+            if (!seq || !val) continue;
+            const int u = (int)(p % width), v = (int)(p / width);
+            const int t = (v / ORC_TILE) * tiles_x + (u / ORC_TILE);
+            const double px = u + 0.5, py = v + 0.5;
+            orc_paths x;
+            x.seq = seq;
+            x.m = 0;
+            for (int ch = 0; ch < 3; ++ch) x.bg[ch] = bg[ch];
+            x.t_rel = mg->t_rel;
+            x.t_unit = mg->t_rel > 0.0 ? 0x1p-23 : 0.0;
+            x.depth_rel = mg->depth_rel;
+            x.max_paths = max_paths;
+            x.npaths = 0;
+            x.overflow = 0;
+            x.val = val;
+            for (int64_t j = ranges[2 * t]; j < ranges[2 * t + 1]; ++j) {
+                const int32_t g = list_gid[j];
+                orc_entry en;
+                entry_eval(px, py, g, list_flags ? list_flags[j] : ORC_KEEP, xy, conic, opac, mg, &en);
+                if (!(en.blend || en.uncertain)) continue;
+                orc_cand *c = &seq[x.m++];
+                c->gid = g;
+                c->uncertain = en.uncertain;
+                c->alpha = en.alpha;
+                c->slack = en.slack;
+                c->depth = depth[g];
+                for (int ch = 0; ch < 3; ++ch) c->c[ch] = rgb[3 * g + ch];
+            }
+            const double C0[3] = {0.0, 0.0, 0.0};
+            paths_walk(&x, 0, 1.0, C0, 0.0, -1, 0);
+            if (x.overflow) {
+                status[p] = 2;
+            } else if (x.npaths <= 1) {
+                status[p] = 0;
+            } else {
+                status[p] = 1;
+                int64_t off;
+#pragma omp atomic capture
+                {
+                    off = total;
+                    total += x.npaths;
+                }
+                for (int k = 0; k < x.npaths && off + k < cap; ++k) {
+                    path_pix[off + k] = p;
+                    for (int q = 0; q < 5; ++q) path_val[5 * (off + k) + q] = val[5 * k + q];
+                }
+            }
+        }
+        free(seq);
+        free(val);
+    }
+    *n_out = total;
+    return failed ? -1 : 0;
 }
 
 /* Brute-force twin: every pixel walks ONE list holding every visible

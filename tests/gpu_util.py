@@ -2,6 +2,8 @@
 the FP64 oracle on the same seeded inputs, and compare what is unique."""
 from __future__ import annotations
 
+from dataclasses import dataclass
+
 import numpy as np
 import torch
 
@@ -89,18 +91,107 @@ def oracle_forward(params, cams, sh_degree=3, bg=(0.0, 0.0, 0.0), margins=oracle
     return pres, lists, outs
 
 
-def image_check(img, out, tol=IMAGE_TOL):
-    """GPU image [3,H,W] against the oracle's: on every pixel whose float32
-    decisions all have a bounded effect, |GPU - oracle| must stay within tol
-    plus the oracle's allowance (the summed effects of the decisions float32
-    may take the other way; zero for most pixels).  Returns (worst excess
-    over that bound, max abs error on those pixels, pixels with an unbounded
-    decision, pixels with a non-zero allowance)."""
-    err = np.abs(np.asarray(img, np.float64) - out["image"]).max(axis=0)
-    ok = ~out["hard"].astype(bool)
-    excess = (err - tol - out["allowance"])[ok]
-    return (float(excess.max(initial=-np.inf)), float(err[ok].max(initial=0.0)),
-            int((~ok).sum()), int((out["allowance"] > 0).sum()))
+T_TOL = 5e-5              # final transmittance, where its decisions are those of a path
+
+
+def gpu_pixel_state(rast, views):
+    """Per view: the GPU's final transmittance T[H,W] and last blended
+    Gaussian [H,W] (-1 for none), read from the workspace of the last
+    forward (n_contrib is the 1-based list position of the last blended
+    entry in the pixel's tile list)."""
+    Tg, ncg = rast.per_pixel()
+    Tg, ncg = Tg.cpu().numpy(), ncg.cpu().numpy().astype(np.int64)
+    _, vals, ranges = rast.sorted_lists()
+    vals = vals.cpu().numpy().astype(np.int64)
+    ranges = ranges.cpu().numpy().astype(np.int64)
+    out, tile_off = [], 0
+    for v, (W, H) in enumerate(views.sizes):
+        a, b = int(views.pix_off[v]), int(views.pix_off[v + 1])
+        nc = ncg[a:b].reshape(H, W)
+        tx, ty = (W + 15) // 16, (H + 15) // 16
+        uu, vv = np.meshgrid(np.arange(W), np.arange(H))
+        start = ranges[tile_off + (vv // 16) * tx + (uu // 16), 0]
+        last = np.where(nc > 0, vals[np.maximum(start + nc - 1, 0)], -1)
+        out.append((Tg[a:b].reshape(H, W), last))
+        tile_off += tx * ty
+    return out
+
+
+@dataclass
+class ImageCheck:
+    """Outcome of image_check.  bad: pixels that fail their check;
+    exact_pixels / exact_max: pixels whose every float32 decision is
+    determined and their max abs error; path_pixels / path_max: pixels
+    checked against the admissible results of the oracle's decision paths
+    and the largest error to the nearest admissible result; allowance_pixels
+    / allowance_excess: pixels whose paths overflowed, held to tol plus the
+    oracle's summed allowance, and their largest excess over that bound;
+    excluded: pixels with no bound at all (none in any test scene)."""
+    bad: int
+    exact_pixels: int
+    exact_max: float
+    path_pixels: int
+    path_max: float
+    allowance_pixels: int
+    allowance_excess: float
+    excluded: int
+
+    @property
+    def pixels(self):
+        return self.exact_pixels + self.path_pixels + self.allowance_pixels + self.excluded
+
+    def summary(self):
+        return (f"{self.path_pixels} px checked against an admissible path (max err to the nearest "
+                f"{self.path_max:.2e}), {self.allowance_pixels} px on allowance, {self.excluded} "
+                f"excluded, max err on {self.exact_pixels} exact px {self.exact_max:.2e}")
+
+
+def image_check(img, out, tol=IMAGE_TOL, T=None, last=None, t_tol=T_TOL):
+    """GPU image [3,H,W] (and optionally its final transmittance T[H,W] and
+    last blended Gaussian last[H,W], -1 for none) against the oracle.
+    Every pixel whose float32 decisions are all determined (path status 0)
+    must be within tol of the oracle (T within t_tol, the same last
+    Gaussian).  A pixel with decisions float32 may take either way (status
+    1) must be within tol of one of the FP64 results of its admissible
+    decision paths, jointly in colour, T and last Gaussian.  Only pixels
+    whose paths overflowed (status 2) fall back to tol plus the oracle's
+    summed first-order allowance; pixels without a bound at all (hard) are
+    excluded and counted."""
+    img = np.asarray(img, np.float64)
+    H, W = img.shape[1:]
+    err = np.abs(img - out["image"]).max(axis=0)
+    status = out["status"]
+    hard = out["hard"].astype(bool) & (status == 2)
+    exact = status == 0
+    bad = exact & (err > tol)
+    if T is not None:
+        bad |= exact & (np.abs(np.asarray(T, np.float64) - out["T_final"]) > t_tol)
+    if last is not None:
+        bad |= exact & (np.asarray(last) != out["last_gid"])
+    # several admissible results: the nearest one, all fields at once
+    pix, val = out["path_pix"], out["path_val"]
+    flat = img.reshape(3, -1)
+    d = np.abs(val[:, :3] - flat[:, pix].T).max(axis=1)
+    fits = d <= tol
+    if T is not None:
+        fits &= np.abs(val[:, 3] - np.asarray(T, np.float64).reshape(-1)[pix]) <= t_tol
+    if last is not None:
+        fits &= val[:, 4] == np.asarray(last).reshape(-1)[pix]
+    any_fit = np.zeros(H * W, bool)
+    np.logical_or.at(any_fit, pix, fits)
+    nearest = np.full(H * W, np.inf)
+    np.minimum.at(nearest, pix, d)
+    multi = (status == 1).reshape(-1)
+    bad |= (multi & ~any_fit).reshape(H, W)
+    # overflowed enumerations: the allowance bound
+    over = (status == 2) & ~hard
+    excess = (err - tol - out["allowance"])[over]
+    bad |= over & (err > tol + out["allowance"])
+    return ImageCheck(bad=int(bad.sum()), exact_pixels=int(exact.sum()),
+                      exact_max=float(err[exact].max(initial=0.0)), path_pixels=int(multi.sum()),
+                      path_max=float(nearest[multi].max(initial=0.0)),
+                      allowance_pixels=int(over.sum()),
+                      allowance_excess=float(excess.max(initial=-np.inf)), excluded=int(hard.sum()))
 
 
 def dilate_mask(m, r):

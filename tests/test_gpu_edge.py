@@ -12,7 +12,8 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 from gpu_util import (GRAD_REL_L2, ambiguity_masks, compare_lists, gpu_forward, gpu_grads,  # noqa: E402
-                      grad_errors, ill_conditioned, image_check, oracle_forward, oracle_grads)
+                      gpu_pixel_state, grad_errors, ill_conditioned, image_check, oracle_forward,
+                      oracle_grads)
 from paper_2602_09999_gb300 import binding as B  # noqa: E402
 from paper_2602_09999_gb300 import scenes  # noqa: E402
 from paper_2602_09999_gb300 import train as T  # noqa: E402
@@ -24,9 +25,12 @@ def _images_match(params, cams, bg=(0.0, 0.0, 0.0)):
     rast, views, t, images = gpu_forward(params, cams, bg=bg)
     pres, lists, outs = oracle_forward(params, cams, bg=bg)
     compare_lists(rast, views, pres, lists)
+    states = gpu_pixel_state(rast, views)
     for v, img in enumerate(views.split(images)):
-        excess, worst, hard, allowed = image_check(img.cpu().numpy(), outs[v])
-        assert excess <= 0.0, (v, excess, worst)
+        T_, last = states[v]
+        r = image_check(img.cpu().numpy(), outs[v], T=T_, last=last)
+        assert r.bad == 0 and r.excluded == 0, (v, r)
+        assert r.allowance_pixels <= 1e-4 * r.pixels, (v, r)
     return rast, views, images, outs
 
 

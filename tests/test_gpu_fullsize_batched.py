@@ -5,9 +5,12 @@ dynamic scene (600k Gaussians with velocity and temporal centre, 6 views of
 uneven sizes at different times, the launch configuration bench.py times for
 it).  One graph replay of the whole step (forward, loss, backward and the
 fused Adam update, with the gradients also stored) is compared against the
-FP64 oracle on the same seeded inputs: every view's image within 2e-4 plus
-the oracle's per-pixel allowance (pixels with an unbounded float32 decision
-excluded and counted), the batch loss, and every gradient tensor within 1e-3
+FP64 oracle on the same seeded inputs: every view's image, final
+transmittance and last contributor against the oracle where every float32
+decision is determined, else against one of the FP64 results of the pixel's
+admissible decision paths (colour within 2e-4), the batch loss, the
+replay's own stored gradients against an eager backward of the same
+parameters, and every gradient tensor within 1e-3
 relative L2 (dL/dC zeroed on both sides where float32 decisions can move the
 value beyond the image tolerance or flip the sign of the L1 term; Gaussians whose footprint dwarfs the image
 excluded and counted).  The Adam update is checked by its first-step closed
@@ -20,7 +23,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
-from gpu_util import GRAD_REL_L2, grad_errors, gradient_mask, ill_conditioned, image_check  # noqa: E402
+from gpu_util import (GRAD_REL_L2, gpu_pixel_state, grad_errors, gradient_mask,  # noqa: E402
+                      ill_conditioned, image_check)
 from paper_2602_09999_gb300 import scenes  # noqa: E402
 from paper_2602_09999_gb300 import train as T  # noqa: E402
 from paper_2602_09999_gb300 import tune  # noqa: E402
@@ -80,15 +84,17 @@ def _oracle_batch(params, cams, targets):
 
 def _check(tr, before, params, cams, targets):
     outs, masks, L_o, g_o = _oracle_batch(params, cams, targets)
-    hard_total = pixels = 0
+    states = gpu_pixel_state(tr.rast, tr.views)
+    checks = []
     for v, img in enumerate(tr.views.split(tr.images)):
-        excess, worst, hard, allowed = image_check(img.cpu().numpy(), outs[v])
-        print(f"view {v} {cams[v].width}x{cams[v].height}: max err {worst:.2e}, "
-              f"hard {hard}, with allowance {allowed}")
-        assert excess <= 0.0, (v, excess, worst)
-        hard_total += hard
-        pixels += outs[v]["hard"].size
-    assert hard_total <= 0.01 * pixels
+        r = image_check(img.cpu().numpy(), outs[v], T=states[v][0], last=states[v][1])
+        print(f"view {v} {cams[v].width}x{cams[v].height}: {r.summary()}")
+        assert r.bad == 0 and r.excluded == 0, (v, r)
+        checks.append(r)
+    allow = sum(r.allowance_pixels for r in checks)
+    pixels = sum(r.pixels for r in checks)
+    print(f"pixels on allowance: {allow} of {pixels}")
+    assert allow <= 1e-4 * pixels
     # the GPU's loss is over unmasked dL/dC; compare it directly
     assert float(tr.loss.item()) == pytest.approx(L_o, rel=1e-5)
 
@@ -96,8 +102,19 @@ def _check(tr, before, params, cams, targets):
     # gradients with the masks through the same workspace (forward state of
     # the replay is still in place; the parameters have moved, so take the
     # pre-update copies)
-    g_gpu = _masked_gpu_grads(tr, before, masks)
+    replay = {k: tr.grads[k].cpu().numpy() for k in tr.groups}
     bad = ill_conditioned(cams, params)
+    # the replay's own gradients (unmasked dL/dC, stored by the fused kernel)
+    # against an eager, unmasked backward of the same parameters: the two
+    # differ only in the order of the float32 atomic additions
+    g_eager = _masked_gpu_grads(tr, before, None)
+    own = grad_errors(replay, g_eager, bad)
+    own_raw = grad_errors(replay, g_eager, None)
+    print("replay vs eager:", {k: f"{e:.2e}" for k, e in own.items()},
+          "with ill-conditioned:", {k: f"{e:.2e}" for k, e in own_raw.items()})
+    for k, e in own.items():
+        assert e <= GRAD_REL_L2, ("replay", k, e)
+    g_gpu = _masked_gpu_grads(tr, before, masks)
     errs = grad_errors(g_gpu, g_o, bad)
     print({k: f"{e:.2e}" for k, e in errs.items()}, "ill-conditioned", int(bad.sum()))
     assert set(errs) == set(tr.groups)
@@ -120,8 +137,9 @@ def _check(tr, before, params, cams, targets):
 
 
 def _masked_gpu_grads(tr, before, masks):
-    """Gradients of the pre-update parameters with dL/dC zeroed on the masks,
-    through the same rasterizer (its forward is re-run on those parameters)."""
+    """Gradients of the pre-update parameters with dL/dC zeroed on the masks
+    (None: unmasked), through the same rasterizer (its forward is re-run on
+    those parameters)."""
     p = {k: before[k] for k in tr.groups}
     if "sigma_t" in tr.params:
         p["sigma_t"] = tr.params["sigma_t"]
@@ -130,7 +148,7 @@ def _masked_gpu_grads(tr, before, masks):
     dl = torch.zeros_like(tr.dl)
     loss = torch.zeros(1, device="cuda")
     tr.rast.loss(tr.images, tr.targets, tr.lam, loss, dl)
-    for v, m in enumerate(masks):
+    for v, m in enumerate(masks or []):
         tr.views.split(dl)[v][:, torch.from_numpy(m).cuda()] = 0.0
     grads = {k: torch.zeros(before[k].shape, device="cuda") for k in tr.groups}
     tr.rast.backward(ps, tr.sh_degree, tr.bg, dl, T.params_struct(grads))

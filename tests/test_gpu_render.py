@@ -1,8 +1,11 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
 same seeded inputs: per-Gaussian screen state, tile lists (bit-exact after
-removing decisions float32 may take either way), images (max abs 2e-4
-outside ambiguous pixels), loss, gradients (relative L2 1e-3 per tensor),
-Adam and the full step, single and batched uneven views."""
+removing decisions float32 may take either way), images, final
+transmittance and last contributor (against the oracle's result where every
+float32 decision is determined, else against one of the results of the
+pixel's admissible decision paths; colour within 2e-4), loss, gradients
+(relative L2 1e-3 per tensor), Adam and the full step, single and batched
+uneven views."""
 import dataclasses
 import math
 
@@ -14,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 from gpu_util import (GRAD_REL_L2, IMAGE_TOL, ambiguity_masks, compare_lists,  # noqa: E402
-                      gpu_forward, gpu_grads, grad_errors, ill_conditioned, image_check,
+                      gpu_forward, gpu_grads, gpu_pixel_state, grad_errors, ill_conditioned, image_check,
                       oracle_forward, oracle_grads, rel_l2)
 from paper_2602_09999_gb300 import binding as B  # noqa: E402
 from paper_2602_09999_gb300 import scenes  # noqa: E402
@@ -85,41 +88,25 @@ def test_tile_lists_bit_exact(case):
 
 
 def test_images_within_tolerance(case):
+    """Every pixel: colour, final transmittance and last blended Gaussian
+    equal to the oracle's (colour within 2e-4, T within 5e-5) where every
+    float32 decision is determined, else jointly equal to one of the FP64
+    results of the pixel's admissible decision paths; pixels whose paths
+    overflow (held to the allowance bound instead) stay below 1e-4 of the
+    pixels."""
     imgs = case["views"].split(case["images"])
-    Tg, ncg = case["rast"].per_pixel()
-    Tg, ncg = Tg.cpu().numpy(), ncg.cpu().numpy()
-    _, vals, ranges = [x.cpu().numpy() if hasattr(x, "cpu") else x
-                       for x in case["rast"].sorted_lists()]
-    pix_off = case["views"].pix_off
-    total_amb = total_hard = 0
-    tile_off = 0
+    states = gpu_pixel_state(case["rast"], case["views"])
+    npx = allow = paths = 0
     for v, out in enumerate(case["outs"]):
-        img = imgs[v].cpu().numpy()
-        excess, worst, hard, allowed = image_check(img, out)
-        assert excess <= 0.0, (case["name"], excess, worst)
-        total_hard += hard
-        # per-pixel state (T_final, last contributor) changes with any decision
-        # float32 may take the other way: compared where there is none
-        strict = oracle.blend_forward(case["cams"][v], case["pres"][v], case["lists"][v],
-                                      margins=dataclasses.replace(oracle.FP32_MARGINS, value_tol=0.0))
-        amb = strict["ambiguous"].astype(bool)
-        total_amb += int(amb.sum())
-        H, W = amb.shape
-        Tv = Tg[pix_off[v]:pix_off[v + 1]].reshape(H, W)
-        assert np.abs(Tv - out["T_final"])[~amb].max() <= 5e-5
-        # last contributor: unique Gaussian id
-        nc = ncg[pix_off[v]:pix_off[v + 1]].reshape(H, W).astype(np.int64)
-        tx = case["cams"][v].tiles[0]
-        uu, vv = np.meshgrid(np.arange(W), np.arange(H))
-        tiles = tile_off + (vv // 16) * tx + (uu // 16)
-        start = ranges.reshape(-1, 2)[tiles, 0].astype(np.int64)
-        last = np.where(nc > 0, vals[np.maximum(start + nc - 1, 0)], -1)
-        np.testing.assert_array_equal(last[~amb], out["last_gid"][~amb])
-        tile_off += case["lists"][v]["ranges"].shape[0]
-    npx = sum(o["image"].shape[1] * o["image"].shape[2] for o in case["outs"])
-    print(f"{case['name']}: unbounded-decision pixels {total_hard}, any-decision {total_amb} / {npx}")
-    assert total_hard <= 1e-2 * npx
-    assert total_amb <= 0.02 * npx
+        T, last = states[v]
+        r = image_check(imgs[v].cpu().numpy(), out, T=T, last=last)
+        assert r.bad == 0, (case["name"], v, r)
+        assert r.excluded == 0, (case["name"], v, r)
+        npx += r.pixels
+        allow += r.allowance_pixels
+        paths += r.path_pixels
+        print(f"{case['name']} view {v}: {r.summary()}")
+    assert allow <= 1e-4 * npx, (case["name"], allow, npx)
 
 
 def test_forward_is_deterministic(case):
