@@ -244,6 +244,18 @@ PROFILED_WORKLOAD = (3_000_000, 1237, 822)
 MORTON_PERIOD = 5000
 
 
+def check_flags(rast, where):
+    """Raises when the workspace's sticky device flags are set, naming them."""
+    from paper_2602_09999_gb300 import binding as B
+    flags, inst = rast.error()
+    if flags:
+        names = [B.fgs_flag_string(b) for b in (B.FGS_FLAG_CAPACITY, B.FGS_FLAG_NONFINITE, B.FGS_FLAG_TIMEOUT)
+                 if flags & b]
+        raise RuntimeError(f"device flags {flags} {where}: {'; '.join(names)} "
+                           f"(instances {inst}, k_max {rast.k_max})")
+    return inst
+
+
 def fp32_peak_tflops(sm_count, sm_mhz):
     """128 FP32 lanes per SM, one FMA (2 ops) per lane per clock."""
     return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -311,9 +323,7 @@ def run_ours(args, dist):
     for i in range(args.warmup):
         one_step(i)
     torch.cuda.synchronize()
-    flags, _ = tr.rast.error()
-    if flags:
-        raise RuntimeError(f"device flags {flags} after warm-up (capacity)")
+    check_flags(tr.rast, "after warm-up")
 
     clock = ClockSampler(dist.local)
     t0 = torch.cuda.Event(enable_timing=True)
@@ -330,9 +340,7 @@ def run_ours(args, dist):
     clocks = clock.stop()
     dist.barrier()
     elapsed_ms = t0.elapsed_time(t1)
-    flags, inst_last = tr.rast.error()
-    if flags:
-        raise RuntimeError(f"device flags {flags} in the timed region")
+    inst_last = check_flags(tr.rast, "in the timed region")
     max_ms = dist.max(elapsed_ms)
     ms_per_step = max_ms / args.steps
     views_per_s = dist.world * args.steps / (max_ms / 1000.0)
@@ -543,8 +551,7 @@ def run_ours(args, dist):
         q1.record(stream)
         q1.synchronize()
         pg_ms = dist.max(q0.elapsed_time(q1)) / pg_steps
-        if tp.rast.error()[0]:
-            raise RuntimeError("capacity exceeded with the per-Gaussian backward")
+        check_flags(tp.rast, "with the per-Gaussian backward")
         per_gaussian = {"ms_per_step": round(pg_ms, 4),
                         "views_per_s": round(dist.world * 1000.0 / pg_ms, 3),
                         "per_pixel_ms_per_step": round(ms_per_step, 4),
@@ -583,8 +590,7 @@ def run_ours(args, dist):
             load_batch(i)
             tb.replay()
         torch.cuda.synchronize()
-        if tb.rast.error()[0]:
-            raise RuntimeError("capacity exceeded in the batched variant")
+        check_flags(tb.rast, "in the batched variant")
         steps_b = max(10, args.steps // Bv)
         b0 = torch.cuda.Event(enable_timing=True)
         b1 = torch.cuda.Event(enable_timing=True)
@@ -597,8 +603,7 @@ def run_ours(args, dist):
         b1.record(stream)
         b1.synchronize()
         bms = dist.max(b0.elapsed_time(b1))
-        if tb.rast.error()[0]:
-            raise RuntimeError("capacity exceeded in the batched variant")
+        check_flags(tb.rast, "in the batched variant")
         bvps = dist.world * steps_b * Bv / (bms / 1000.0)
         entry = {"views_per_s": round(bvps, 3), "ms_per_step": round(bms / steps_b, 4),
                  "views_per_step": Bv, "resolution": f"{W}x{H}", "graph": True,
@@ -751,8 +756,7 @@ def run_uneven(args, dist, stream, params, plain_views_per_s, pool=25, dtype="bf
     e1.record(stream)
     e1.synchronize()
     ms = dist.max(e0.elapsed_time(e1))
-    if tr.rast.error()[0]:
-        raise RuntimeError("capacity exceeded in the uneven batch")
+    check_flags(tr.rast, f"in the uneven batch ({dtype})")
     mpx = sum(w * h for w, h in sizes) / 1e6
     vps = dist.world * steps * nv / (ms / 1000.0)
     out = {"views_per_s": round(vps, 3), "megapixels_per_s": round(vps / nv * mpx, 3),
@@ -813,8 +817,7 @@ def run_indoor(args, dist, stream, n=2_500_000, views=8, pool=12):
         load(i)
         tr.replay()
     torch.cuda.synchronize()
-    if tr.rast.error()[0]:
-        raise RuntimeError("device flags in the indoor batch")
+    check_flags(tr.rast, "in the indoor batch")
     steps = max(10, args.steps // views)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -827,8 +830,7 @@ def run_indoor(args, dist, stream, n=2_500_000, views=8, pool=12):
     e1.record(stream)
     e1.synchronize()
     ms = dist.max(e0.elapsed_time(e1))
-    if tr.rast.error()[0]:
-        raise RuntimeError("device flags in the indoor batch")
+    check_flags(tr.rast, "in the indoor batch")
     out = {"views_per_s": round(dist.world * steps * views / (ms / 1000.0), 3),
            "ms_per_step": round(ms / steps, 4), "views_per_step": views, "resolution": f"{W}x{H}",
            "gaussians": n, "storage": "float32", "graph": True, "steps": steps,
@@ -883,8 +885,7 @@ def run_dynamic(args, dist, stream, profile_pass, per_step_ms, n=600_000, views=
         load(i)
         tr.replay()
     torch.cuda.synchronize()
-    if tr.rast.error()[0]:
-        raise RuntimeError("capacity exceeded in the dynamic workload")
+    check_flags(tr.rast, "in the dynamic workload")
     steps = max(10, args.steps // views)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -897,8 +898,7 @@ def run_dynamic(args, dist, stream, profile_pass, per_step_ms, n=600_000, views=
     e1.record(stream)
     e1.synchronize()
     ms = dist.max(e0.elapsed_time(e1))
-    if tr.rast.error()[0]:
-        raise RuntimeError("capacity exceeded in the dynamic workload")
+    check_flags(tr.rast, "in the dynamic workload")
     out = {"workload": f"dynamic Gaussians (velocity, temporal centre, sigma_t 0.1), {n} "
                        f"Gaussians, SH degree 3, {views} views per step at random times "
                        f"(150 timestamps) and poses, float32, 0.8 L1 + 0.2 D-SSIM, Adam",

@@ -74,10 +74,13 @@ enum fgs_status {
  * (dropped instances, NaN or infinity), and the caller decides. */
 enum fgs_device_flags {
     FGS_FLAG_CAPACITY = 1u,  /* instances exceeded k_max; the extra ones were dropped */
-    FGS_FLAG_NONFINITE = 2u  /* a NaN or infinity reached the loss (a per-view sum or
+    FGS_FLAG_NONFINITE = 2u, /* a NaN or infinity reached the loss (a per-view sum or
                                 dL/dimages, set by fgs_loss_l1_dssim) or an Adam update
                                 (a new parameter or moment, set by the fused
                                 fgs_render_backward_adam) */
+    FGS_FLAG_TIMEOUT = 4u    /* a bounded wait of a kernel on its own asynchronous copies gave
+                                up (the fused fgs_render_backward_adam); the update of some
+                                Gaussians is then incomplete */
 };
 
 enum fgs_dtype { FGS_F32 = 0, FGS_BF16 = 1, FGS_F16 = 2 };
@@ -169,7 +172,10 @@ enum fgs_ws_slot {
  * list entries staged per shared-memory batch (64, 128 or 256).  Supported
  * pairs: (1,256) (2,128) (2,256) (4,64) (4,128) (4,256).  The per-pixel
  * blend backward may take its own pair (backward_pixels_per_thread,
- * backward_batch; both 0, the default: the forward's pair).
+ * backward_batch; both 0, the default: the forward's pair).  The radix
+ * digit width of each of the two sorts (Sec. 3.2 "Sorting": a pass per
+ * digit) is 8 or 11 bits: 11 takes 3 passes instead of 4 over the 32 depth
+ * bits, with 2048 digit counters per CTA instead of 256.
  * fgs_workspace_size fills the defaults; an autotuner may overwrite them in
  * the layout before the calls that use it.  The forward and the backward
  * that share a workspace must run with the same layout. */
@@ -180,7 +186,10 @@ typedef struct fgs_tuning {
     int32_t blend_backward;  /* FGS_BACKWARD_PER_PIXEL (default) or FGS_BACKWARD_PER_GAUSSIAN */
     int32_t backward_pixels_per_thread;  /* 0: blend_pixels_per_thread */
     int32_t backward_batch;              /* 0: blend_batch */
-    int32_t reserved[2];
+    int32_t depth_sort_digit_bits;       /* radix digit of the depth sort: 8 or 11 (0: 8) */
+    int32_t tile_sort_digit_bits;        /* radix digit of the tile sort: 8 or 11 (0: 8); the
+                                            layout's sorted_in_alt must then be the parity of
+                                            ceil(sort_bits / digit bits) */
 } fgs_tuning;
 
 /* Order of the blend backward (the same gradients up to float32 rounding).
@@ -213,7 +222,8 @@ typedef struct fgs_workspace_layout {
     int32_t total_tiles;
     int64_t total_pixels;
     int32_t sort_bits;       /* tile-id bits the tile sort orders (the depth sort: 32) */
-    int32_t sorted_in_alt;   /* 1: the tile-sorted keys/values end in the *_ALT slots */
+    int32_t sorted_in_alt;   /* 1: the tile-sorted keys/values end in the *_ALT slots (an odd
+                                number of passes of tuning.tile_sort_digit_bits) */
     int32_t flags;           /* the FGS_WS_* options the layout was made with */
     fgs_tuning tuning;       /* launch choices (defaults filled in) */
 } fgs_workspace_layout;

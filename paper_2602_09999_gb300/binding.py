@@ -22,6 +22,7 @@ FGS_NUM_GROUPS = 8
 FGS_F32, FGS_BF16, FGS_F16 = 0, 1, 2
 FGS_FLAG_CAPACITY = 1
 FGS_FLAG_NONFINITE = 2
+FGS_FLAG_TIMEOUT = 4
 
 (FGS_WS_HEADER, FGS_WS_SCREEN, FGS_WS_RECT, FGS_WS_LOCAL_OFF, FGS_WS_BLOCK_SUM, FGS_WS_KEYS,
  FGS_WS_VALS, FGS_WS_KEYS_ALT, FGS_WS_VALS_ALT, FGS_WS_SORT_HIST, FGS_WS_RANGES, FGS_WS_T_FINAL,
@@ -70,10 +71,11 @@ class fgs_tuning(ctypes.Structure):
     _fields_ = [("blend_pixels_per_thread", ctypes.c_int32), ("blend_batch", ctypes.c_int32),
                 ("blend_schedule", ctypes.c_int32), ("blend_backward", ctypes.c_int32),
                 ("backward_pixels_per_thread", ctypes.c_int32), ("backward_batch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("depth_sort_digit_bits", ctypes.c_int32), ("tile_sort_digit_bits", ctypes.c_int32)]
 
 
 BLEND_CONFIGS = ((1, 256), (2, 128), (2, 256), (4, 64), (4, 128), (4, 256))
+SORT_DIGIT_BITS = (8, 11)   # radix digit widths of the render path's two sorts
 FGS_SCHEDULE_QUEUE, FGS_SCHEDULE_GRID = 0, 1
 BLEND_SCHEDULES = (FGS_SCHEDULE_QUEUE, FGS_SCHEDULE_GRID)
 FGS_BACKWARD_PER_PIXEL, FGS_BACKWARD_PER_GAUSSIAN = 0, 1

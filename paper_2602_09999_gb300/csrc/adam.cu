@@ -10,7 +10,9 @@
 // Every element is updated, zero gradients included (Sec. 3.3).
 // Storage: parameters float32 / bf16 / fp16; moments float32 / bf16 / fp16.
 // An fp16 second moment is stored as sqrt(v): g^2 underflows fp16 for
-// |g| < 2.4e-4 while |g| itself stays representable.
+// |g| < 2.4e-4 while |g| itself stays representable.  A second moment that
+// still rounds to zero in its storage type stores the first moment as zero
+// too (v_vanishes).
 #include "adam_math.cuh"
 
 namespace fgs {
@@ -79,6 +81,7 @@ adam_kernel(int64_t count, PT* __restrict__ p, const float* __restrict__ g, MT* 
         float mm = to_f32(m[i]);
         float vv = VStore<MT>::load(v[i]);
         const float pn = adam_update(to_f32(p[i]), g[i], mm, vv, a);
+        if (v_vanishes<MT>(vv)) mm = 0.f;
         p[i] = from_f32<PT>(pn);
         m[i] = from_f32<MT>(mm);
         v[i] = VStore<MT>::store(vv);
@@ -99,6 +102,10 @@ adam_f32x4_kernel(int64_t count4, float4* __restrict__ p, const float4* __restri
         pp.y = adam_update(pp.y, gg.y, mm.y, vv.y, a);
         pp.z = adam_update(pp.z, gg.z, mm.z, vv.z, a);
         pp.w = adam_update(pp.w, gg.w, mm.w, vv.w, a);
+        if (vv.x == 0.f) mm.x = 0.f;
+        if (vv.y == 0.f) mm.y = 0.f;
+        if (vv.z == 0.f) mm.z = 0.f;
+        if (vv.w == 0.f) mm.w = 0.f;
         p[i] = pp;
         m[i] = mm;
         v[i] = vv;

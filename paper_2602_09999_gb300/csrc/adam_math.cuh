@@ -28,6 +28,22 @@ template <> __device__ __forceinline__ float v_decode<__half>(float s) { return 
 template <typename MT> __device__ __forceinline__ float v_encode(float v) { return v; }
 template <> __device__ __forceinline__ float v_encode<__half>(float v) { return sqrtf(v); }
 
+// True when the second moment v (decoded value) rounds to zero in its
+// storage type.  The first moment is then stored as zero too: an FP16 sqrt(v)
+// underflows below |g| of about 2e-6 while m = (1 - b1) g still fits, and a
+// later step would divide that m by eps = 1e-15 alone (a parameter thrown by
+// 1e5 learning rates).  With float32 or bf16 storage v rounds to zero only
+// when it is zero.
+template <typename MT> __device__ __forceinline__ bool v_vanishes(float v) { return v == 0.f; }
+template <> __device__ __forceinline__ bool v_vanishes<__nv_bfloat16>(float v)
+{
+    return __bfloat162float(__float2bfloat16_rn(v)) == 0.f;
+}
+template <> __device__ __forceinline__ bool v_vanishes<__half>(float v)
+{
+    return __half2float(__float2half_rn(sqrtf(v))) == 0.f;
+}
+
 struct AdamScalars {
     float step_size, inv_bc2_sqrt, b1, b2, omb1, omb2, eps;
 };

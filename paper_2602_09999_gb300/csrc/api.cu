@@ -18,13 +18,17 @@ cudaError_t launch_sorted_duplicate(int64_t n, const ViewTable& vt, const Screen
                                     const TileRect* rects, const uint32_t* svals, uint32_t* sorted_off,
                                     uint32_t* sorted_block, WsHeader* hdr, int64_t k_max, uint32_t* keys,
                                     uint32_t* vals, cudaStream_t st);
+cudaError_t launch_sh_colour(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
+                             const ViewTable& vt, Screen* screen, const uint32_t* dvals,
+                             const uint32_t* count, cudaStream_t st);
 int64_t count_scan_blocks(int64_t pairs);
 cudaError_t launch_preprocess_bwd(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
                                   const ViewTable& vt, const Screen* screen,
                                   const ScreenGrad* sgrad, const fgs_params* g, cudaStream_t st);
-size_t sort_hist_bytes(int64_t n_max);
+size_t sort_hist_bytes(int64_t n_max, int rb);
+int radix_passes(int bits, int rb);
 int radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n_max,
-                   const uint32_t* n_dev, int bits, uint32_t* hist, bool depth, cudaStream_t st,
+                   const uint32_t* n_dev, int bits, uint32_t* hist, bool depth, int rb, cudaStream_t st,
                    cudaError_t* err);
 int radix_sort(unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
                uint32_t* vals_alt, int64_t n_max, const uint32_t* n_dev, int bits, uint32_t* hist,
@@ -148,6 +152,12 @@ static int sort_bits_for(int64_t total_tiles)
 // The depth sort orders all 32 bits of the (positive) float depths.
 static const int kDepthBits = 32;
 
+// Radix digit widths of the render path's sorts (a launch choice): 8 or 11
+// bits, 0 meaning 8.
+static const int kMaxDigitBits = 11;
+static int digit_bits(int32_t choice) { return choice ? choice : 8; }
+static bool digit_bits_ok(int32_t choice) { return choice == 0 || choice == 8 || choice == 11; }
+
 // Buckets of 32 list entries the per-Gaussian backward can meet: every
 // instance in one, plus a partial bucket per tile.
 static int64_t max_buckets_for(int64_t k_max, int64_t total_tiles)
@@ -177,7 +187,7 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     sz[FGS_WS_VALS] = sizeof(uint32_t) * (size_t)k_max;
     sz[FGS_WS_KEYS_ALT] = sz[FGS_WS_KEYS];
     sz[FGS_WS_VALS_ALT] = sz[FGS_WS_VALS];
-    sz[FGS_WS_SORT_HIST] = sort_hist_bytes(k_max > vn ? k_max : vn);
+    sz[FGS_WS_SORT_HIST] = sort_hist_bytes(k_max > vn ? k_max : vn, kMaxDigitBits);
     sz[FGS_WS_RANGES] = sizeof(uint2) * (size_t)vt->total_tiles;
     sz[FGS_WS_T_FINAL] = sizeof(float) * (size_t)vt->total_pixels;
     sz[FGS_WS_N_CONTRIB] = sizeof(uint32_t) * (size_t)vt->total_pixels;
@@ -211,7 +221,7 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     L->total_tiles = vt->total_tiles;
     L->total_pixels = vt->total_pixels;
     L->sort_bits = sort_bits_for(vt->total_tiles);
-    L->sorted_in_alt = ((L->sort_bits + 7) / 8) & 1;
+    L->sorted_in_alt = radix_passes(L->sort_bits, 8) & 1;
     L->flags = flags;
     L->tuning.blend_pixels_per_thread = kDefaultPPT;
     L->tuning.blend_batch = kDefaultBatch;
@@ -236,6 +246,11 @@ static int check_layout(void* ws, const fgs_workspace_layout* L, const fgs_camer
         return FGS_ERR_ARG;
     if (L->tuning.blend_schedule != FGS_SCHEDULE_QUEUE && L->tuning.blend_schedule != FGS_SCHEDULE_GRID)
         return FGS_ERR_ARG;
+    if (!digit_bits_ok(L->tuning.depth_sort_digit_bits) || !digit_bits_ok(L->tuning.tile_sort_digit_bits))
+        return FGS_ERR_ARG;
+    // where the tile sort leaves its result follows from its digit width
+    if (L->sorted_in_alt != (radix_passes(L->sort_bits, digit_bits(L->tuning.tile_sort_digit_bits)) & 1))
+        return FGS_ERR_WORKSPACE;
     if (L->tuning.blend_backward != FGS_BACKWARD_PER_PIXEL &&
         L->tuning.blend_backward != FGS_BACKWARD_PER_GAUSSIAN)
         return FGS_ERR_ARG;
@@ -328,9 +343,13 @@ int fgs_render_forward(void* ws, const fgs_workspace_layout* L, const fgs_params
     if ((rc = cuda_rc(launch_compact_visible(n, vt, screen, rects, local_off, block_sum, hdr, dkeys, dvals,
                                              st))) != FGS_OK)
         return rc;
+    // the colour of the rendered pairs, from the compacted list
+    if ((rc = cuda_rc(launch_sh_colour(n, sh_degree, params, cams_device, vt, screen, dvals, &hdr->counters[1],
+                                       st))) != FGS_OK)
+        return rc;
     cudaError_t e;
     const int dalt = radix_sort_u32(dkeys, dvals, dkeys_alt, dvals_alt, vn, &hdr->counters[1], kDepthBits,
-                                    hist, true, st, &e);
+                                    hist, true, digit_bits(L->tuning.depth_sort_digit_bits), st, &e);
     if (e != cudaSuccess) return FGS_ERR_CUDA;
     // stage 2: their instances, emitted in depth order, stably by tile id
     if ((rc = cuda_rc(launch_sorted_duplicate(n, vt, screen, rects, dalt ? dvals_alt : dvals,
@@ -340,7 +359,7 @@ int fgs_render_forward(void* ws, const fgs_workspace_layout* L, const fgs_params
         return rc;
     const uint32_t* k_dev = &hdr->counters[0];
     const int alt = radix_sort_u32(keys, vals, keys_alt, vals_alt, L->k_max, k_dev, L->sort_bits, hist,
-                                   false, st, &e);
+                                   false, digit_bits(L->tuning.tile_sort_digit_bits), st, &e);
     if (e != cudaSuccess) return FGS_ERR_CUDA;
     const uint32_t* skeys = alt ? keys_alt : keys;
     const uint32_t* svals = alt ? vals_alt : vals;
@@ -519,7 +538,7 @@ int fgs_adam_step_device(const fgs_params* params, const fgs_params* grads, cons
 
 size_t fgs_sort_scratch_bytes(int64_t n)
 {
-    return align256(sizeof(uint32_t) * 4) + sort_hist_bytes(n > 0 ? n : 0);
+    return align256(sizeof(uint32_t) * 4) + sort_hist_bytes(n > 0 ? n : 0, 8);
 }
 
 int fgs_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
@@ -601,6 +620,7 @@ const char* fgs_flag_string(uint32_t flag)
     switch (flag) {
     case FGS_FLAG_CAPACITY: return "instances exceeded the workspace capacity k_max (extra ones dropped)";
     case FGS_FLAG_NONFINITE: return "a NaN or infinity reached the loss or an Adam update";
+    case FGS_FLAG_TIMEOUT: return "a bounded wait on a kernel's own asynchronous copies gave up";
     default: return "unknown flag";
     }
 }

@@ -24,7 +24,7 @@ int radix_sort_u32_labeled(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, u
                            int64_t n_max, const uint32_t* n_dev, int bits, uint32_t* hist,
                            const char* const labels[3], cudaStream_t st, cudaError_t* err);
 cudaError_t launch_set_count(uint32_t* dst, uint32_t value, cudaStream_t st);
-size_t sort_hist_bytes(int64_t n_max);
+size_t sort_hist_bytes(int64_t n_max, int rb);
 
 namespace {
 
@@ -180,7 +180,7 @@ MortonScratch morton_scratch(int64_t n)
     s.codes_alt = s.codes + v;
     s.ids_alt = s.codes_alt + v;
     s.hist = s.ids_alt + v;
-    s.total = s.hist + align256(sort_hist_bytes(n > 0 ? n : 0));
+    s.total = s.hist + align256(sort_hist_bytes(n > 0 ? n : 0, 8));
     return s;
 }
 

@@ -5,8 +5,9 @@
 // in that order by their tile id alone (a stable sort keeps the depth order
 // inside each tile); the standalone entry points sort 64-bit keys.
 //
-// Each pass orders 8 key bits (the last pass only the remaining ones) with
-// three kernels:
+// Each pass orders RB key bits (the last pass only the remaining ones; RB =
+// 8 or 11, a launch choice that changes speed, never results) with three
+// kernels:
 //   upsweep   : per-CTA digit histogram of 4096 keys -> hist[digit][cta]
 //   scan      : one CTA per digit, exclusive prefix over the CTAs
 //   downsweep : stable rank of each key inside its CTA (warp ballots give
@@ -22,21 +23,25 @@ namespace fgs {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per CTA
-constexpr int kRadix = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 
-template <typename KT>
+// Digit histogram of 4096 keys per CTA.  With 8-bit digits each warp keeps
+// its own copy (fewer shared-atomic collisions); with 11-bit digits two
+// copies are shared by the warps (16 KB of shared memory).
+template <typename KT, int RB>
 __global__ void __launch_bounds__(kSortThreads)
 radix_upsweep_kernel(const KT* __restrict__ keys, const uint32_t* __restrict__ n_dev,
                      int shift, uint32_t dmask, int nb_max, uint32_t* __restrict__ hist)
 {
-    __shared__ uint32_t h[kSortWarps][kRadix];
+    constexpr int kRadix = 1 << RB;
+    constexpr int kCopies = RB <= 8 ? kSortWarps : 2;
+    __shared__ uint32_t h[kCopies][kRadix];
     const uint32_t n = *n_dev;
     const int nb = (int)((n + kSortTile - 1) / kSortTile);
-    const int warp = threadIdx.x >> 5;
+    const int copy = (threadIdx.x >> 5) % kCopies;
     for (int b = blockIdx.x; b < nb; b += gridDim.x) {
         const int64_t base = (int64_t)b * kSortTile;
-        for (int d = threadIdx.x; d < kSortWarps * kRadix; d += kSortThreads) (&h[0][0])[d] = 0;
+        for (int d = threadIdx.x; d < kCopies * kRadix; d += kSortThreads) (&h[0][0])[d] = 0;
         __syncthreads();
         // all loads in flight before the first counter update
         KT k[kSortItems];
@@ -48,13 +53,13 @@ radix_upsweep_kernel(const KT* __restrict__ keys, const uint32_t* __restrict__ n
 #pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
             const int64_t idx = base + (int64_t)r * kSortThreads + threadIdx.x;
-            if (idx < n) atomicAdd(&h[warp][(uint32_t)(k[r] >> shift) & dmask], 1u);
+            if (idx < n) atomicAdd(&h[copy][(uint32_t)(k[r] >> shift) & dmask], 1u);
         }
         __syncthreads();
         for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
             uint32_t s = 0;
 #pragma unroll
-            for (int w = 0; w < kSortWarps; ++w) s += h[w][d];
+            for (int w = 0; w < kCopies; ++w) s += h[w][d];
             hist[(int64_t)d * nb_max + b] = s;
         }
         __syncthreads();
@@ -100,18 +105,50 @@ radix_scan_kernel(uint32_t* __restrict__ hist, const uint32_t* __restrict__ n_de
     if (t == 255) dtot[blockIdx.x] = total;
 }
 
-template <typename KT> struct DownSmem {
+template <typename KT, int RB> struct DownSmem {
     KT keys[kSortTile];
     uint32_t vals[kSortTile];
-    uint32_t cnt[kSortWarps][kRadix];
-    uint32_t local_start[kRadix];
-    uint32_t glob_off[kRadix];
-    uint32_t scan_a[kRadix];
-    uint32_t scan_b[kRadix];
+    uint32_t cnt[kSortWarps][1 << RB];  // per-warp digit counts, then their start in the tile
+    uint32_t glob_off[1 << RB];
+    uint32_t wsum[2][kSortWarps];
 };
 
-template <typename KT>
-__device__ __forceinline__ void radix_downsweep_tile(DownSmem<KT>& S, const KT* __restrict__ keys_in,
+// Exclusive prefix over the CTA's 256 threads of (a, b); returns the
+// prefixes, and the totals through ta, tb.  s_w: 2 x 8 words of scratch.
+__device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t& pa, uint32_t& pb, uint32_t& ta,
+                                            uint32_t& tb, uint32_t (*s_w)[kSortWarps])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t xa = a, xb = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ya = __shfl_up_sync(0xffffffffu, xa, o);
+        const uint32_t yb = __shfl_up_sync(0xffffffffu, xb, o);
+        if (lane >= o) {
+            xa += ya;
+            xb += yb;
+        }
+    }
+    if (lane == 31) {
+        s_w[0][warp] = xa;
+        s_w[1][warp] = xb;
+    }
+    __syncthreads();
+    uint32_t ba = 0, bb = 0;
+    ta = tb = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        ba += w < warp ? s_w[0][w] : 0u;
+        bb += w < warp ? s_w[1][w] : 0u;
+        ta += s_w[0][w];
+        tb += s_w[1][w];
+    }
+    pa = ba + xa - a;
+    pb = bb + xb - b;
+}
+
+template <typename KT, int RB>
+__device__ __forceinline__ void radix_downsweep_tile(DownSmem<KT, RB>& S, const KT* __restrict__ keys_in,
                                                      const uint32_t* __restrict__ vals_in,
                                                      KT* __restrict__ keys_out,
                                                      uint32_t* __restrict__ vals_out,
@@ -119,6 +156,8 @@ __device__ __forceinline__ void radix_downsweep_tile(DownSmem<KT>& S, const KT* 
                                                      const uint32_t* __restrict__ dtot, uint32_t n,
                                                      int shift, uint32_t dmask, int nb_max, int b)
 {
+    constexpr int kRadix = 1 << RB;
+    constexpr int kDpt = kRadix / kSortThreads;  // digits per thread in the digit scans
     const int64_t base = (int64_t)b * kSortTile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -127,7 +166,7 @@ __device__ __forceinline__ void radix_downsweep_tile(DownSmem<KT>& S, const KT* 
 
     KT k[kSortItems];
     uint32_t val[kSortItems];
-    uint32_t dr[kSortItems];  // digit (bits 24..31) | rank within the warp (bits 0..23)
+    uint32_t dr[kSortItems];  // digit (bits 20..31) | rank within the warp (bits 0..19)
     // all loads in flight before the ranking (its warp barriers would order them)
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
@@ -143,7 +182,7 @@ __device__ __forceinline__ void radix_downsweep_tile(DownSmem<KT>& S, const KT* 
         const uint32_t d = (uint32_t)(k[r] >> shift) & dmask;
         uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
-        for (int bit = 0; bit < 8; ++bit) {
+        for (int bit = 0; bit < RB; ++bit) {
             const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
             peers &= ((d >> bit) & 1u) ? bb : ~bb;
         }
@@ -152,41 +191,46 @@ __device__ __forceinline__ void radix_downsweep_tile(DownSmem<KT>& S, const KT* 
         __syncwarp();
         if (valid && before == (uint32_t)__popc(peers) - 1u) S.cnt[warp][d] = prior + __popc(peers);
         __syncwarp();
-        dr[r] = valid ? ((d << 24) | (prior + before)) : 0xffffffffu;
+        dr[r] = valid ? ((d << 20) | (prior + before)) : 0xffffffffu;
     }
     __syncthreads();
-    // per digit: prefix over warps (in place) and the CTA total
-    const int d = tid;  // kSortThreads == kRadix
-    uint32_t run = 0;
+    // per digit: prefix over the warps (in place) and the CTA total; thread t
+    // owns digits t kDpt .. t kDpt + kDpt - 1
+    uint32_t run[kDpt], gt[kDpt], sa = 0, sb = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t c = S.cnt[w][d];
-        S.cnt[w][d] = run;
-        run += c;
+    for (int q = 0; q < kDpt; ++q) {
+        const int d = tid * kDpt + q;
+        uint32_t r = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = S.cnt[w][d];
+            S.cnt[w][d] = r;
+            r += c;
+        }
+        run[q] = r;
+        gt[q] = dtot[d];
+        sa += r;
+        sb += gt[q];
     }
-    // exclusive scans over digits: CTA-local starts and global digit bases
-    const uint32_t gt = dtot[d];
-    S.scan_a[d] = run;
-    S.scan_b[d] = gt;
-    __syncthreads();
-    for (int o = 1; o < kRadix; o <<= 1) {
-        const uint32_t ya = d >= o ? S.scan_a[d - o] : 0u;
-        const uint32_t yb = d >= o ? S.scan_b[d - o] : 0u;
-        __syncthreads();
-        S.scan_a[d] += ya;
-        S.scan_b[d] += yb;
-        __syncthreads();
+    // exclusive scans over the digits: CTA-local starts and global digit bases
+    uint32_t pa, pb, ta, tb;
+    block_scan2(sa, sb, pa, pb, ta, tb, S.wsum);
+#pragma unroll
+    for (int q = 0; q < kDpt; ++q) {
+        const int d = tid * kDpt + q;
+        // the digit's start in the tile goes into every warp's count
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) S.cnt[w][d] += pa;
+        S.glob_off[d] = pb + hist[(int64_t)d * nb_max + b] - pa;
+        pa += run[q];
+        pb += gt[q];
     }
-    const uint32_t local_start = S.scan_a[d] - run;
-    const uint32_t digit_base = S.scan_b[d] - gt;
-    S.local_start[d] = local_start;
-    S.glob_off[d] = digit_base + hist[(int64_t)d * nb_max + b] - local_start;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         if (dr[r] == 0xffffffffu) continue;
-        const uint32_t dd = dr[r] >> 24;
-        const uint32_t pos = S.local_start[dd] + S.cnt[warp][dd] + (dr[r] & 0xffffffu);
+        const uint32_t dd = dr[r] >> 20;
+        const uint32_t pos = S.cnt[warp][dd] + (dr[r] & 0xfffffu);
         S.keys[pos] = k[r];
         S.vals[pos] = val[r];
     }
@@ -201,7 +245,7 @@ __device__ __forceinline__ void radix_downsweep_tile(DownSmem<KT>& S, const KT* 
     }
 }
 
-template <typename KT>
+template <typename KT, int RB>
 __global__ void __launch_bounds__(kSortThreads)
 radix_downsweep_kernel(const KT* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                        KT* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
@@ -209,7 +253,7 @@ radix_downsweep_kernel(const KT* __restrict__ keys_in, const uint32_t* __restric
                        const uint32_t* __restrict__ n_dev, int shift, uint32_t dmask, int nb_max)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    DownSmem<KT>& S = *reinterpret_cast<DownSmem<KT>*>(smem_raw);
+    DownSmem<KT, RB>& S = *reinterpret_cast<DownSmem<KT, RB>*>(smem_raw);
     const uint32_t n = *n_dev;
     const int nb = (int)((n + kSortTile - 1) / kSortTile);
     for (int b = blockIdx.x; b < nb; b += gridDim.x) {
@@ -258,41 +302,51 @@ cudaError_t launch_set_count(uint32_t* dst, uint32_t value, cudaStream_t st)
     return cudaGetLastError();
 }
 
-size_t sort_hist_bytes(int64_t n_max)
+// Histogram bytes of a sort of up to n_max keys with rb-bit digits: one row
+// of CTA counts per digit, then the digit totals.
+size_t sort_hist_bytes(int64_t n_max, int rb)
 {
     const int64_t nb = (n_max + kSortTile - 1) / kSortTile;
-    return (size_t)(kRadix * (nb > 0 ? nb : 1) + kRadix + 64) * sizeof(uint32_t);
+    const int64_t radix = (int64_t)1 << rb;
+    return (size_t)(radix * (nb > 0 ? nb : 1) + radix + 64) * sizeof(uint32_t);
 }
 
-// Sorts n_dev[0] pairs on bits [0, bits).  Returns 1 when the result is in
-// the *_alt buffers.  hist: sort_hist_bytes(n_max) bytes.  `label` prefixes
-// the per-kernel profiling marks.
-template <typename KT>
+// Passes of a sort of `bits` key bits with digits of rb bits.
+int radix_passes(int bits, int rb) { return (bits + rb - 1) / rb; }
+
+// Sorts n_dev[0] pairs on bits [0, bits) with RB-bit digits.  Returns 1 when
+// the result is in the *_alt buffers.  hist: sort_hist_bytes(n_max) bytes.
+// `labels` name the per-kernel profiling marks.
+template <typename KT, int RB>
 static int radix_sort_t(KT* keys, uint32_t* vals, KT* keys_alt, uint32_t* vals_alt, int64_t n_max,
                         const uint32_t* n_dev, int bits, uint32_t* hist, cudaStream_t st, cudaError_t* err,
                         const char* const labels[3])
 {
-    const int smem = (int)sizeof(DownSmem<KT>);
-    cudaFuncSetAttribute(radix_downsweep_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    constexpr int kRadix = 1 << RB;
+    const int smem = (int)sizeof(DownSmem<KT, RB>);
+    cudaFuncSetAttribute(radix_downsweep_kernel<KT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int nb_max = (int)((n_max + kSortTile - 1) / kSortTile);
-    const int per_sm = sizeof(KT) == 4 ? 3 : 2;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, radix_downsweep_kernel<KT, RB>, kSortThreads,
+                                                      smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
     const int grid = nb_max < resident_grid(per_sm) ? nb_max : resident_grid(per_sm);
     uint32_t* dtot = hist + (int64_t)kRadix * (nb_max > 0 ? nb_max : 1);
-    int passes = (bits + 7) / 8;
+    const int passes = radix_passes(bits, RB);
     KT *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     *err = cudaSuccess;
     if (nb_max == 0) return 0;
     for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        const int dbits = bits - shift < 8 ? bits - shift : 8;  // the last pass may be narrower
+        const int shift = RB * p;
+        const int dbits = bits - shift < RB ? bits - shift : RB;  // the last pass may be narrower
         const uint32_t dmask = (1u << dbits) - 1u;
-        radix_upsweep_kernel<KT><<<grid, kSortThreads, 0, st>>>(ki, n_dev, shift, dmask, nb_max, hist);
+        radix_upsweep_kernel<KT, RB><<<grid, kSortThreads, 0, st>>>(ki, n_dev, shift, dmask, nb_max, hist);
         profile_mark(st, labels[0]);
         radix_scan_kernel<<<kRadix, 256, 0, st>>>(hist, n_dev, nb_max, dtot);
         profile_mark(st, labels[1]);
-        radix_downsweep_kernel<KT><<<grid, kSortThreads, smem, st>>>(ki, vi, ko, vo, hist, dtot, n_dev,
-                                                                     shift, dmask, nb_max);
+        radix_downsweep_kernel<KT, RB><<<grid, kSortThreads, smem, st>>>(ki, vi, ko, vo, hist, dtot, n_dev,
+                                                                         shift, dmask, nb_max);
         profile_mark(st, labels[2]);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -313,17 +367,21 @@ int radix_sort(unsigned long long* keys, uint32_t* vals, unsigned long long* key
                uint32_t* vals_alt, int64_t n_max, const uint32_t* n_dev, int bits,
                uint32_t* hist, cudaStream_t st, cudaError_t* err)
 {
-    return radix_sort_t<unsigned long long>(keys, vals, keys_alt, vals_alt, n_max, n_dev, bits, hist, st,
-                                            err, kSortLabels);
+    return radix_sort_t<unsigned long long, 8>(keys, vals, keys_alt, vals_alt, n_max, n_dev, bits, hist, st,
+                                               err, kSortLabels);
 }
 
-// 32-bit keys: the depth sort (depth = true) and the tile sort of the render path.
+// 32-bit keys: the depth sort (depth = true) and the tile sort of the render
+// path, with digits of rb bits (8 or 11).
 int radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n_max,
-                   const uint32_t* n_dev, int bits, uint32_t* hist, bool depth, cudaStream_t st,
+                   const uint32_t* n_dev, int bits, uint32_t* hist, bool depth, int rb, cudaStream_t st,
                    cudaError_t* err)
 {
-    return radix_sort_t<uint32_t>(keys, vals, keys_alt, vals_alt, n_max, n_dev, bits, hist, st, err,
-                                  depth ? kDepthSortLabels : kSortLabels);
+    const char* const* labels = depth ? kDepthSortLabels : kSortLabels;
+    if (rb == 11)
+        return radix_sort_t<uint32_t, 11>(keys, vals, keys_alt, vals_alt, n_max, n_dev, bits, hist, st, err,
+                                          labels);
+    return radix_sort_t<uint32_t, 8>(keys, vals, keys_alt, vals_alt, n_max, n_dev, bits, hist, st, err, labels);
 }
 
 // 32-bit keys with the caller's profiling labels (the z-order sort).
@@ -331,8 +389,8 @@ int radix_sort_u32_labeled(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, u
                            int64_t n_max, const uint32_t* n_dev, int bits, uint32_t* hist,
                            const char* const labels[3], cudaStream_t st, cudaError_t* err)
 {
-    return radix_sort_t<uint32_t>(keys, vals, keys_alt, vals_alt, n_max, n_dev, bits, hist, st, err,
-                                  labels);
+    return radix_sort_t<uint32_t, 8>(keys, vals, keys_alt, vals_alt, n_max, n_dev, bits, hist, st, err,
+                                     labels);
 }
 
 cudaError_t launch_tile_ranges(const uint32_t* keys, const uint32_t* n_dev, int64_t n_max,

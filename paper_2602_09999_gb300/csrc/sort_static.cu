@@ -28,7 +28,7 @@ int radix_sort(unsigned long long* keys, uint32_t* vals, unsigned long long* key
                uint32_t* vals_alt, int64_t n_max, const uint32_t* n_dev, int bits, uint32_t* hist,
                cudaStream_t st, cudaError_t* err);
 cudaError_t launch_set_count(uint32_t* dst, uint32_t value, cudaStream_t st);
-size_t sort_hist_bytes(int64_t n_max);
+size_t sort_hist_bytes(int64_t n_max, int rb);
 
 namespace {
 
@@ -78,7 +78,7 @@ extern "C" int fgs_sort_pairs_static(uint64_t* keys, uint32_t* vals, int64_t n, 
     if (!keys || !vals) return FGS_ERR_NULL;
     // 8-byte key and 4-byte value accesses
     if ((uintptr_t)keys % 8 != 0 || (uintptr_t)vals % 4 != 0) return FGS_ERR_ALIGN;
-    if (sort_hist_bytes(n) > kHistBytes) return FGS_ERR_TOO_LARGE;
+    if (sort_hist_bytes(n, 8) > kHistBytes) return FGS_ERR_TOO_LARGE;
     unsigned char* base = nullptr;
     const int rc = scratch_on_current_device(&base);
     if (rc != FGS_OK) return rc;

@@ -10,7 +10,8 @@ times the per-pixel backward with each other (pixels, batch) pair of its own
 with that choice fixed (the backward's best pair can differ from the
 forward's: it sums each entry's gradients over the warp once per entry, so
 more pixels per thread spread that cost over more pixels), then the
-forward's other pairs with the backward's fixed, keeps the fastest, and
+forward's other pairs with the backward's fixed, then the radix digit width
+(8 or 11 bits) of the depth sort and of the tile sort, keeps the fastest, and
 caches it in a JSON file keyed by GPU name, Gaussian count and pixel count
 (rounded to powers of two), view count, backward order and storage types,
 so later runs of the same shape skip the search.
@@ -57,16 +58,26 @@ def _store(table):
     os.replace(tmp, CACHE)
 
 
+CHOICE_FIELDS = 7
+
+
 def apply(layout, choice):
     """choice = (pixels per thread, batch[, schedule[, backward pixels per
-    thread, backward batch]]); a backward pair of (0, 0) or none means the
-    forward's pair."""
+    thread, backward batch[, depth-sort digit bits, tile-sort digit
+    bits]]]); a backward pair of (0, 0) or none means the forward's pair,
+    digit bits of 0 or none mean 8.  The layout's sorted_in_alt follows the
+    tile sort's pass count."""
     layout.tuning.blend_pixels_per_thread = int(choice[0])
     layout.tuning.blend_batch = int(choice[1])
     layout.tuning.blend_schedule = int(choice[2]) if len(choice) > 2 else B.FGS_SCHEDULE_QUEUE
     bwd = tuple(choice[3:5]) if len(choice) > 4 else (0, 0)
     layout.tuning.backward_pixels_per_thread = int(bwd[0])
     layout.tuning.backward_batch = int(bwd[1])
+    digits = tuple(choice[5:7]) if len(choice) > 6 else (0, 0)
+    layout.tuning.depth_sort_digit_bits = int(digits[0])
+    layout.tuning.tile_sort_digit_bits = int(digits[1])
+    rb = int(digits[1]) or 8
+    layout.sorted_in_alt = ((int(layout.sort_bits) + rb - 1) // rb) & 1
 
 
 def label(choice) -> str:
@@ -74,6 +85,8 @@ def label(choice) -> str:
     text = f"{choice[0]}x{choice[1]}/{sched}"
     if len(choice) > 4 and choice[3]:
         text += f"+bwd{choice[3]}x{choice[4]}"
+    if len(choice) > 6 and (choice[5] or choice[6]):
+        text += f"+sort{choice[5] or 8}/{choice[6] or 8}"
     return text
 
 
@@ -89,7 +102,7 @@ def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=None):
         (tuple(c) + (B.FGS_SCHEDULE_QUEUE,))[:3] for c in configs]
     key = _key(trainer)
     table = _load() if use_cache else {}
-    if key in table and len(table[key].get("choice", [])) == 5:
+    if key in table and len(table[key].get("choice", [])) == CHOICE_FIELDS:
         choice = tuple(table[key]["choice"])
         apply(trainer.rast.layout, choice)
         return choice, table[key].get("ms", {})
@@ -124,6 +137,13 @@ def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=None):
         for cfg in fwd:
             time_choice(cfg)
         best = min([best] + fwd, key=lambda c: timings[label(c)])
+    # then the radix digit width of each sort, the blend choice fixed
+    best = tuple(best[:5]) + (0, 0)
+    sorts = [tuple(best[:5]) + (d, t) for d in B.SORT_DIGIT_BITS for t in B.SORT_DIGIT_BITS
+             if (d, t) != (8, 8)]
+    for cfg in sorts:
+        time_choice(cfg)
+    best = min([best] + sorts, key=lambda c: timings[label(c)])
     apply(trainer.rast.layout, best)
     if use_cache:
         table[key] = {"choice": list(best), "ms": timings}

@@ -120,13 +120,13 @@ def test_device_flags_and_their_strings(lib):
     binding, each with its own description; anything else is unknown."""
     flags = _header_enum("fgs_device_flags")
     assert flags == {"FGS_FLAG_CAPACITY": B.FGS_FLAG_CAPACITY,
-                     "FGS_FLAG_NONFINITE": B.FGS_FLAG_NONFINITE}
+                     "FGS_FLAG_NONFINITE": B.FGS_FLAG_NONFINITE, "FGS_FLAG_TIMEOUT": B.FGS_FLAG_TIMEOUT}
     bits = list(flags.values())
     assert all(b and (b & (b - 1)) == 0 for b in bits) and len(set(bits)) == len(bits)
     texts = {B.fgs_flag_string(b) for b in bits}
     assert len(texts) == len(bits) and "unknown flag" not in texts
     assert "NaN" in B.fgs_flag_string(B.FGS_FLAG_NONFINITE)
-    for other in (0, 4, B.FGS_FLAG_CAPACITY | B.FGS_FLAG_NONFINITE, 0xffffffff):
+    for other in (0, 8, B.FGS_FLAG_CAPACITY | B.FGS_FLAG_NONFINITE, 0xffffffff):
         assert B.fgs_flag_string(other) == "unknown flag"
     assert _header_enum("fgs_status") == {v: k for k, v in B.STATUS.items()}
 
@@ -280,5 +280,39 @@ def test_tuning_choice_encoding(lib):
     best = (2, 128, 0)
     second = [best + tuple(pb) for pb in B.BLEND_CONFIGS if tuple(pb) != best[:2]]
     third = [tuple(pb) + (0, 4, 64) for pb in B.BLEND_CONFIGS if tuple(pb) != best[:2]]
-    labels = [tune.label(c) for c in first + second + third]
+    sorts = [best + (0, 0, d, t) for d in B.SORT_DIGIT_BITS for t in B.SORT_DIGIT_BITS if (d, t) != (8, 8)]
+    labels = [tune.label(c) for c in first + second + third + sorts]
     assert len(set(labels)) == len(labels)
+
+
+def test_sort_digit_width_choice(lib):
+    """The radix digit widths: 8 or 11 bits (0 means 8) for each sort; the
+    tile sort's width decides where its result ends (sorted_in_alt, the
+    parity of its pass count), which tune.apply keeps in step and every call
+    checks on the host."""
+    from paper_2602_09999_gb300 import tune
+    cam = B.camera_array([scenes.look_at((0, 0, 4), (0, 0, 0), 1237, 822)])
+    layout = B.fgs_workspace_size(1000, cam, 1, 64_000)
+    assert layout.sort_bits == 12 and layout.sorted_in_alt == 0          # 8 + 4 bits: two passes
+    tune.apply(layout, (2, 128, 0, 0, 0, 11, 11))
+    assert (layout.tuning.depth_sort_digit_bits, layout.tuning.tile_sort_digit_bits) == (11, 11)
+    assert layout.sorted_in_alt == 0                                      # 11 + 1 bits: two passes
+    small = B.fgs_workspace_size(1000, B.camera_array([scenes.tiny_camera(100, 70)]), 1, 64_000)
+    assert small.sort_bits == 6 and small.sorted_in_alt == 1              # 35 tiles: one pass
+    tune.apply(small, (2, 128, 0, 0, 0, 8, 11))
+    assert small.sorted_in_alt == 1
+    assert tune.label((2, 128, 0, 0, 0, 11, 0)) == "2x128/queue+sort11/8"
+    fake_ws = ctypes.c_void_p(1 << 20)
+    p = B.params_struct(1000, [1 << 40] * 6, [B.FGS_F32] * 6)
+    for bad in ((9, 8), (8, 16), (-1, 0)):
+        layout.tuning.depth_sort_digit_bits, layout.tuning.tile_sort_digit_bits = bad
+        with pytest.raises(B.FGSError) as e:
+            B.fgs_render_forward(fake_ws, layout, p, 3, cam, 1 << 30, (0, 0, 0), 1 << 31, None)
+        assert e.value.code == -9, bad
+    # a sorted_in_alt out of step with the tile sort's width
+    tune.apply(small, (2, 128, 0, 0, 0, 8, 8))
+    small.sorted_in_alt = 0
+    scam = B.camera_array([scenes.tiny_camera(100, 70)])
+    with pytest.raises(B.FGSError) as e:
+        B.fgs_render_forward(fake_ws, small, p, 3, scam, 1 << 30, (0, 0, 0), 1 << 31, None)
+    assert e.value.code == -4

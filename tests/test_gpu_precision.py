@@ -146,3 +146,48 @@ def test_reduced_storage_adam(oracle_mod, name):
             assert np.all(np.abs(got_s - ref_s) <= _ulp(ref_s, dt) * 1.01), k
         else:
             assert np.all(np.abs(got_s - vo) <= _ulp(vo, dt) * 1.01 + 1e-30), k
+
+
+@pytest.mark.parametrize("name", ["bf16", "fp16"])
+def test_vanishing_second_moment_keeps_parameters_bounded(name):
+    """Gradients of 8e-7: their fp16 sqrt(v) (2.5e-8) rounds to zero while
+    m = 8e-8 still fits.  Where the stored second moment vanishes the stored
+    first moment is zero too, so the 40 steps of zero gradient that follow
+    move no parameter by more than Adam's own bound (|step| <= about 7.3 lr
+    with b1 = 0.9, b2 = 0.999); without that rule they would divide m by
+    eps = 1e-15.  bf16 keeps both moments (its exponent range is float32's)."""
+    dt = DTYPES[name]
+    n = 4096
+    rng = np.random.default_rng(8)
+    shapes = {"means": (n, 3), "log_scales": (n, 3), "quats": (n, 4), "opacity": (n,),
+              "sh_dc": (n, 3), "sh_rest": (n, 15, 3)}
+    tp = {k: torch.from_numpy(rng.uniform(-1, 1, s).astype(np.float32)).cuda()
+          .to(dt if k in ("sh_dc", "sh_rest") else torch.float32) for k, s in shapes.items()}
+    p0 = {k: tp[k].float().clone() for k in GROUPS}
+    sign = {k: np.where(rng.random(s) < 0.5, -1.0, 1.0) for k, s in shapes.items()}
+    tg = {k: torch.from_numpy((8e-7 * sign[k]).astype(np.float32)).cuda() for k in GROUPS}
+    tm = {k: torch.zeros(s, device="cuda", dtype=dt) for k, s in shapes.items()}
+    tv = {k: torch.zeros(s, device="cuda", dtype=dt) for k, s in shapes.items()}
+    lr = T.DEFAULT_LR
+    stream = torch.cuda.current_stream().cuda_stream
+    args = [T.params_struct(tp), T.params_struct(tg), T.params_struct(tm), T.params_struct(tv)]
+    B.fgs_adam_step(*args, lr, 0.9, 0.999, 1e-15, 1, stream)
+    torch.cuda.synchronize()
+    vanished = 0
+    for k in GROUPS:
+        gone = tv[k] == 0
+        vanished += int(gone.sum())
+        assert torch.all(tm[k][gone] == 0), k
+    if dt == torch.float16:
+        assert vanished == sum(int(np.prod(s)) for s in shapes.values())
+    else:
+        assert vanished == 0
+    for k in GROUPS:
+        tg[k].zero_()
+    for step in range(2, 42):
+        B.fgs_adam_step(*args, lr, 0.9, 0.999, 1e-15, step, stream)
+    torch.cuda.synchronize()
+    for i, k in enumerate(GROUPS):
+        moved = (tp[k].float() - p0[k]).abs().max().item()
+        assert torch.isfinite(tp[k].float()).all(), k
+        assert moved <= 41 * 7.3 * lr[i] + 2e-2, (k, moved)

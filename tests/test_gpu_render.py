@@ -497,10 +497,37 @@ def test_autotuner_picks_a_supported_configuration(tmp_path, monkeypatch):
     choice, ms = tune.autotune(tr, reps=1)
     assert tuple(choice[:2]) in B.BLEND_CONFIGS and choice[2] in B.BLEND_SCHEDULES
     assert tuple(choice[3:5]) == (0, 0) or tuple(choice[3:5]) in B.BLEND_CONFIGS
-    # every choice, then the backward's other pairs, then the forward's
-    assert len(ms) == len(B.BLEND_CONFIGS) * len(B.BLEND_SCHEDULES) + 2 * (len(B.BLEND_CONFIGS) - 1)
+    assert tuple(choice[5:7]) == (0, 0) or all(d in B.SORT_DIGIT_BITS for d in choice[5:7])
+    # every choice, then the backward's other pairs, then the forward's, then
+    # the sort digit widths
+    assert len(ms) == (len(B.BLEND_CONFIGS) * len(B.BLEND_SCHEDULES) + 2 * (len(B.BLEND_CONFIGS) - 1)
+                       + len(B.SORT_DIGIT_BITS) ** 2 - 1)
     again, _ = tune.autotune(tr)           # cached
     assert tuple(again) == tuple(choice)
+
+
+@pytest.mark.parametrize("digits", [(11, 8), (8, 11), (11, 11)])
+def test_sort_digit_widths_give_the_same_lists(digits):
+    """The radix digit width of either sort changes speed only: the sorted
+    tile lists, ranges, image and per-pixel state are bit-identical to the
+    8-bit sorts' (the two-view batch has 12 tile-id bits: two passes at
+    either width; a single small view, 6 bits, one)."""
+    from paper_2602_09999_gb300 import tune
+    params = scenes.outdoor_scene(60_000, seed=31)
+    for cams in (scenes.orbit_cameras(2, 640, 480, radius=6.0, seed=32),
+                 [scenes.tiny_camera(100, 70)]):
+        rast, views, t, images = gpu_forward(params, cams)
+        ref = [x.clone() for x in rast.sorted_lists()] + [images.clone()] + [x.clone() for x in rast.per_pixel()]
+        tune.apply(rast.layout, (2, 128, 0, 0, 0) + digits)
+        images2 = torch.zeros_like(images)
+        rast.forward(T.params_struct(t), 3, (0.0, 0.0, 0.0), images2)
+        torch.cuda.synchronize()
+        got = list(rast.sorted_lists()) + [images2] + list(rast.per_pixel())
+        K = min(rast.error()[1], rast.k_max)
+        for a, b, name in zip(ref, got, ("keys", "vals", "ranges", "image", "T", "n_contrib")):
+            if name in ("keys", "vals"):
+                a, b = a[:K], b[:K]
+            assert torch.equal(a, b), (digits, name)
 
 
 def test_unsupported_configuration_is_rejected():
