@@ -1410,9 +1410,11 @@ int orc_loss(int32_t H, int32_t W, const double *img, const double *tgt, double 
                 const double d1 = ux * ux + uy * uy + C1, d2 = vx + vy + C2;
                 const double S = (n1 * n2) / (d1 * d2);
                 rs += S;
-                const double dS_dux = S * (2.0 * uy / n1 - 2.0 * ux / d1);
+                /* the partials of S = n1 n2 / (d1 d2), none divided by n1 or
+                 * n2 (n2 = 2 cov + C2 vanishes where cov = -C2 / 2) */
+                const double dS_dux = 2.0 * uy * n2 / (d1 * d2) - 2.0 * ux * S / d1;
                 const double dS_dvx = -S / d2;
-                const double dS_dcxy = 2.0 * S / n2;
+                const double dS_dcxy = 2.0 * n1 / (d1 * d2);
                 /* vx = exx - ux^2 and cxy = exy - ux uy also depend on ux */
                 D0[p] = dS_dux + dS_dvx * (-2.0 * ux) + dS_dcxy * (-uy);
                 D1[p] = dS_dvx;   /* d/d exx */

@@ -151,10 +151,14 @@ ssim_fwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
             const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
             const float n1 = 2.f * mx * my + C1, n2 = 2.f * cxy + C2;
             const float d1 = mx * mx + my * my + C1, d2 = vx + vy + C2;
-            const float S = (n1 * n2) / (d1 * d2);
-            const float dS_dmx = S * (2.f * my / n1 - 2.f * mx / d1);
+            // S = n1 n2 / (d1 d2) and its partials, none of them divided by n1
+            // or n2: n2 = 2 cov + C2 vanishes where the covariance is -C2 / 2,
+            // and 2 S / n2 would then be 0 / 0
+            const float den = d1 * d2;
+            const float S = (n1 * n2) / den;
+            const float dS_dmx = 2.f * my * n2 / den - 2.f * mx * S / d1;
             const float dS_dvx = -S / d2;
-            const float dS_dcxy = 2.f * S / n2;
+            const float dS_dcxy = 2.f * n1 / den;
             const int64_t gp = vt.pix_off[v] + (int64_t)py * W + px;
             maps[(int64_t)(3 * ch + 0) * ptot + gp] = dS_dmx - 2.f * mx * dS_dvx - my * dS_dcxy;
             maps[(int64_t)(3 * ch + 1) * ptot + gp] = dS_dvx;

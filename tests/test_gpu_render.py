@@ -148,6 +148,34 @@ def test_loss_matches_oracle(sizes, lam):
         assert np.abs(gg - grads[v]).max() <= 2e-5 * scale + 1e-12
 
 
+def test_loss_finite_where_the_covariance_term_vanishes():
+    """Images anticorrelated with their targets, so that the SSIM term
+    2 cov + C2 passes through zero over many windows: the loss and dL/dC
+    stay finite (the SSIM partials are never divided by that term), no
+    flag is set, and both match the oracle."""
+    rng = np.random.default_rng(77)
+    W, H = 640, 480
+    cams = [scenes.look_at((0, 0, 4), (0, 0, 0), W, H)]
+    tgt = rng.uniform(0.0, 0.1, (3, H, W)).astype(np.float32)
+    # cov(x, y) = -k var(y): with var(y) ~ 8.3e-4, k ~ 0.54 puts 2 cov + C2 near 0
+    k = rng.uniform(0.3, 0.8, (3, H, W)).astype(np.float32)
+    img = (0.5 - k * tgt).astype(np.float32)
+    views = T.Views(cams)
+    rast = T.Rasterizer(10, views, 16)
+    im = views.concat([torch.from_numpy(img)]).cuda()
+    tg = views.concat([torch.from_numpy(tgt)]).cuda()
+    loss = torch.zeros(1, device="cuda")
+    dl = torch.zeros_like(im)
+    rast.loss(im, tg, 0.2, loss, dl)
+    torch.cuda.synchronize()
+    assert torch.isfinite(dl).all() and np.isfinite(float(loss.item()))
+    assert rast.error()[0] == 0
+    Lo, go = oracle.loss(img.astype(np.float64), tgt.astype(np.float64), 0.2)
+    assert float(loss.item()) == pytest.approx(Lo, rel=2e-6, abs=1e-7)
+    gg = views.split(dl)[0].cpu().numpy()
+    assert np.abs(gg - go).max() <= 2e-5 * np.abs(go).max() + 1e-12
+
+
 # --------------------------------------------------------------------------
 # backward: gradients through the C ABI vs the oracle's exact adjoint.
 # dL/dC is zeroed, on both sides, on pixels where decisions float32 may take
