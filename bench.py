@@ -249,8 +249,7 @@ def check_flags(rast, where):
     from paper_2602_09999_gb300 import binding as B
     flags, inst = rast.error()
     if flags:
-        names = [B.fgs_flag_string(b) for b in (B.FGS_FLAG_CAPACITY, B.FGS_FLAG_NONFINITE, B.FGS_FLAG_TIMEOUT)
-                 if flags & b]
+        names = [B.fgs_flag_string(b) for b in (B.FGS_FLAG_CAPACITY, B.FGS_FLAG_NONFINITE) if flags & b]
         raise RuntimeError(f"device flags {flags} {where}: {'; '.join(names)} "
                            f"(instances {inst}, k_max {rast.k_max})")
     return inst

@@ -74,13 +74,10 @@ enum fgs_status {
  * (dropped instances, NaN or infinity), and the caller decides. */
 enum fgs_device_flags {
     FGS_FLAG_CAPACITY = 1u,  /* instances exceeded k_max; the extra ones were dropped */
-    FGS_FLAG_NONFINITE = 2u, /* a NaN or infinity reached the loss (a per-view sum or
+    FGS_FLAG_NONFINITE = 2u  /* a NaN or infinity reached the loss (a per-view sum or
                                 dL/dimages, set by fgs_loss_l1_dssim) or an Adam update
                                 (a new parameter or moment, set by the fused
                                 fgs_render_backward_adam) */
-    FGS_FLAG_TIMEOUT = 4u    /* a bounded wait of a kernel on its own asynchronous copies gave
-                                up (the fused fgs_render_backward_adam); the update of some
-                                Gaussians is then incomplete */
 };
 
 enum fgs_dtype { FGS_F32 = 0, FGS_BF16 = 1, FGS_F16 = 2 };

@@ -22,7 +22,6 @@ FGS_NUM_GROUPS = 8
 FGS_F32, FGS_BF16, FGS_F16 = 0, 1, 2
 FGS_FLAG_CAPACITY = 1
 FGS_FLAG_NONFINITE = 2
-FGS_FLAG_TIMEOUT = 4
 
 (FGS_WS_HEADER, FGS_WS_SCREEN, FGS_WS_RECT, FGS_WS_LOCAL_OFF, FGS_WS_BLOCK_SUM, FGS_WS_KEYS,
  FGS_WS_VALS, FGS_WS_KEYS_ALT, FGS_WS_VALS_ALT, FGS_WS_SORT_HIST, FGS_WS_RANGES, FGS_WS_T_FINAL,

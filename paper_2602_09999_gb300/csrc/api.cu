@@ -18,9 +18,6 @@ cudaError_t launch_sorted_duplicate(int64_t n, const ViewTable& vt, const Screen
                                     const TileRect* rects, const uint32_t* svals, uint32_t* sorted_off,
                                     uint32_t* sorted_block, WsHeader* hdr, int64_t k_max, uint32_t* keys,
                                     uint32_t* vals, cudaStream_t st);
-cudaError_t launch_sh_colour(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                             const ViewTable& vt, Screen* screen, const uint32_t* dvals,
-                             const uint32_t* count, cudaStream_t st);
 int64_t count_scan_blocks(int64_t pairs);
 cudaError_t launch_preprocess_bwd(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
                                   const ViewTable& vt, const Screen* screen,
@@ -343,10 +340,6 @@ int fgs_render_forward(void* ws, const fgs_workspace_layout* L, const fgs_params
     if ((rc = cuda_rc(launch_compact_visible(n, vt, screen, rects, local_off, block_sum, hdr, dkeys, dvals,
                                              st))) != FGS_OK)
         return rc;
-    // the colour of the rendered pairs, from the compacted list
-    if ((rc = cuda_rc(launch_sh_colour(n, sh_degree, params, cams_device, vt, screen, dvals, &hdr->counters[1],
-                                       st))) != FGS_OK)
-        return rc;
     cudaError_t e;
     const int dalt = radix_sort_u32(dkeys, dvals, dkeys_alt, dvals_alt, vn, &hdr->counters[1], kDepthBits,
                                     hist, true, digit_bits(L->tuning.depth_sort_digit_bits), st, &e);
@@ -620,7 +613,6 @@ const char* fgs_flag_string(uint32_t flag)
     switch (flag) {
     case FGS_FLAG_CAPACITY: return "instances exceeded the workspace capacity k_max (extra ones dropped)";
     case FGS_FLAG_NONFINITE: return "a NaN or infinity reached the loss or an Adam update";
-    case FGS_FLAG_TIMEOUT: return "a bounded wait on a kernel's own asynchronous copies gave up";
     default: return "unknown flag";
     }
 }

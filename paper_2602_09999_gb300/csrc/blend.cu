@@ -176,101 +176,6 @@ __device__ __forceinline__ void frag_grads(const Entry& e, const Frag& f, float 
     }
 }
 
-// ---------------------------------------------------------------------------
-// Two pixels at once: packed FP32x2 arithmetic (add / sub / mul / fma on a
-// pair of float32 lanes in one 64-bit register, sm_100-class SMs).  Each
-// lane rounds exactly as the scalar instruction does, so a pixel evaluated
-// in a pair takes bit for bit the decisions and values of the scalar path
-// (eval_frag and the forward update above).  The two pixels of a pair are
-// blocks 2p and 2p + 1 of the warp's slots: the same row, 8 columns apart.
-// ---------------------------------------------------------------------------
-typedef unsigned long long f2_t;
-
-__device__ __forceinline__ f2_t f2_pack(float lo, float hi)
-{
-    f2_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float f2_lo(f2_t v)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return lo;
-}
-__device__ __forceinline__ float f2_hi(f2_t v)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return hi;
-}
-__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b)
-{
-    f2_t d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
-{
-    f2_t d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b)
-{
-    f2_t d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
-{
-    f2_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-// A staged entry with every value duplicated into both lanes of a pair, so
-// that five 16-byte shared loads give the operands of the pair arithmetic:
-// mean, the pre-scaled axes (c sqrt(a), s sqrt(a), c sqrt(b), -s sqrt(b): the
-// last negated, so that w' = coef.z dy + (-coef.w) dx is one fused step that
-// rounds as the scalar fma(coef.z, dy, -(coef.w dx))), colour and opacity.
-struct Entry2 {
-    f2_t x, y;     // mean
-    f2_t cx, cy;   // coef.x, coef.y
-    f2_t cz, ncw;  // coef.z, -coef.w
-    f2_t r, g;
-    f2_t b, o;
-};
-
-__device__ __forceinline__ void stage_entry2(const Screen& rec, Entry2& e2)
-{
-    Entry e;
-    stage_entry(rec, e);
-    e2.x = f2_pack(e.xy.x, e.xy.x);
-    e2.y = f2_pack(e.xy.y, e.xy.y);
-    e2.cx = f2_pack(e.coef.x, e.coef.x);
-    e2.cy = f2_pack(e.coef.y, e.coef.y);
-    e2.cz = f2_pack(e.coef.z, e.coef.z);
-    e2.ncw = f2_pack(-e.coef.w, -e.coef.w);
-    e2.r = f2_pack(e.rgbo.x, e.rgbo.x);
-    e2.g = f2_pack(e.rgbo.y, e.rgbo.y);
-    e2.b = f2_pack(e.rgbo.z, e.rgbo.z);
-    e2.o = f2_pack(e.rgbo.w, e.rgbo.w);
-}
-
-// o G of a pixel pair (pixel centres px, py), as eval_frag forms it: returns
-// o G and leaves the scaled axis offsets u', w' and G in the pairs.
-__device__ __forceinline__ f2_t eval_pair(f2_t px, f2_t py, const Entry2& e, f2_t& u, f2_t& w, f2_t& G)
-{
-    const f2_t dx = f2_sub(px, e.x);
-    const f2_t dy = f2_sub(py, e.y);
-    u = f2_fma(e.cx, dx, f2_mul(e.cy, dy));
-    w = f2_fma(e.cz, dy, f2_mul(e.ncw, dx));
-    const f2_t q = f2_fma(u, u, f2_mul(w, w));
-    G = f2_pack(exp2_ftz(-f2_lo(q)), exp2_ftz(-f2_hi(q)));
-    return f2_mul(e.o, G);
-}
-
 // Buffers of the per-Gaussian backward (state == nullptr: not in use).
 struct PgBuffers {
     const uint32_t* bucket_off;  // [total_tiles + 1]
@@ -450,145 +355,6 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
     }
 }
 
-// The same forward with the thread's pixels in pairs (PPT = 2 or 4): one
-// pair evaluation per entry and pair, the 2^x per pixel, and the update
-// T <- T (1 - a), C <- C + a T c with a = alpha where the pixel blends the
-// entry and a = 0 where it does not (which leaves T and C unchanged exactly).
-// Every value and decision equals the scalar version's bit for bit.
-template <int PPT, int BATCH, bool CKPT>
-__device__ __forceinline__ void blend_fwd_tile2(const ViewTable& vt, int64_t n, const uint2* __restrict__ ranges,
-                                                const uint32_t* __restrict__ gids,
-                                                const Screen* __restrict__ screen, float bg0, float bg1,
-                                                float bg2, float* __restrict__ images,
-                                                float* __restrict__ T_final, uint32_t* __restrict__ n_contrib,
-                                                uint32_t* __restrict__ n_blended, const PgBuffers& pg, int tile)
-{
-    using Map = TileMap<PPT>;
-    constexpr int NP = PPT / 2;
-    __shared__ Entry2 s_e[BATCH];
-    __shared__ uint8_t s_mask[BATCH];
-    const Map tm(vt, tile);
-    const int warp = threadIdx.x >> 5;
-    const uint2 range = ranges[tile];
-    const Screen* scr = screen + (int64_t)tm.v * n;
-    const f2_t one = f2_pack(1.0f, 1.0f);
-    f2_t T[NP], C0[NP], C1[NP], C2[NP], px[NP], py[NP];
-    uint32_t last[PPT], blended[PPT];
-    bool done[PPT];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        T[p] = one;
-        C0[p] = C1[p] = C2[p] = f2_pack(0.f, 0.f);
-        px[p] = f2_pack((float)tm.px[2 * p] + 0.5f, (float)tm.px[2 * p + 1] + 0.5f);
-        py[p] = f2_pack((float)tm.py[2 * p] + 0.5f, (float)tm.py[2 * p + 1] + 0.5f);
-    }
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        last[k] = 0;
-        blended[k] = 0;
-        done[k] = !tm.inside[k];
-    }
-    const int64_t bucket0 = CKPT ? (int64_t)pg.bucket_off[tile] : 0;
-    float4* ckpt = CKPT ? pg.state + bucket0 * kTilePixels : nullptr;
-    for (uint32_t start = range.x; start < range.y; start += BATCH) {
-        bool all_done = true;
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) all_done &= done[k];
-        if (__syncthreads_count(all_done) == Map::NT) break;
-        for (int e = threadIdx.x; e < BATCH; e += Map::NT) {
-            const uint32_t j = start + e;
-            if (j < range.y) {
-                const Screen rec = scr[gids[j]];
-                stage_entry2(rec, s_e[e]);
-                s_mask[e] = (uint8_t)block_mask(rec, tm.x0, tm.y0);
-            }
-        }
-        __syncthreads();
-        const int cnt = (int)min((uint32_t)BATCH, range.y - start);
-        for (int jj = 0; jj < cnt && !all_done; ++jj) {
-            if (CKPT && (jj & 31) == 0 && bucket0 + ((start - range.x + jj) >> 5) < pg.max_buckets) {
-                // (T, C) in front of a bucket's first entry (BATCH is a multiple of 32)
-                float4* st = ckpt + (int64_t)((start - range.x + jj) >> 5) * kTilePixels;
-#pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    const int p = k >> 1;
-                    const bool h = k & 1;
-                    if (!done[k])
-                        st[(tm.py[k] - tm.y0) * kTile + (tm.px[k] - tm.x0)] =
-                            make_float4(h ? f2_hi(T[p]) : f2_lo(T[p]), h ? f2_hi(C0[p]) : f2_lo(C0[p]),
-                                        h ? f2_hi(C1[p]) : f2_lo(C1[p]), h ? f2_hi(C2[p]) : f2_lo(C2[p]));
-                }
-            }
-            const uint32_t wm = ((uint32_t)s_mask[jj] >> (warp * PPT)) & ((1u << PPT) - 1u);
-            if (!wm) continue;  // uniform over the warp
-            const Entry2 e = s_e[jj];
-            const uint32_t pos = start + jj - range.x + 1;
-            all_done = true;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const int k0 = 2 * p, k1 = 2 * p + 1;
-                const bool live0 = !done[k0] && ((wm >> k0) & 1u);
-                const bool live1 = !done[k1] && ((wm >> k1) & 1u);
-                if (live0 || live1) {
-                    f2_t u, w, G;
-                    const f2_t oG = eval_pair(px[p], py[p], e, u, w, G);
-                    const float o0 = f2_lo(oG), o1 = f2_hi(oG);
-                    const float a0 = o0 >= kAlphaMax ? kAlphaMax : o0;
-                    const float a1 = o1 >= kAlphaMax ? kAlphaMax : o1;
-                    bool b0 = live0 && a0 >= kAlphaMin, b1 = live1 && a1 >= kAlphaMin;
-                    const f2_t test = f2_mul(T[p], f2_sub(one, f2_pack(a0, a1)));
-                    const float t0 = f2_lo(test), t1 = f2_hi(test);
-                    if (b0 && t0 < kTMin) {
-                        done[k0] = true;
-                        b0 = false;
-                    }
-                    if (b1 && t1 < kTMin) {
-                        done[k1] = true;
-                        b1 = false;
-                    }
-                    if (b0 || b1) {
-                        const f2_t wt = f2_mul(f2_pack(b0 ? a0 : 0.f, b1 ? a1 : 0.f), T[p]);
-                        C0[p] = f2_fma(wt, e.r, C0[p]);
-                        C1[p] = f2_fma(wt, e.g, C1[p]);
-                        C2[p] = f2_fma(wt, e.b, C2[p]);
-                        T[p] = f2_pack(b0 ? t0 : f2_lo(T[p]), b1 ? t1 : f2_hi(T[p]));
-                        if (b0) {
-                            last[k0] = pos;
-                            ++blended[k0];
-                        }
-                        if (b1) {
-                            last[k1] = pos;
-                            ++blended[k1];
-                        }
-                    }
-                }
-                all_done &= done[k0] && done[k1];
-            }
-        }
-    }
-    const int64_t P = (int64_t)tm.W * tm.H;
-    float* img = images + 3 * vt.pix_off[tm.v];
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        if (!tm.inside[k]) continue;
-        const int p = k >> 1;
-        const bool h = k & 1;
-        const float Tk = h ? f2_hi(T[p]) : f2_lo(T[p]);
-        const float c0 = h ? f2_hi(C0[p]) : f2_lo(C0[p]);
-        const float c1 = h ? f2_hi(C1[p]) : f2_lo(C1[p]);
-        const float c2 = h ? f2_hi(C2[p]) : f2_lo(C2[p]);
-        const int64_t pix = (int64_t)tm.py[k] * tm.W + tm.px[k];
-        const float o0 = __fmaf_rn(Tk, bg0, c0), o1 = __fmaf_rn(Tk, bg1, c1), o2 = __fmaf_rn(Tk, bg2, c2);
-        img[pix] = o0;
-        img[P + pix] = o1;
-        img[2 * P + pix] = o2;
-        if (CKPT) pg.pixel_final[vt.pix_off[tm.v] + pix] = make_float4(o0, o1, o2, 0.0f);
-        T_final[vt.pix_off[tm.v] + pix] = Tk;
-        n_contrib[vt.pix_off[tm.v] + pix] = last[k];
-        n_blended[vt.pix_off[tm.v] + pix] = blended[k];
-    }
-}
-
 template <int PPT, int BATCH, bool CKPT>
 __global__ void __launch_bounds__(kTilePixels / PPT)
 blend_fwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
@@ -599,14 +365,9 @@ blend_fwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
 {
     __shared__ uint32_t s_slot;
     int iter = 0;
-    for (int tile; (tile = sched_next(sched, vt.total_tiles, iter, s_slot)) >= 0;) {
-        if constexpr (PPT >= 2)
-            blend_fwd_tile2<PPT, BATCH, CKPT>(vt, n, ranges, gids, screen, bg0, bg1, bg2, images, T_final,
-                                              n_contrib, n_blended, pg, tile);
-        else
-            blend_fwd_tile<PPT, BATCH, CKPT>(vt, n, ranges, gids, screen, bg0, bg1, bg2, images, T_final,
-                                             n_contrib, n_blended, pg, tile);
-    }
+    for (int tile; (tile = sched_next(sched, vt.total_tiles, iter, s_slot)) >= 0;)
+        blend_fwd_tile<PPT, BATCH, CKPT>(vt, n, ranges, gids, screen, bg0, bg1, bg2, images, T_final,
+                                         n_contrib, n_blended, pg, tile);
 }
 
 __device__ __forceinline__ float warp_sum(float x)
@@ -770,173 +531,6 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
     }
 }
 
-// The same backward with the thread's pixels in pairs (PPT = 2 or 4).  A
-// pixel that does not blend the entry takes a = 0, which leaves its T, its
-// g . A and the gradient sums unchanged (T / (1 - 0) = T, additions of 0);
-// the per-pixel decisions are the forward's, bit for bit (eval_pair).  The
-// nine sums of a pair are added lane to lane before the warp reduction.
-template <int PPT, int BATCH>
-__device__ __forceinline__ void blend_bwd_tile2(const ViewTable& vt, int64_t n, const uint2* __restrict__ ranges,
-                                                const uint32_t* __restrict__ gids,
-                                                const Screen* __restrict__ screen, float bg0, float bg1,
-                                                float bg2, const float* __restrict__ dL_dimg,
-                                                const float* __restrict__ T_final,
-                                                const uint32_t* __restrict__ n_contrib,
-                                                ScreenGrad* __restrict__ sgrad, int tile)
-{
-    using Map = TileMap<PPT>;
-    constexpr int NP = PPT / 2;
-    __shared__ Entry2 s_e[BATCH];
-    __shared__ uint8_t s_mask[BATCH];
-    __shared__ uint32_t s_gid[BATCH];
-    __shared__ float s_acc[9][BATCH + 1];
-    __shared__ uint32_t s_max;
-    const Map tm(vt, tile);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint2 range = ranges[tile];
-    const Screen* scr = screen + (int64_t)tm.v * n;
-    ScreenGrad* sg = sgrad + (int64_t)tm.v * n;
-    const int64_t P = (int64_t)tm.W * tm.H;
-    const float* dl = dL_dimg + 3 * vt.pix_off[tm.v];
-    const f2_t one = f2_pack(1.0f, 1.0f), zero = f2_pack(0.f, 0.f);
-    const f2_t k_mu = f2_pack(kTwoLn2, kTwoLn2);
-    const f2_t k_sig = f2_pack(0.5f * kTwoLn2 * kTwoLn2, 0.5f * kTwoLn2 * kTwoLn2);
-
-    // per pair: T, dL/dC = g, S = g . A (A: the colour behind, bg behind the last)
-    f2_t T[NP], g0[NP], g1[NP], g2[NP], S[NP], px[NP], py[NP];
-    uint32_t last[PPT];
-    uint32_t my_max = 0;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        float t[2] = {1.0f, 1.0f}, a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f}, c[2] = {0.f, 0.f}, sv[2] = {0.f, 0.f};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k = 2 * p + h;
-            last[k] = 0;
-            if (tm.inside[k]) {
-                const int64_t pix = (int64_t)tm.py[k] * tm.W + tm.px[k];
-                a[h] = dl[pix];
-                b[h] = dl[P + pix];
-                c[h] = dl[2 * P + pix];
-                sv[h] = a[h] * bg0 + b[h] * bg1 + c[h] * bg2;
-                t[h] = T_final[vt.pix_off[tm.v] + pix];
-                last[k] = n_contrib[vt.pix_off[tm.v] + pix];
-                my_max = max(my_max, last[k]);
-            }
-        }
-        T[p] = f2_pack(t[0], t[1]);
-        g0[p] = f2_pack(a[0], a[1]);
-        g1[p] = f2_pack(b[0], b[1]);
-        g2[p] = f2_pack(c[0], c[1]);
-        S[p] = f2_pack(sv[0], sv[1]);
-        px[p] = f2_pack((float)tm.px[2 * p] + 0.5f, (float)tm.px[2 * p + 1] + 0.5f);
-        py[p] = f2_pack((float)tm.py[2 * p] + 0.5f, (float)tm.py[2 * p + 1] + 0.5f);
-    }
-    const uint32_t warp_max = __reduce_max_sync(0xffffffffu, my_max);
-    if (threadIdx.x == 0) s_max = 0;
-    __syncthreads();
-    if (lane == 0 && warp_max) atomicMax(&s_max, warp_max);
-    __syncthreads();
-    const uint32_t end = range.x + s_max;
-
-    for (uint32_t bend = end; bend > range.x;) {
-        const uint32_t bstart = bend > range.x + BATCH ? bend - BATCH : range.x;
-        const int cnt = (int)(bend - bstart);
-        __syncthreads();
-        for (int e = threadIdx.x; e < BATCH; e += Map::NT) {
-            if (e < cnt) {
-                const uint32_t j = bend - 1 - e;  // slot 0 is the back-most entry
-                const uint32_t g = gids[j];
-                const Screen rec = scr[g];
-                s_gid[e] = g;
-                stage_entry2(rec, s_e[e]);
-                s_mask[e] = (uint8_t)block_mask(rec, tm.x0, tm.y0);
-            }
-#pragma unroll
-            for (int k = 0; k < 9; ++k) s_acc[k][e] = 0.f;
-        }
-        __syncthreads();
-        for (int jj = 0; jj < cnt; ++jj) {
-            const uint32_t pos = bend - jj - range.x;  // 1-based list position
-            const uint32_t wm = ((uint32_t)s_mask[jj] >> (warp * PPT)) & ((1u << PPT) - 1u);
-            if (pos > warp_max || !wm) continue;  // uniform over the warp
-            const Entry2 e = s_e[jj];
-            f2_t d[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) d[k] = zero;
-            bool any = false;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const int k0 = 2 * p, k1 = 2 * p + 1;
-                const bool live0 = ((wm >> k0) & 1u) && pos <= last[k0];
-                const bool live1 = ((wm >> k1) & 1u) && pos <= last[k1];
-                if (!(live0 || live1)) continue;
-                f2_t u, w, G;
-                const f2_t oG = eval_pair(px[p], py[p], e, u, w, G);
-                const float o0 = f2_lo(oG), o1 = f2_hi(oG);
-                const bool c0 = o0 >= kAlphaMax, c1 = o1 >= kAlphaMax;
-                const float a0 = c0 ? kAlphaMax : o0, a1 = c1 ? kAlphaMax : o1;
-                const bool b0 = live0 && a0 >= kAlphaMin, b1 = live1 && a1 >= kAlphaMin;
-                if (!(b0 || b1)) continue;
-                any = true;
-                const float ea0 = b0 ? a0 : 0.f, ea1 = b1 ? a1 : 0.f;
-                const f2_t A = f2_pack(ea0, ea1);
-                // transmittance in front of the entry; 1 - a >= 0.01, so the
-                // approximate reciprocal (2 ulp) is in range
-                const f2_t om = f2_sub(one, A);
-                const f2_t Ti = f2_mul(T[p], f2_pack(__fdividef(1.0f, f2_lo(om)), __fdividef(1.0f, f2_hi(om))));
-                // g . (c - A): dL/dalpha and the update of the colour behind
-                const f2_t gc = f2_sub(f2_fma(g0[p], e.r, f2_fma(g1[p], e.g, f2_mul(g2[p], e.b))), S[p]);
-                const f2_t dalpha = f2_mul(Ti, gc);
-                const f2_t wT = f2_mul(A, Ti);
-                d[6] = f2_fma(wT, g0[p], d[6]);
-                d[7] = f2_fma(wT, g1[p], d[7]);
-                d[8] = f2_fma(wT, g2[p], d[8]);
-                // alpha = o G where the clamp is off: the exponent's terms
-                const bool n0 = b0 && !c0, n1 = b1 && !c1;
-                const f2_t dpow = f2_mul(dalpha, f2_pack(n0 ? a0 : 0.f, n1 ? a1 : 0.f));
-                d[5] = f2_fma(dalpha, f2_pack(n0 ? f2_lo(G) : 0.f, n1 ? f2_hi(G) : 0.f), d[5]);
-                // C d = 2 ln 2 (vx, vy) from the eigen form
-                const f2_t vx = f2_fma(e.cx, u, f2_mul(e.ncw, w));
-                const f2_t vy = f2_fma(e.cy, u, f2_mul(e.cz, w));
-                const f2_t dk = f2_mul(dpow, k_mu);
-                d[0] = f2_fma(dk, vx, d[0]);
-                d[1] = f2_fma(dk, vy, d[1]);
-                const f2_t hs = f2_mul(dpow, k_sig);
-                const f2_t hx = f2_mul(hs, vx), hy = f2_mul(hs, vy);
-                d[2] = f2_fma(hx, vx, d[2]);
-                d[3] = f2_fma(hx, vy, d[3]);
-                d[4] = f2_fma(hy, vy, d[4]);
-                S[p] = f2_fma(A, gc, S[p]);
-                T[p] = Ti;
-            }
-            if (!__any_sync(0xffffffffu, any)) continue;
-            float ds[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) ds[k] = f2_lo(d[k]) + f2_hi(d[k]);
-            // value index of lane l after the scatter: (l >> 2) & 7
-            const float part = warp_sum8_scatter(ds, lane);
-            const float last_v = warp_sum(ds[8]);
-            if ((lane & 3) == 0) atomicAdd(&s_acc[(lane >> 2) & 7][jj], part);
-            if (lane == 1) atomicAdd(&s_acc[8][jj], last_v);
-        }
-        __syncthreads();
-        for (int s = threadIdx.x; s < cnt; s += Map::NT) {
-            const float4 ga = make_float4(s_acc[0][s], s_acc[1][s], s_acc[2][s], s_acc[3][s]);
-            const float4 gb = make_float4(s_acc[4][s], s_acc[5][s], s_acc[6][s], s_acc[7][s]);
-            const float gblue = s_acc[8][s];
-            if (ga.x != 0.f || ga.y != 0.f || ga.z != 0.f || ga.w != 0.f || gb.x != 0.f || gb.y != 0.f ||
-                gb.z != 0.f || gb.w != 0.f || gblue != 0.f) {
-                ScreenGrad* dst = sg + s_gid[s];
-                atomicAdd(&dst->g0, ga);
-                atomicAdd(&dst->g1, gb);
-                atomicAdd(&dst->g2.x, gblue);
-            }
-        }
-        bend = bstart;
-    }
-}
-
 template <int PPT, int BATCH>
 __global__ void __launch_bounds__(kTilePixels / PPT)
 blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
@@ -947,14 +541,9 @@ blend_bwd_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
 {
     __shared__ uint32_t s_slot;
     int iter = 0;
-    for (int tile; (tile = sched_next(sched, vt.total_tiles, iter, s_slot)) >= 0;) {
-        if constexpr (PPT >= 2)
-            blend_bwd_tile2<PPT, BATCH>(vt, n, ranges, gids, screen, bg0, bg1, bg2, dL_dimg, T_final,
-                                        n_contrib, sgrad, tile);
-        else
-            blend_bwd_tile<PPT, BATCH>(vt, n, ranges, gids, screen, bg0, bg1, bg2, dL_dimg, T_final,
-                                       n_contrib, sgrad, tile);
-    }
+    for (int tile; (tile = sched_next(sched, vt.total_tiles, iter, s_slot)) >= 0;)
+        blend_bwd_tile<PPT, BATCH>(vt, n, ranges, gids, screen, bg0, bg1, bg2, dL_dimg, T_final, n_contrib,
+                                   sgrad, tile);
 }
 
 // ---------------------------------------------------------------------------

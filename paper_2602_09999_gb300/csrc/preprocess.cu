@@ -14,7 +14,6 @@
 //                   parameters, summed over the views; writes every
 //                   Gaussian's gradient (zero where invisible).
 #include "adam_math.cuh"
-#include "bulk.cuh"
 
 namespace fgs {
 
@@ -217,6 +216,7 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
             t0 = mo.t0[i];
         }
     }
+    const int ncoef = (sh_degree + 1) * (sh_degree + 1);
     for (int v = 0; v < vt.n_views; ++v) {
         const Cam cam = load_cam(cams, v);
         // the Gaussian at this view's time (static ones: as stored)
@@ -245,11 +245,31 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
             rect.r = make_ushort4((unsigned short)g.tx0, (unsigned short)g.ty0,
                                   (unsigned short)(g.tx0 + g.tw - 1),
                                   (unsigned short)(g.ty0 + g.ntiles / g.tw - 1));
-            // the colour comes from sh_colour_kernel, over the compacted
-            // rendered pairs; here only the visible bit
+            // SH colour from the view direction, streamed from memory
+            float d0 = mv[0] - cam.pos[0], d1 = mv[1] - cam.pos[1], d2 = mv[2] - cam.pos[2];
+            const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            d0 *= il; d1 *= il; d2 *= il;
+            float Y[16];
+            sh_basis(d0, d1, d2, sh_degree, Y);
+            float r0 = 0.5f + Y[0] * to_f32(sh_dc[3 * i]);
+            float r1 = 0.5f + Y[0] * to_f32(sh_dc[3 * i + 1]);
+            float r2 = 0.5f + Y[0] * to_f32(sh_dc[3 * i + 2]);
+            const SHT* rest = sh_rest + 45 * i;
+#pragma unroll
+            for (int kk = 1; kk < 16; ++kk) {
+                if (kk < ncoef) {
+                    r0 += Y[kk] * to_f32(rest[3 * (kk - 1)]);
+                    r1 += Y[kk] * to_f32(rest[3 * (kk - 1) + 1]);
+                    r2 += Y[kk] * to_f32(rest[3 * (kk - 1) + 2]);
+                }
+            }
+            uint32_t bits = 8u;  // visible
+            if (r0 < 0.f) { bits |= 1u; r0 = 0.f; }
+            if (r1 < 0.f) { bits |= 2u; r1 = 0.f; }
+            if (r2 < 0.f) { bits |= 4u; r2 = 0.f; }
             rec.q0 = make_float4(g.mx, g.my, g.e.lb, g.e.ls);
             rec.q1 = make_float4(g.e.c, g.e.s, ov, g.depth);
-            rec.q2 = make_float4(0.f, 0.f, 0.f, __uint_as_float(8u));
+            rec.q2 = make_float4(r0, r1, r2, __uint_as_float(bits));
         }
         const int64_t vi = (int64_t)v * n + i;
         if (valid) {
@@ -355,59 +375,6 @@ compact_visible_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ scree
     const uint32_t pos = local_off[gi] + block_sum[(int64_t)v * nblk + i / kPreBlock];
     dkeys[pos] = __float_as_uint(screen[gi].q1.w);
     dvals[pos] = (uint32_t)gi;
-}
-
-// SH colour of every rendered (view, Gaussian) pair (Sec. 2.1: real SH of
-// degree <= 3 at the view direction, + 0.5, clamped at 0 per channel), one
-// thread per pair of the compacted list the depth sort starts from
-// (dvals[0 .. count), view * n + id in (view, id) order).  Taken out of the
-// preprocess, where only the rendered third of the threads of a warp would
-// run it: here every lane has a pair, and the SH rows are read in increasing
-// address order.  Writes rgb and the clamp bits (0..2) next to the visible
-// bit of the screen record.
-template <typename SHT, bool MOTION>
-__global__ void __launch_bounds__(256)
-sh_colour_kernel(int64_t n, int sh_degree, const float* __restrict__ means, const SHT* __restrict__ sh_dc,
-                 const SHT* __restrict__ sh_rest, const fgs_camera* __restrict__ cams, Motion mo,
-                 Screen* __restrict__ screen, const uint32_t* __restrict__ dvals,
-                 const uint32_t* __restrict__ count)
-{
-    const uint32_t F = *count;
-    const int ncoef = (sh_degree + 1) * (sh_degree + 1);
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < F; q += gridDim.x * blockDim.x) {
-        const uint32_t gi = dvals[q];
-        const int v = (int)(gi / (uint32_t)n);
-        const int64_t i = (int64_t)gi - (int64_t)v * n;
-        const float* cp = cams[v].cam_pos;
-        float mv[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
-        if (MOTION) {
-            const float dt = __ldg(&cams[v].time) - mo.t0[i];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) mv[a] = mv[a] + mo.vel[3 * i + a] * dt;
-        }
-        float d0 = mv[0] - __ldg(cp), d1 = mv[1] - __ldg(cp + 1), d2 = mv[2] - __ldg(cp + 2);
-        const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-        d0 *= il; d1 *= il; d2 *= il;
-        float Y[16];
-        sh_basis(d0, d1, d2, sh_degree, Y);
-        float r0 = 0.5f + Y[0] * to_f32(sh_dc[3 * i]);
-        float r1 = 0.5f + Y[0] * to_f32(sh_dc[3 * i + 1]);
-        float r2 = 0.5f + Y[0] * to_f32(sh_dc[3 * i + 2]);
-        const SHT* rest = sh_rest + 45 * i;
-#pragma unroll
-        for (int kk = 1; kk < 16; ++kk) {
-            if (kk < ncoef) {
-                r0 += Y[kk] * to_f32(rest[3 * (kk - 1)]);
-                r1 += Y[kk] * to_f32(rest[3 * (kk - 1) + 1]);
-                r2 += Y[kk] * to_f32(rest[3 * (kk - 1) + 2]);
-            }
-        }
-        uint32_t bits = 8u;  // visible
-        if (r0 < 0.f) { bits |= 1u; r0 = 0.f; }
-        if (r1 < 0.f) { bits |= 2u; r1 = 0.f; }
-        if (r2 < 0.f) { bits |= 4u; r2 = 0.f; }
-        screen[gi].q2 = make_float4(r0, r1, r2, __uint_as_float(bits));
-    }
 }
 
 // Instance offsets in depth order: exclusive prefix, within each CTA of
@@ -557,8 +524,7 @@ struct AdamArgs {
     void* m[8];
     void* v[8];
     const fgs_adam_state* st;
-    WsHeader* hdr;  // receives FGS_FLAG_NONFINITE and FGS_FLAG_TIMEOUT
-    int staged;     // every p, m, v buffer 16-byte aligned: bulk-staged Adam (below)
+    WsHeader* hdr;  // receives FGS_FLAG_NONFINITE
 };
 
 // True unless all three are finite (v >= 0; a NaN fails the comparison, and
@@ -612,7 +578,7 @@ template <typename T> __device__ __forceinline__ bool aligned_for_pack(const voi
 // elements per access and kAdamPacks packs per thread in flight; a scalar
 // loop takes what is left (the partial last CTA, or unaligned buffers).
 constexpr int kAdamPacks = 2;
-template <typename PT, typename MT>
+template <typename PT, typename MT, int PACKS = kAdamPacks>
 __device__ __forceinline__ void adam_slice(void* p, void* m, void* v, const float* sg, float* g_out,
                                            int64_t base, int64_t cnt, const AdamScalars& a, bool& bad)
 {
@@ -623,13 +589,13 @@ __device__ __forceinline__ void adam_slice(void* p, void* m, void* v, const floa
     const bool vec = aligned_for_pack<PT>(pp) && aligned_for_pack<MT>(mm) && aligned_for_pack<MT>(vv) &&
                      (!go || aligned_for_pack<float>(go));
     const int64_t n4 = vec ? cnt / 4 : 0;
-    for (int64_t q0 = threadIdx.x; q0 < n4; q0 += kAdamPacks * kBwdBlock) {
-        float pv[kAdamPacks][4], mv[kAdamPacks][4], vvv[kAdamPacks][4];
-        int64_t qs[kAdamPacks];
+    for (int64_t q0 = threadIdx.x; q0 < n4; q0 += PACKS * kBwdBlock) {
+        float pv[PACKS][4], mv[PACKS][4], vvv[PACKS][4];
+        int64_t qs[PACKS];
 #pragma unroll
-        for (int u = 0; u < kAdamPacks; ++u) qs[u] = q0 + u * kBwdBlock;
+        for (int u = 0; u < PACKS; ++u) qs[u] = q0 + u * kBwdBlock;
 #pragma unroll
-        for (int u = 0; u < kAdamPacks; ++u) {
+        for (int u = 0; u < PACKS; ++u) {
             if (qs[u] < n4) {
                 Pack4<PT>::load(pp + 4 * qs[u], pv[u]);
                 Pack4<MT>::load(mm + 4 * qs[u], mv[u]);
@@ -637,7 +603,7 @@ __device__ __forceinline__ void adam_slice(void* p, void* m, void* v, const floa
             }
         }
 #pragma unroll
-        for (int u = 0; u < kAdamPacks; ++u) {
+        for (int u = 0; u < PACKS; ++u) {
             if (qs[u] >= n4) continue;
             const float4 g4 = *reinterpret_cast<const float4*>(sg + 4 * qs[u]);
             const float gg[4] = {g4.x, g4.y, g4.z, g4.w};
@@ -669,98 +635,46 @@ __device__ __forceinline__ void adam_slice(void* p, void* m, void* v, const floa
     }
 }
 
-// Bulk-staged Adam of a full CTA (128 Gaussians).  The CTA's slice of each
-// group is contiguous in p, m and v, so the Adam step streams them as chunks
-// of up to kAdamChunk elements through a ring of kAdamStages shared-memory
-// stages, loaded by bulk asynchronous copies (one elected thread per chunk:
-// p, m and v, completion counted on the stage's mbarrier).  The first
-// kAdamStages chunks are issued when the CTA starts, so their loads overlap
-// the gradient pass; each later chunk is issued as soon as its stage has
-// been consumed.  Per chunk, thread t updates elements 4t .. 4t + 3 from
-// shared memory and stores p, m and v with 16- or 8-byte stores.  Chunks
-// never straddle groups: the CTA's slice of a group of width w is w * 128
-// elements, cut into chunks of kAdamChunk and a remainder, every one a
-// multiple of 4 elements and of 16 bytes in any storage type.
-constexpr int kAdamChunk = 512;
-constexpr int kAdamStages = 2;
-constexpr int kRingStage = kAdamChunk * 12;  // p, m, v of a chunk, 4 bytes per element at most
-
-__host__ __device__ constexpr int group_width(int g)
-{
-    return g == 2 ? 4 : (g == 3 || g == 7) ? 1 : g == 5 ? 45 : 3;
-}
-
-// Offsets of the small groups' gradient slices in s_small (sh_rest's are in s_rest).
-__device__ __forceinline__ int small_slice(int g)
-{
-    return g == 0 ? 0 : g == 1 ? 3 * kBwdBlock : g == 2 ? 6 * kBwdBlock : g == 3 ? 10 * kBwdBlock
-         : g == 4 ? 11 * kBwdBlock : g == 6 ? 14 * kBwdBlock : 17 * kBwdBlock;
-}
-
-struct AdamChunk {
-    int g, off, cnt;  // group, first element within the CTA's slice, elements
+// One 4-element pack of one group's Adam slice, split into its loads and its
+// update + stores, so that the packs of several small groups are in flight
+// together (one memory round trip for all of them instead of one per group).
+template <typename PT, typename MT> struct AdamPack {
+    float p[4], m[4], v[4];
+    bool on;
+    __device__ __forceinline__ void load(const void* pp, const void* mm, const void* vv, int64_t e, bool use)
+    {
+        on = use;
+        if (!use) return;
+        Pack4<PT>::load(static_cast<const PT*>(pp) + e, p);
+        Pack4<MT>::load(static_cast<const MT*>(mm) + e, m);
+        Pack4<MT>::load(static_cast<const MT*>(vv) + e, v);
+    }
+    __device__ __forceinline__ void finish(void* pp, void* mm, void* vv, int64_t e, const float* sg, float* g_out,
+                                           const AdamScalars& a, bool& bad)
+    {
+        if (!on) return;
+        const float4 g4 = *reinterpret_cast<const float4*>(sg);
+        const float gg[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float vf = v_decode<MT>(v[j]);
+            p[j] = adam_update(p[j], gg[j], m[j], vf, a);
+            bad |= adam_nonfinite(p[j], m[j], vf);
+            if (v_vanishes<MT>(vf)) m[j] = 0.f;
+            v[j] = v_encode<MT>(vf);
+        }
+        Pack4<PT>::store(static_cast<PT*>(pp) + e, p);
+        Pack4<MT>::store(static_cast<MT*>(mm) + e, m);
+        Pack4<MT>::store(static_cast<MT*>(vv) + e, v);
+        if (g_out) Pack4<float>::store(g_out + e, gg);
+    }
 };
 
-__device__ __forceinline__ AdamChunk adam_chunk(int c, int ngroups)
-{
-    for (int g = 0; g < ngroups; ++g) {
-        const int total = group_width(g) * kBwdBlock;
-        const int nch = (total + kAdamChunk - 1) / kAdamChunk;
-        if (c < nch) return AdamChunk{g, c * kAdamChunk, min(kAdamChunk, total - c * kAdamChunk)};
-        c -= nch;
-    }
-    return AdamChunk{-1, 0, 0};
-}
-
-__host__ __device__ constexpr int adam_chunks(int ngroups)
-{
-    int c = 0;
-    for (int g = 0; g < ngroups; ++g) c += (group_width(g) * kBwdBlock + kAdamChunk - 1) / kAdamChunk;
-    return c;
-}
-
-// Arms the stage's barrier and issues the three copies of chunk ch (one thread).
-template <typename SHT, typename MT>
-__device__ __forceinline__ void adam_issue(const AdamArgs& aa, int64_t i0, const AdamChunk& ch,
-                                           unsigned char* stage, uint64_t* bar)
-{
-    const uint32_t pb = (ch.g == 4 || ch.g == 5) ? (uint32_t)sizeof(SHT) : 4u;
-    const int64_t e0 = (int64_t)group_width(ch.g) * i0 + ch.off;
-    const uint32_t pbytes = (uint32_t)ch.cnt * pb, mbytes = (uint32_t)ch.cnt * (uint32_t)sizeof(MT);
-    bulk_expect(bar, pbytes + 2 * mbytes);
-    bulk_load(stage, static_cast<const unsigned char*>(aa.p[ch.g]) + e0 * pb, pbytes, bar);
-    bulk_load(stage + 4 * kAdamChunk, static_cast<const unsigned char*>(aa.m[ch.g]) + e0 * sizeof(MT), mbytes,
-              bar);
-    bulk_load(stage + 8 * kAdamChunk, static_cast<const unsigned char*>(aa.v[ch.g]) + e0 * sizeof(MT), mbytes,
-              bar);
-}
-
-// Adam on one staged chunk: elements 4t .. 4t + 3 of it for thread t.
 template <typename PT, typename MT>
-__device__ __forceinline__ void adam_consume(void* p, void* m, void* v, const unsigned char* stage,
-                                             const float* sg, float* g_out, int64_t e0, int cnt,
-                                             const AdamScalars& a, bool& bad)
+__device__ __forceinline__ bool group_vectorisable(const AdamArgs& aa, int g, const float* g_out)
 {
-    const int e = 4 * threadIdx.x;
-    if (e >= cnt) return;
-    float pv[4], mv[4], vv[4];
-    Pack4<PT>::load(reinterpret_cast<const PT*>(stage) + e, pv);
-    Pack4<MT>::load(reinterpret_cast<const MT*>(stage + 4 * kAdamChunk) + e, mv);
-    Pack4<MT>::load(reinterpret_cast<const MT*>(stage + 8 * kAdamChunk) + e, vv);
-    const float4 g4 = *reinterpret_cast<const float4*>(sg + e);
-    const float gg[4] = {g4.x, g4.y, g4.z, g4.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        float vf = v_decode<MT>(vv[j]);
-        pv[j] = adam_update(pv[j], gg[j], mv[j], vf, a);
-        bad |= adam_nonfinite(pv[j], mv[j], vf);
-        if (v_vanishes<MT>(vf)) mv[j] = 0.f;
-        vv[j] = v_encode<MT>(vf);
-    }
-    Pack4<PT>::store(static_cast<PT*>(p) + e0 + e, pv);
-    Pack4<MT>::store(static_cast<MT*>(m) + e0 + e, mv);
-    Pack4<MT>::store(static_cast<MT*>(v) + e0 + e, vv);
-    if (g_out) Pack4<float>::store(g_out + e0 + e, gg);
+    return aligned_for_pack<PT>(aa.p[g]) && aligned_for_pack<MT>(aa.m[g]) && aligned_for_pack<MT>(aa.v[g]) &&
+           (!g_out || aligned_for_pack<float>(g_out));
 }
 
 // Gradients of all parameters of 128 Gaussians per CTA, summed over the
@@ -774,7 +688,10 @@ __device__ __forceinline__ void adam_consume(void* p, void* m, void* v, const un
 // SM (104 registers) and 1.19-1.24 ms at 7; at 5 (96 registers, no spill)
 // 0.91 against 0.87 ms in z-order.  The motion variant spills twice as much
 // at 6 and runs best at 5: 0.364 against 0.428 ms on the dynamic workload.
-constexpr int kFusedMinBlocks = 5;
+// A full CTA takes the small groups' Adam in two memory round trips (means,
+// log-scales and quaternions; then opacity and sh_dc) instead of one per
+// group: 0.831 against 0.900 ms.
+constexpr int kFusedMinBlocks = 6;
 constexpr int kFusedMinBlocksMotion = 5;
 
 template <typename SHT, typename MT, bool FUSED, bool MOTION>
@@ -792,25 +709,9 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
     // FUSED: gradients of the small groups, one contiguous slice per group
     constexpr int kSmall = FUSED ? kBwdBlock * 18 : 1;
     __shared__ __align__(16) float s_small[kSmall];
-    // FUSED: the ring of staged Adam chunks and its barriers
-    constexpr int kRing = FUSED ? kAdamStages * kRingStage : 16;
-    __shared__ __align__(128) unsigned char s_ring[kRing];
-    __shared__ uint64_t s_bar[kAdamStages];
     const int64_t i0 = (int64_t)blockIdx.x * kBwdBlock;
     const int64_t i = i0 + threadIdx.x;
     const bool valid = i < n;
-    constexpr int kGroups = MOTION ? 8 : 6;
-    // the partial last CTA, and buffers off a 16-byte boundary, take the
-    // unstaged Adam (adam_slice)
-    const bool staged = FUSED && aa.staged && i0 + kBwdBlock <= n;
-    if (staged && threadIdx.x == 0) {
-#pragma unroll
-        for (int st = 0; st < kAdamStages; ++st) bulk_bar_init(&s_bar[st]);
-        bulk_fence_init();
-#pragma unroll
-        for (int c = 0; c < kAdamStages; ++c)
-            adam_issue<SHT, MT>(aa, i0, adam_chunk(c, kGroups), s_ring + c * kRingStage, &s_bar[c]);
-    }
     float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
     float gw = 0.f;
     float gdc[3] = {0.f, 0.f, 0.f};
@@ -1012,56 +913,49 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
         s_small[10 * kBwdBlock + t] = gw;
         __syncthreads();
         bool bad = false;
-        if (staged) {
-            constexpr int nch = adam_chunks(kGroups);
-            float* g_out_of[8] = {g_means, g_scales, g_quats, g_opac, g_dc, g_rest, g_vel, g_t0};
-            for (int c = 0; c < nch; ++c) {
-                const int st = c % kAdamStages;
-                const AdamChunk ch = adam_chunk(c, kGroups);
-                const bool ok = bulk_wait(&s_bar[st], (uint32_t)(c / kAdamStages) & 1u);
-                if (ok) {
-                    const unsigned char* stage = s_ring + st * kRingStage;
-                    const float* sg = (ch.g == 5 ? s_rest : s_small + small_slice(ch.g)) + ch.off;
-                    const int64_t e0 = (int64_t)group_width(ch.g) * i0 + ch.off;
-                    const AdamScalars sc = resolve(AdamScalars{}, aa.st, ch.g);
-                    if (ch.g == 4 || ch.g == 5)
-                        adam_consume<SHT, MT>(aa.p[ch.g], aa.m[ch.g], aa.v[ch.g], stage, sg, g_out_of[ch.g], e0,
-                                              ch.cnt, sc, bad);
-                    else
-                        adam_consume<float, MT>(aa.p[ch.g], aa.m[ch.g], aa.v[ch.g], stage, sg, g_out_of[ch.g],
-                                                e0, ch.cnt, sc, bad);
-                }
-                if (__syncthreads_or(!ok)) {
-                    // a copy did not complete within the bounded wait: flag it,
-                    // wait (bounded) for this CTA's copies still in flight, leave
-                    if (threadIdx.x == 0) {
-                        set_flag(aa.hdr, FGS_FLAG_TIMEOUT);
-                        for (int k = c; k < nch && k < c + kAdamStages; ++k)
-                            bulk_wait(&s_bar[k % kAdamStages], (uint32_t)(k / kAdamStages) & 1u);
-                    }
-                    __syncthreads();
-                    return;
-                }
-                if (threadIdx.x == 0 && c + kAdamStages < nch) {
-                    bulk_fence_proxy();  // the stage's reads above, before the copy into it
-                    adam_issue<SHT, MT>(aa, i0, adam_chunk(c + kAdamStages, kGroups), s_ring + st * kRingStage,
-                                        &s_bar[st]);
-                }
-            }
-            if (__syncthreads_or(bad) && threadIdx.x == 0) set_flag(aa.hdr, FGS_FLAG_NONFINITE);
-            return;
-        }
         const int64_t nb = min((int64_t)kBwdBlock, n - i0);
-        adam_slice<float, MT>(aa.p[0], aa.m[0], aa.v[0], s_small, g_means, 3 * i0, 3 * nb,
-                              resolve(AdamScalars{}, aa.st, 0), bad);
-        adam_slice<float, MT>(aa.p[1], aa.m[1], aa.v[1], s_small + 3 * kBwdBlock, g_scales, 3 * i0,
-                              3 * nb, resolve(AdamScalars{}, aa.st, 1), bad);
-        adam_slice<float, MT>(aa.p[2], aa.m[2], aa.v[2], s_small + 6 * kBwdBlock, g_quats, 4 * i0,
-                              4 * nb, resolve(AdamScalars{}, aa.st, 2), bad);
-        adam_slice<float, MT>(aa.p[3], aa.m[3], aa.v[3], s_small + 10 * kBwdBlock, g_opac, i0, nb,
-                              resolve(AdamScalars{}, aa.st, 3), bad);
-        adam_slice<SHT, MT>(aa.p[4], aa.m[4], aa.v[4], s_small + 11 * kBwdBlock, g_dc, 3 * i0, 3 * nb,
-                            resolve(AdamScalars{}, aa.st, 4), bad);
+        const bool merged = nb == kBwdBlock && group_vectorisable<float, MT>(aa, 0, g_means) &&
+                      group_vectorisable<float, MT>(aa, 1, g_scales) &&
+                      group_vectorisable<float, MT>(aa, 2, g_quats) &&
+                      group_vectorisable<float, MT>(aa, 3, g_opac) && group_vectorisable<SHT, MT>(aa, 4, g_dc);
+        if (merged) {
+            // a full CTA: the small groups' packs in two memory round trips,
+            // thread t taking pack t of each (means, log-scales and sh_dc have
+            // 96 packs, quaternions 128, opacity 32)
+            {
+                AdamPack<float, MT> a0, a1, a2;
+                a0.load(aa.p[0], aa.m[0], aa.v[0], 3 * i0 + 4 * t, t < 96);
+                a1.load(aa.p[1], aa.m[1], aa.v[1], 3 * i0 + 4 * t, t < 96);
+                a2.load(aa.p[2], aa.m[2], aa.v[2], 4 * i0 + 4 * t, true);
+                a0.finish(aa.p[0], aa.m[0], aa.v[0], 3 * i0 + 4 * t, s_small + 4 * t, g_means,
+                          resolve(AdamScalars{}, aa.st, 0), bad);
+                a1.finish(aa.p[1], aa.m[1], aa.v[1], 3 * i0 + 4 * t, s_small + 3 * kBwdBlock + 4 * t, g_scales,
+                          resolve(AdamScalars{}, aa.st, 1), bad);
+                a2.finish(aa.p[2], aa.m[2], aa.v[2], 4 * i0 + 4 * t, s_small + 6 * kBwdBlock + 4 * t, g_quats,
+                          resolve(AdamScalars{}, aa.st, 2), bad);
+            }
+            {
+                AdamPack<float, MT> b0;
+                AdamPack<SHT, MT> b1;
+                b0.load(aa.p[3], aa.m[3], aa.v[3], i0 + 4 * t, t < 32);
+                b1.load(aa.p[4], aa.m[4], aa.v[4], 3 * i0 + 4 * t, t < 96);
+                b0.finish(aa.p[3], aa.m[3], aa.v[3], i0 + 4 * t, s_small + 10 * kBwdBlock + 4 * t, g_opac,
+                          resolve(AdamScalars{}, aa.st, 3), bad);
+                b1.finish(aa.p[4], aa.m[4], aa.v[4], 3 * i0 + 4 * t, s_small + 11 * kBwdBlock + 4 * t, g_dc,
+                          resolve(AdamScalars{}, aa.st, 4), bad);
+            }
+        } else {
+            adam_slice<float, MT>(aa.p[0], aa.m[0], aa.v[0], s_small, g_means, 3 * i0, 3 * nb,
+                                  resolve(AdamScalars{}, aa.st, 0), bad);
+            adam_slice<float, MT>(aa.p[1], aa.m[1], aa.v[1], s_small + 3 * kBwdBlock, g_scales, 3 * i0,
+                                  3 * nb, resolve(AdamScalars{}, aa.st, 1), bad);
+            adam_slice<float, MT>(aa.p[2], aa.m[2], aa.v[2], s_small + 6 * kBwdBlock, g_quats, 4 * i0,
+                                  4 * nb, resolve(AdamScalars{}, aa.st, 2), bad);
+            adam_slice<float, MT>(aa.p[3], aa.m[3], aa.v[3], s_small + 10 * kBwdBlock, g_opac, i0, nb,
+                                  resolve(AdamScalars{}, aa.st, 3), bad);
+            adam_slice<SHT, MT>(aa.p[4], aa.m[4], aa.v[4], s_small + 11 * kBwdBlock, g_dc, 3 * i0, 3 * nb,
+                                resolve(AdamScalars{}, aa.st, 4), bad);
+        }
         adam_slice<SHT, MT>(aa.p[5], aa.m[5], aa.v[5], s_rest, g_rest, 45 * i0, 45 * nb,
                             resolve(AdamScalars{}, aa.st, 5), bad);
         if (MOTION) {
@@ -1170,42 +1064,6 @@ cudaError_t launch_compact_visible(int64_t n, const ViewTable& vt, const Screen*
     return cudaGetLastError();
 }
 
-template <typename SHT>
-static cudaError_t launch_sh_colour_t(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                                      const ViewTable& vt, Screen* screen, const uint32_t* dvals,
-                                      const uint32_t* count, cudaStream_t st)
-{
-    // a resident grid that strides over the pairs (their number is on the device)
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t most = (int64_t)vt.n_views * n;
-    const int64_t want = (most + 255) / 256;
-    const int grid = (int)(want < (int64_t)sms * 8 ? (want > 0 ? want : 1) : (int64_t)sms * 8);
-    const Motion mo = motion_of(p);
-    auto kernel = mo.vel ? sh_colour_kernel<SHT, true> : sh_colour_kernel<SHT, false>;
-    kernel<<<grid, 256, 0, st>>>(n, deg, (const float*)p->data[0], (const SHT*)p->data[4],
-                                 (const SHT*)p->data[5], cams, mo, screen, dvals, count);
-    profile_mark(st, "sh_colour");
-    return cudaGetLastError();
-}
-
-// SH colour of the rendered pairs compact_visible listed (count: their
-// number, on the device).
-cudaError_t launch_sh_colour(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                             const ViewTable& vt, Screen* screen, const uint32_t* dvals,
-                             const uint32_t* count, cudaStream_t st)
-{
-    switch (p->dtype[4]) {
-    case FGS_BF16:
-        return launch_sh_colour_t<__nv_bfloat16>(n, deg, p, cams, vt, screen, dvals, count, st);
-    case FGS_F16:
-        return launch_sh_colour_t<__half>(n, deg, p, cams, vt, screen, dvals, count, st);
-    default:
-        return launch_sh_colour_t<float>(n, deg, p, cams, vt, screen, dvals, count, st);
-    }
-}
-
 int64_t count_scan_blocks(int64_t pairs) { return (pairs + kCountTile - 1) / kCountTile; }
 
 // After the depth sort (svals: view * n + id in depth order): the instance
@@ -1272,23 +1130,17 @@ static cudaError_t launch_pre_bwd_adam_t(int64_t n, int deg, const fgs_params* p
     const int grid = (int)((n + kBwdBlock - 1) / kBwdBlock);
     AdamArgs aa;
     aa.hdr = hdr;
-    aa.staged = 1;
     for (int k = 0; k < FGS_NUM_GROUPS; ++k) {
         aa.p[k] = p->data[k];
         aa.m[k] = m->data[k];
         aa.v[k] = v->data[k];
     }
     aa.st = ds;
-    for (int k = 0; k < (p->data[6] ? FGS_NUM_GROUPS : 6); ++k)
-        if ((uintptr_t)aa.p[k] % 16 || (uintptr_t)aa.m[k] % 16 || (uintptr_t)aa.v[k] % 16) aa.staged = 0;
     float* gp[FGS_NUM_GROUPS] = {};
     if (g)
         for (int k = 0; k < FGS_NUM_GROUPS; ++k) gp[k] = (float*)g->data[k];
     const Motion mo = motion_of(p);
     auto kernel = mo.vel ? preprocess_bwd_kernel<SHT, MT, true, true> : preprocess_bwd_kernel<SHT, MT, true, false>;
-    // the largest shared-memory carveout, so that the staged CTAs fit at
-    // their register-bound occupancy
-    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     kernel<<<grid, kBwdBlock, 0, st>>>(
         n, deg, (const float*)p->data[0], (const float*)p->data[1], (const float*)p->data[2],
         (const float*)p->data[3], (const SHT*)p->data[4], (const SHT*)p->data[5], cams, vt, screen,
