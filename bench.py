@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--batch", type=int, nargs="+", default=[4, 8],
                     help="views per step of the batched variants")
     ap.add_argument("--no-tune", action="store_true", help="default launch configuration")
+    ap.add_argument("--config", default="",
+                    help="launch choice of the single-view trainer instead of the tuner's: pixels per "
+                         "thread,batch[,schedule[,backward pixels,backward batch[,depth digit,tile digit]]]")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-dynamic", action="store_true",
                     help="skip the dynamic (4D) workload: 600k Gaussians, 6 views per step")
@@ -309,7 +312,12 @@ def run_ours(args, dist):
     stream = torch.cuda.current_stream()
     morton = None if args.no_morton else reorder_once(tr, stream)
     tuned = None
-    if not args.no_tune:
+    if args.config:
+        from paper_2602_09999_gb300 import tune
+        choice = tuple(int(x) for x in args.config.split(","))
+        tune.apply(tr.rast.layout, choice)
+        tuned = (choice, {})
+    elif not args.no_tune:
         from paper_2602_09999_gb300 import tune
         tr.targets.copy_(targets[0])
         tuned = tune.autotune(tr, reps=3)
