@@ -189,22 +189,23 @@ def algorithmic_bytes(label, n, views, instances, pixels, sh_bytes, moment_bytes
     if label == "adam":
         return None  # per group; handled by the caller
     if label == "preprocess_fwd":
-        # geometry of every Gaussian, the 48 SH coefficients of each rendered
-        # pair, and per (view, Gaussian) the screen record, the tile record and
-        # the compaction offset
-        return n * 44 + visible * 48 * sh_bytes + views * n * (48 + 16 + 4)
+        # geometry of every Gaussian, the 48 SH coefficients and the screen
+        # record of each rendered pair, and per (view, Gaussian) the tile record
+        # and the compaction offset
+        return n * 44 + visible * (48 * sh_bytes + 48) + views * n * (16 + 4)
     if label == "preprocess_bwd":
-        # the 45 sh_rest coefficients of each rendered pair (sh_dc's gradient
-        # needs no coefficient), screen and screen-gradient records, and the
+        # the geometry, the kept-tile count of every pair, the screen and
+        # screen-gradient records and the 45 sh_rest coefficients of each
+        # rendered pair (sh_dc's gradient needs no coefficient), and the
         # gradient of every parameter
-        return n * 44 + views * n * 48 * 2 + visible * 45 * sh_bytes + n * 236
+        return n * 44 + views * n * 4 + visible * (48 + 48 + 45 * sh_bytes) + n * 236
     if label == "preprocess_bwd_adam":
-        # visibility words of every (view, Gaussian), the rest of the screen
-        # and screen-gradient records of visible ones, and the Adam step of
-        # every element: parameter, first and second moment read and written
+        # the kept-tile count of every (view, Gaussian), the screen and
+        # screen-gradient records of rendered ones, and the Adam step of every
+        # element: parameter, first and second moment read and written
         widths, p_bytes = (3, 3, 4, 1, 3, 45), (4, 4, 4, 4, sh_bytes, sh_bytes)
         adam = sum(w * (2 * pb + 4 * moment_bytes) for w, pb in zip(widths, p_bytes))
-        return views * n * 16 + visible * views * (32 + 48) + n * adam
+        return views * n * 4 + visible * views * (48 + 48) + n * adam
     if label == "compact_visible":
         return views * n * 16 + visible * 16
     if label == "duplicate":
@@ -399,9 +400,7 @@ def run_ours(args, dist):
         dom = max(phases, key=lambda k: phases[k][0])
         avg_ms = phases[dom][0] / phases[dom][1]
         pixels = W * H
-        scr = tr.rast.screen()[0]
-        bits = scr[:, 11].contiguous().view(torch.int32)
-        visible_est = int(((bits & 8) != 0).sum().item())
+        visible_est = int(tr.rast.rendered()[0].sum().item())
         if dom in BLEND_FLOPS:
             # fragment counts of every camera the timed region visited
             visits = {}

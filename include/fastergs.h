@@ -120,11 +120,13 @@ enum fgs_ws_slot {
     FGS_WS_HEADER = 0,
     FGS_WS_SCREEN,      /* 48-byte records [n_views*n]: float4 (mu2D, conic eigenvalues lb >= ls),
                            float4 (major-axis direction cos, sin, o, depth),
-                           float4 (rgb, bits: clamp mask 0..2, visible 3) */
+                           float4 (rgb, bits: clamp mask 0..2, visible 3); written only for the
+                           pairs the forward renders (FGS_WS_RECT count > 0), the others keep
+                           whatever they held */
     FGS_WS_RECT,        /* 16-byte records [n_views*n]: tile rectangle x0, y0, x1, y1 (uint16,
                            inclusive; x0 > x1 when not rendered), then for rectangles of at most
                            32 tiles the uint32 mask of tiles kept by culling (bit t = row-major
-                           tile t), then an unused uint32 */
+                           tile t), then the uint32 number of kept tiles (0: not rendered) */
     FGS_WS_LOCAL_OFF,   /* uint32 [n_views*n]: CTA-local exclusive prefix of the rendered flags */
     FGS_WS_BLOCK_SUM,   /* uint32 [n_views*ceil(n/128)+1]: prefix of the CTA totals */
     FGS_WS_KEYS,        /* uint32 [k_max]: global tile id of each instance (tile sort keys) */

@@ -20,7 +20,7 @@ cudaError_t launch_sorted_duplicate(int64_t n, const ViewTable& vt, const Screen
                                     uint32_t* vals, cudaStream_t st);
 int64_t count_scan_blocks(int64_t pairs);
 cudaError_t launch_preprocess_bwd(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                                  const ViewTable& vt, const Screen* screen,
+                                  const ViewTable& vt, const Screen* screen, const TileRect* rects,
                                   const ScreenGrad* sgrad, const fgs_params* g, cudaStream_t st);
 size_t sort_hist_bytes(int64_t n_max, int rb);
 int radix_passes(int bits, int rb);
@@ -62,7 +62,8 @@ cudaError_t launch_adam_prepare(fgs_adam_state* ds, cudaStream_t st);
 cudaError_t launch_zero_and_adam_prepare(ScreenGrad* sgrad, const uint32_t* block_sum, const uint32_t* total,
                                          int64_t n, int nv, fgs_adam_state* ds, cudaStream_t st);
 cudaError_t launch_preprocess_bwd_adam(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                                       const ViewTable& vt, const Screen* screen, const ScreenGrad* sgrad,
+                                       const ViewTable& vt, const Screen* screen, const TileRect* rects,
+                                       const ScreenGrad* sgrad,
                                        const fgs_params* g, const fgs_params* m, const fgs_params* v,
                                        const fgs_adam_state* ds, WsHeader* hdr, cudaStream_t st);
 bool fused_adam_supported(int sh_dtype, int moment_dtype);
@@ -451,7 +452,7 @@ int fgs_render_backward(void* ws, const fgs_workspace_layout* L, const fgs_param
     profile_mark(st, "begin");
     if ((rc = backward_blend(ws, L, vt, bg, dl_dimages, nullptr, st)) != FGS_OK) return rc;
     return cuda_rc(launch_preprocess_bwd(L->n, sh_degree, params, cams_device, vt,
-                                         slot<Screen>(ws, L, FGS_WS_SCREEN),
+                                         slot<Screen>(ws, L, FGS_WS_SCREEN), slot<TileRect>(ws, L, FGS_WS_RECT),
                                          slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD), grads, st));
 }
 
@@ -479,7 +480,7 @@ int fgs_render_backward_adam(void* ws, const fgs_workspace_layout* L, const fgs_
     profile_mark(st, "begin");
     if ((rc = backward_blend(ws, L, vt, bg, dl_dimages, state_device, st)) != FGS_OK) return rc;
     return cuda_rc(launch_preprocess_bwd_adam(L->n, sh_degree, params, cams_device, vt,
-                                              slot<Screen>(ws, L, FGS_WS_SCREEN),
+                                              slot<Screen>(ws, L, FGS_WS_SCREEN), slot<TileRect>(ws, L, FGS_WS_RECT),
                                               slot<ScreenGrad>(ws, L, FGS_WS_SCREEN_GRAD), grads, exp_avg,
                                               exp_avg_sq, state_device, slot<WsHeader>(ws, L, FGS_WS_HEADER),
                                               st));

@@ -273,7 +273,9 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
         }
         const int64_t vi = (int64_t)v * n + i;
         if (valid) {
-            screen[vi] = rec;
+            // the screen record only where the pair is rendered: every reader
+            // takes the rendered flag from the tile record's count
+            if (count > 0) screen[vi] = rec;
             rects[vi] = rect;
         }
         // compaction offsets of the rendered (view, Gaussian) pairs
@@ -699,7 +701,8 @@ __global__ void __launch_bounds__(kBwdBlock, FUSED ? (MOTION ? kFusedMinBlocksMo
 preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float* log_scales,
                       const float* quats, const float* opac, const SHT* sh_dc, const SHT* sh_rest,
                       const fgs_camera* __restrict__ cams, ViewTable vt,
-                      const Screen* __restrict__ screen, const ScreenGrad* __restrict__ sgrad,
+                      const Screen* __restrict__ screen, const TileRect* __restrict__ rects,
+                      const ScreenGrad* __restrict__ sgrad,
                       float* __restrict__ g_means, float* __restrict__ g_scales,
                       float* __restrict__ g_quats, float* __restrict__ g_opac,
                       float* __restrict__ g_dc, float* __restrict__ g_rest, float* __restrict__ g_vel,
@@ -719,7 +722,7 @@ preprocess_bwd_kernel(int64_t n, int sh_degree, const float* means, const float*
     uint32_t vis_mask = 0;
     if (valid)
         for (int v = 0; v < vt.n_views; ++v)
-            if (__float_as_uint(screen[(int64_t)v * n + i].q2.w) & 8u) vis_mask |= 1u << v;
+            if (rects[(int64_t)v * n + i].count > 0) vis_mask |= 1u << v;
     float mu[3] = {0.f, 0.f, 0.f};
     const int ncoef = (sh_degree + 1) * (sh_degree + 1);
     // this Gaussian's sh_rest gradient row in shared memory (stride 45 floats:
@@ -1090,7 +1093,7 @@ cudaError_t launch_sorted_duplicate(int64_t n, const ViewTable& vt, const Screen
 
 template <typename SHT>
 static cudaError_t launch_pre_bwd_t(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                                    const ViewTable& vt, const Screen* screen,
+                                    const ViewTable& vt, const Screen* screen, const TileRect* rects,
                                     const ScreenGrad* sgrad, const fgs_params* g, cudaStream_t st)
 {
     const int grid = (int)((n + kBwdBlock - 1) / kBwdBlock);
@@ -1100,7 +1103,7 @@ static cudaError_t launch_pre_bwd_t(int64_t n, int deg, const fgs_params* p, con
     kernel<<<grid, kBwdBlock, 0, st>>>(
         n, deg, (const float*)p->data[0], (const float*)p->data[1], (const float*)p->data[2],
         (const float*)p->data[3], (const SHT*)p->data[4], (const SHT*)p->data[5], cams, vt, screen,
-        sgrad, (float*)g->data[0], (float*)g->data[1], (float*)g->data[2], (float*)g->data[3],
+        rects, sgrad, (float*)g->data[0], (float*)g->data[1], (float*)g->data[2], (float*)g->data[3],
         (float*)g->data[4], (float*)g->data[5], (float*)g->data[6], (float*)g->data[7], mo,
         AdamArgs{});
     profile_mark(st, "preprocess_bwd");
@@ -1108,22 +1111,23 @@ static cudaError_t launch_pre_bwd_t(int64_t n, int deg, const fgs_params* p, con
 }
 
 cudaError_t launch_preprocess_bwd(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                                  const ViewTable& vt, const Screen* screen,
+                                  const ViewTable& vt, const Screen* screen, const TileRect* rects,
                                   const ScreenGrad* sgrad, const fgs_params* g, cudaStream_t st)
 {
     switch (p->dtype[4]) {
     case FGS_BF16:
-        return launch_pre_bwd_t<__nv_bfloat16>(n, deg, p, cams, vt, screen, sgrad, g, st);
+        return launch_pre_bwd_t<__nv_bfloat16>(n, deg, p, cams, vt, screen, rects, sgrad, g, st);
     case FGS_F16:
-        return launch_pre_bwd_t<__half>(n, deg, p, cams, vt, screen, sgrad, g, st);
+        return launch_pre_bwd_t<__half>(n, deg, p, cams, vt, screen, rects, sgrad, g, st);
     default:
-        return launch_pre_bwd_t<float>(n, deg, p, cams, vt, screen, sgrad, g, st);
+        return launch_pre_bwd_t<float>(n, deg, p, cams, vt, screen, rects, sgrad, g, st);
     }
 }
 
 template <typename SHT, typename MT>
 static cudaError_t launch_pre_bwd_adam_t(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                                         const ViewTable& vt, const Screen* screen, const ScreenGrad* sgrad,
+                                         const ViewTable& vt, const Screen* screen, const TileRect* rects,
+                                         const ScreenGrad* sgrad,
                                          const fgs_params* g, const fgs_params* m, const fgs_params* v,
                                          const fgs_adam_state* ds, WsHeader* hdr, cudaStream_t st)
 {
@@ -1144,7 +1148,7 @@ static cudaError_t launch_pre_bwd_adam_t(int64_t n, int deg, const fgs_params* p
     kernel<<<grid, kBwdBlock, 0, st>>>(
         n, deg, (const float*)p->data[0], (const float*)p->data[1], (const float*)p->data[2],
         (const float*)p->data[3], (const SHT*)p->data[4], (const SHT*)p->data[5], cams, vt, screen,
-        sgrad, gp[0], gp[1], gp[2], gp[3], gp[4], gp[5], gp[6], gp[7], mo, aa);
+        rects, sgrad, gp[0], gp[1], gp[2], gp[3], gp[4], gp[5], gp[6], gp[7], mo, aa);
     profile_mark(st, "preprocess_bwd_adam");
     return cudaGetLastError();
 }
@@ -1154,12 +1158,13 @@ static cudaError_t launch_pre_bwd_adam_t(int64_t n, int deg, const fgs_params* p
 // SH type.  Returns cudaErrorInvalidValue for any other pair (the caller
 // checks first).
 cudaError_t launch_preprocess_bwd_adam(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
-                                       const ViewTable& vt, const Screen* screen, const ScreenGrad* sgrad,
+                                       const ViewTable& vt, const Screen* screen, const TileRect* rects,
+                                       const ScreenGrad* sgrad,
                                        const fgs_params* g, const fgs_params* m, const fgs_params* v,
                                        const fgs_adam_state* ds, WsHeader* hdr, cudaStream_t st)
 {
     const int sht = p->dtype[4], mt = m->dtype[0];
-#define FGS_PB(S, M) launch_pre_bwd_adam_t<S, M>(n, deg, p, cams, vt, screen, sgrad, g, m, v, ds, hdr, st)
+#define FGS_PB(S, M) launch_pre_bwd_adam_t<S, M>(n, deg, p, cams, vt, screen, rects, sgrad, g, m, v, ds, hdr, st)
     if (sht == FGS_F32 && mt == FGS_F32) return FGS_PB(float, float);
     if (sht == FGS_BF16 && mt == FGS_F32) return FGS_PB(__nv_bfloat16, float);
     if (sht == FGS_BF16 && mt == FGS_BF16) return FGS_PB(__nv_bfloat16, __nv_bfloat16);

@@ -163,7 +163,12 @@ class Rasterizer:
         return keys, vals, ranges
 
     def screen(self):
+        """Screen records [views, n, 12]; valid where rendered() is true."""
         return self.slot(B.FGS_WS_SCREEN, torch.float32).view(self.views.n, self.n, 12)
+
+    def rendered(self):
+        """[views, n] bool: the pairs the last forward rendered (kept tiles > 0)."""
+        return self.slot(B.FGS_WS_RECT, torch.int32).view(self.views.n, self.n, 4)[:, :, 3] > 0
 
     def per_pixel(self):
         return (self.slot(B.FGS_WS_T_FINAL, torch.float32),

@@ -46,10 +46,12 @@ def case(request, oracle_mod):
 
 def test_screen_state_matches_oracle(case):
     scr = case["rast"].screen().cpu().numpy()
+    rendered = case["rast"].rendered().cpu().numpy()
     for v, pre in enumerate(case["pres"]):
         s = scr[v]
         bits = s[:, 11].view(np.uint32)
-        gvis = (bits & 8) != 0
+        gvis = rendered[v]
+        assert np.all((bits[gvis] & 8) != 0)
         keep_any = np.zeros(pre["xy"].shape[0], bool)
         li = case["lists"][v]
         keep_any[li["gid"][(li["flags"] & oracle.KEEP) != 0]] = True
