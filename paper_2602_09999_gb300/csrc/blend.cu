@@ -635,17 +635,12 @@ blend_bwd_pg_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
             e.coef = make_float4(0.f, 0.f, 0.f, 0.f);
             e.rgbo = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        // the tile's pixels still blending in front of this bucket, in the
-        // 8x4 blocks some entry of the bucket reaches (elsewhere every
-        // entry's alpha is below 1/255: nothing to replay)
-        const uint32_t reach = __reduce_or_sync(full, bmask);
+        // the tile's pixels still blending in front of this bucket
         int na = 0;
         for (int c = 0; c < kTilePixels / 32; ++c) {
             const int p = 32 * c + lane;
-            const int lx = p & (kTile - 1), ly = p >> 4;
-            const int px = x0 + lx, py = y0 + ly;
-            const bool act = ((reach >> ((lx >> 3) | ((ly >> 2) << 1))) & 1u) && px < W && py < H &&
-                             n_contrib[poff + (int64_t)py * W + px] > first;
+            const int px = x0 + (p & (kTile - 1)), py = y0 + (p >> 4);
+            const bool act = px < W && py < H && n_contrib[poff + (int64_t)py * W + px] > first;
             const uint32_t bal = __ballot_sync(full, act);
             if (act) s_list[warp][na + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)p;
             na += __popc(bal);
