@@ -13,13 +13,14 @@
 // accumulates is dL/dSigma2D directly, dpow (C d)(C d)^T / 2 per fragment,
 // instead of dL/dconic followed by -C G C: for needle-like splats the conic
 // gradient is large and C G C cancels by orders of magnitude in float32,
-// while C d is well conditioned.  The CTA walks the same list back to front
+// while C d is well conditioned.  It sums these in the conic's eigen basis
+// (frag_moments) and rotates the sums once per entry.  The CTA walks the same list back to front
 // from the largest last-contributor position of its pixels; each pixel
 // recovers T_i = T_{i+1} / (1 - alpha_i) and the colour behind it,
 // A_i = alpha_{i+1} c_{i+1} + (1 - alpha_{i+1}) A_{i+1} (A = bg behind the
 // last), so dC/dalpha_i = T_i (c_i - A_i) and dC/dc_i = alpha_i T_i; only
 // the scalar g . A_i is kept, g = dL/dC of the pixel.  The 9
-// per-fragment gradients are summed over the warp with shuffles, over the
+// per-fragment sums are summed over the warp with shuffles, over the
 // CTA with shared-memory atomics, and leave the CTA as one set of global
 // vector atomics per (instance, CTA).
 //
@@ -44,14 +45,18 @@ constexpr float kLog2e = 1.4426950408889634f;
 // 2 ln 2: converts the exp2-scaled axis coordinates back to C d (below).
 constexpr float kTwoLn2 = 1.3862943611198906f;
 
-// One list entry staged in shared memory: mean, the conic's eigen form as
-// its two axes pre-scaled for exp2, colour and opacity.  With a = ls log2(e)
-// / 2, b = lb log2(e) / 2 and the major axis (c, s), coef = (c sqrt(a),
+// One list entry staged in shared memory for one tile: the conic's eigen
+// form as its two axes pre-scaled for exp2, the scaled axis coordinates at
+// the tile's first pixel centre, colour and opacity.  With a = ls log2(e) /
+// 2, b = lb log2(e) / 2 and the major axis (c, s), coef = (c sqrt(a),
 // s sqrt(a), c sqrt(b), s sqrt(b)), so that with u' = coef.x dx + coef.y dy
 // and w' = coef.z dy - coef.w dx the exponent of Eq. 3 in base 2 is
-// -(u'^2 + w'^2) = -(log2 e / 2) d^T conic d, never positive.
+// -(u'^2 + w'^2) = -(log2 e / 2) d^T conic d, never positive.  Both
+// coordinates are affine in the pixel position, so a pixel at (lx, ly)
+// within the tile has u' = uw0.x + coef.x lx + coef.y ly (and likewise
+// w'), which pixels of one row share in part (eval_frag).
 struct Entry {
-    float2 xy;
+    float2 uw0;
     float4 coef;
     float4 rgbo;  // r, g, b, o
 };
@@ -67,6 +72,7 @@ template <int PPT> struct TileMap {
     static_assert(NW * PPT == 8, "eight blocks per tile");
     int v, W, H, x0, y0;
     int px[PPT], py[PPT];
+    float lx[PPT], ly[PPT];  // pixel position within the tile, as floats
     bool inside[PPT];
     __device__ __forceinline__ TileMap(const ViewTable& vt, int tile)
     {
@@ -79,9 +85,14 @@ template <int PPT> struct TileMap {
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            const int b = w * PPT + k;
-            px[k] = x0 + 8 * (b & 1) + (lane & 7);
-            py[k] = y0 + 4 * (b >> 1) + (lane >> 3);
+            // block w PPT + k; slots k and k ^ 1 share the block row when PPT >= 2
+            const int bcol = PPT >= 2 ? (k & 1) : (w & 1);
+            const int brow = PPT >= 2 ? w * (PPT / 2) + (k >> 1) : (w >> 1);
+            const int cx = 8 * bcol + (lane & 7), cy = 4 * brow + (lane >> 3);
+            px[k] = x0 + cx;
+            py[k] = y0 + cy;
+            lx[k] = (float)cx;
+            ly[k] = (float)cy;
             inside[k] = px[k] < W && py[k] < H;
         }
     }
@@ -111,12 +122,15 @@ __device__ __forceinline__ uint32_t block_mask(const Screen& rec, int x0, int y0
     return m;
 }
 
-__device__ __forceinline__ void stage_entry(const Screen& rec, Entry& e)
+__device__ __forceinline__ void stage_entry(const Screen& rec, int x0, int y0, Entry& e)
 {
     const float sa = sqrtf(0.5f * kLog2e * rec.q0.w), sb = sqrtf(0.5f * kLog2e * rec.q0.z);
     const float c = rec.q1.x, sn = rec.q1.y;
-    e.xy = make_float2(rec.q0.x, rec.q0.y);
     e.coef = make_float4(c * sa, sn * sa, c * sb, sn * sb);
+    const float dx0 = __fsub_rn((float)x0 + 0.5f, rec.q0.x);
+    const float dy0 = __fsub_rn((float)y0 + 0.5f, rec.q0.y);
+    e.uw0 = make_float2(__fmaf_rn(e.coef.x, dx0, __fmul_rn(e.coef.y, dy0)),
+                        __fmaf_rn(e.coef.z, dy0, -__fmul_rn(e.coef.w, dx0)));
     e.rgbo = make_float4(rec.q2.x, rec.q2.y, rec.q2.z, rec.q1.z);
 }
 
@@ -129,18 +143,18 @@ __device__ __forceinline__ float exp2_ftz(float x)
     return y;
 }
 
-// Alpha of one fragment (Eq. 3 with the 3DGS rules), shared by the forward
-// and the backward so both take the same decisions: skip alpha < 1/255;
-// alpha = min(0.99, o G).  The exponent is a negated sum of squares, so the
-// positive-exponent case cannot arise.  Also returns the scaled offsets u'
-// (along the major axis) and w' (across it) for the backward.
-__device__ __forceinline__ bool eval_frag(float px, float py, const Entry& e, Frag& f, float& u,
-                                          float& w)
+// Alpha of one fragment (Eq. 3 with the 3DGS rules) at the pixel (lx, ly)
+// of the entry's tile, shared by the forward and both backwards so all take
+// the same decisions: skip alpha < 1/255; alpha = min(0.99, o G).  The
+// coordinates are evaluated in one fixed order of roundings, the row term
+// first, so every launch configuration computes them bit for bit alike.  The
+// exponent is a negated sum of squares, so the positive-exponent case cannot
+// arise.  Also returns the scaled offsets u' (along the major axis) and w'
+// (across it) for the backward.
+__device__ __forceinline__ bool eval_frag(float lx, float ly, const Entry& e, Frag& f, float& u, float& w)
 {
-    f.dx = __fsub_rn(px, e.xy.x);
-    f.dy = __fsub_rn(py, e.xy.y);
-    u = __fmaf_rn(e.coef.x, f.dx, __fmul_rn(e.coef.y, f.dy));
-    w = __fmaf_rn(e.coef.z, f.dy, -__fmul_rn(e.coef.w, f.dx));
+    u = __fmaf_rn(e.coef.x, lx, __fmaf_rn(e.coef.y, ly, e.uw0.x));
+    w = __fmaf_rn(-e.coef.w, lx, __fmaf_rn(e.coef.z, ly, e.uw0.y));
     const float l2 = -__fmaf_rn(u, u, __fmul_rn(w, w));
     f.G = exp2_ftz(l2);
     const float oG = __fmul_rn(e.rgbo.w, f.G);
@@ -149,31 +163,59 @@ __device__ __forceinline__ bool eval_frag(float px, float py, const Entry& e, Fr
     return f.alpha >= kAlphaMin;
 }
 
-// Adds the screen-space gradients of one blended fragment to d[9]: dL/dmu2D
-// (2), dL/dSigma2D (H00, H01, H11 of the full symmetric gradient), dL/do and
-// dL/drgb, given dL/dalpha, wT = alpha T and the pixel's dL/dC.
-__device__ __forceinline__ void frag_grads(const Entry& e, const Frag& f, float u, float w, float dalpha,
-                                           float wT, float g0, float g1, float g2, float d[9])
+// Adds one blended fragment to the nine sums m[9] from which the entry's
+// screen-space gradients follow (entry_grads below), given dL/dalpha, wT =
+// alpha T and the pixel's dL/dC = g.  With q = dL/dalpha G (zero where alpha
+// is clamped, since it then does not depend on the Gaussian's geometry or
+// opacity) the sums are q u, q w, q u^2, q u w, q w^2, q and wT g: the
+// gradients of the mean and of Sigma2D are linear in the first five, with
+// coefficients that depend on the entry alone, so the per-fragment work is
+// these eight products instead of forming C d and (C d)(C d)^T per fragment.
+// u and w are the exp2-scaled axis coordinates of eval_frag; the sums stay
+// in the conic's eigen basis, where C d is a positive diagonal scaling, and
+// are rotated back once per entry.
+__device__ __forceinline__ void frag_moments(const Frag& f, float u, float w, float dalpha, float wT,
+                                             float g0, float g1, float g2, float m[9])
 {
-    d[6] += wT * g0;
-    d[7] += wT * g1;
-    d[8] += wT * g2;
-    if (!f.clamped) {
-        // power = -q/2 with q = d^T C d; C d = ls u e + lb w e_perp from
-        // the eigen form (no cancellation) = 2 ln 2 (vx, vy) below
-        const float dpow = dalpha * f.alpha;  // alpha = o G here
-        const float vx = e.coef.x * u - e.coef.w * w;
-        const float vy = e.coef.y * u + e.coef.z * w;
-        d[5] += dalpha * f.G;
-        const float dk = dpow * kTwoLn2;
-        d[0] += dk * vx;  // dL/dmu = dpow C d
-        d[1] += dk * vy;
-        // dL/dSigma (full symmetric) = -C (dL/dC) C = dpow (C d)(C d)^T / 2
-        const float hx = dpow * (0.5f * kTwoLn2 * kTwoLn2) * vx;
-        d[2] += hx * vx;
-        d[3] += hx * vy;
-        d[4] += dpow * (0.5f * kTwoLn2 * kTwoLn2) * vy * vy;
-    }
+    m[6] = __fmaf_rn(wT, g0, m[6]);
+    m[7] = __fmaf_rn(wT, g1, m[7]);
+    m[8] = __fmaf_rn(wT, g2, m[8]);
+    const float q = f.clamped ? 0.0f : dalpha * f.G;
+    m[5] += q;
+    m[0] = __fmaf_rn(q, u, m[0]);
+    m[1] = __fmaf_rn(q, w, m[1]);
+    const float qu = q * u;
+    m[2] = __fmaf_rn(qu, u, m[2]);
+    m[3] = __fmaf_rn(qu, w, m[3]);
+    m[4] = __fmaf_rn(q, __fmul_rn(w, w), m[4]);
+}
+
+// The entry's screen-space gradients from its sums m[9] over the pixels
+// (frag_moments): dL/dmu2D, dL/dSigma2D (H00, H01, H11 of the full symmetric
+// gradient), dL/do and dL/drgb.  Per fragment the exponent's derivative is
+// dpow = dL/dalpha alpha = o q (power = -d^T C d / 2), and with the eigen
+// form C d = 2 ln 2 (vx, vy), vx = cx u - cw w, vy = cy u + cz w (coef =
+// (cx, cy, cz, cw)):
+//   dL/dmu    = sum dpow C d                  = 2 ln 2 o (cx S_u - cw S_w, cy S_u + cz S_w)
+//   dL/dSigma = sum dpow (C d)(C d)^T / 2     = 2 (ln 2)^2 o sum q (vx, vy)(vx, vy)^T
+// expanded in S_uu, S_uw, S_ww.  The dense C G C product of the conic
+// gradient, which cancels for needle-like splats in float32, never forms.
+__device__ __forceinline__ void entry_grads(const Entry& e, const float m[9], float4& ga, float4& gb,
+                                            float& gblue)
+{
+    const float o = e.rgbo.w;
+    const float cx = e.coef.x, cy = e.coef.y, cz = e.coef.z, cw = e.coef.w;
+    const float k1 = kTwoLn2 * o;
+    const float k2 = (0.5f * kTwoLn2 * kTwoLn2) * o;
+    ga.x = k1 * (cx * m[0] - cw * m[1]);
+    ga.y = k1 * (cy * m[0] + cz * m[1]);
+    ga.z = k2 * (cx * cx * m[2] - 2.0f * cx * cw * m[3] + cw * cw * m[4]);
+    ga.w = k2 * (cx * cy * m[2] + (cx * cz - cw * cy) * m[3] - cw * cz * m[4]);
+    gb.x = k2 * (cy * cy * m[2] + 2.0f * cy * cz * m[3] + cz * cz * m[4]);
+    gb.y = m[5];
+    gb.z = m[6];
+    gb.w = m[7];
+    gblue = m[8];
 }
 
 // Buffers of the per-Gaussian backward (state == nullptr: not in use).
@@ -293,7 +335,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
             const uint32_t j = start + e;
             if (j < range.y) {
                 const Screen rec = scr[gids[j]];
-                stage_entry(rec, s_e[e]);
+                stage_entry(rec, tm.x0, tm.y0, s_e[e]);
                 s_mask[e] = (uint8_t)block_mask(rec, tm.x0, tm.y0);
             }
         }
@@ -318,7 +360,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
                 Frag f;
                 float u, w;
                 if (((wm >> k) & 1u) &&
-                    eval_frag((float)tm.px[k] + 0.5f, (float)tm.py[k] + 0.5f, e, f, u, w)) {
+                    eval_frag(tm.lx[k], tm.ly[k], e, f, u, w)) {
                     const float test = __fmul_rn(T[k], __fsub_rn(1.0f, f.alpha));
                     if (test < kTMin) {
                         done[k] = true;
@@ -470,7 +512,7 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
                 const uint32_t g = gids[j];
                 const Screen rec = scr[g];
                 s_gid[e] = g;
-                stage_entry(rec, s_e[e]);
+                stage_entry(rec, tm.x0, tm.y0, s_e[e]);
                 s_mask[e] = (uint8_t)block_mask(rec, tm.x0, tm.y0);
             }
 #pragma unroll
@@ -491,7 +533,7 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
                 Frag f;
                 float u, w;
                 if (!(((wm >> k) & 1u) && pos <= last[k] &&
-                      eval_frag((float)tm.px[k] + 0.5f, (float)tm.py[k] + 0.5f, e, f, u, w)))
+                      eval_frag(tm.lx[k], tm.ly[k], e, f, u, w)))
                     continue;
                 any = true;
                 // transmittance in front of the entry; 1 - alpha >= 0.01, so the
@@ -501,7 +543,7 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
                 // behind, A <- A + alpha (c - A)
                 const float gc = g0[k] * e.rgbo.x + g1[k] * e.rgbo.y + g2[k] * e.rgbo.z - S[k];
                 const float dalpha = Ti * gc;
-                frag_grads(e, f, u, w, dalpha, f.alpha * Ti, g0[k], g1[k], g2[k], d);
+                frag_moments(f, u, w, dalpha, f.alpha * Ti, g0[k], g1[k], g2[k], d);
                 S[k] += f.alpha * gc;
                 T[k] = Ti;
             }
@@ -514,13 +556,14 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
         }
         __syncthreads();
         for (int s = threadIdx.x; s < cnt; s += Map::NT) {
-            // dL/dmu2D, dL/dSigma2D (H00, H01, H11 of the full symmetric
-            // gradient), dL/do and dL/drgb of this entry over the CTA
-            const float4 ga = make_float4(s_acc[0][s], s_acc[1][s], s_acc[2][s], s_acc[3][s]);
-            const float4 gb = make_float4(s_acc[4][s], s_acc[5][s], s_acc[6][s], s_acc[7][s]);
-            const float gblue = s_acc[8][s];
-            if (ga.x != 0.f || ga.y != 0.f || ga.z != 0.f || ga.w != 0.f || gb.x != 0.f || gb.y != 0.f ||
-                gb.z != 0.f || gb.w != 0.f || gblue != 0.f) {
+            float m[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) m[k] = s_acc[k][s];
+            if (m[0] != 0.f || m[1] != 0.f || m[2] != 0.f || m[3] != 0.f || m[4] != 0.f || m[5] != 0.f ||
+                m[6] != 0.f || m[7] != 0.f || m[8] != 0.f) {
+                float4 ga, gb;
+                float gblue;
+                entry_grads(s_e[s], m, ga, gb, gblue);
                 ScreenGrad* dst = sg + s_gid[s];
                 atomicAdd(&dst->g0, ga);
                 atomicAdd(&dst->g1, gb);
@@ -600,7 +643,7 @@ struct PgStage {
     uint32_t p[kBucket];
 };
 
-__global__ void __launch_bounds__(kPgWarps * 32)
+__global__ void __launch_bounds__(kPgWarps * 32, 4)
 blend_bwd_pg_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
                     const uint32_t* __restrict__ gids, const Screen* __restrict__ screen,
                     const float* __restrict__ dL_dimg, const uint32_t* __restrict__ n_contrib,
@@ -628,10 +671,10 @@ blend_bwd_pg_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
         if (has) {
             gid = gids[j];
             const Screen rec = screen[(int64_t)v * n + gid];
-            stage_entry(rec, e);
+            stage_entry(rec, x0, y0, e);
             bmask = block_mask(rec, x0, y0);
         } else {
-            e.xy = make_float2(0.f, 0.f);
+            e.uw0 = make_float2(0.f, 0.f);
             e.coef = make_float4(0.f, 0.f, 0.f, 0.f);
             e.rgbo = make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -696,7 +739,7 @@ blend_bwd_pg_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
             Frag f;
             float u, w;
             if (has && pos <= sg.last[k] && ((bmask >> ((lx >> 3) | ((ly >> 2) << 1))) & 1u) &&
-                eval_frag((float)(x0 + lx) + 0.5f, (float)(y0 + ly) + 0.5f, e, f, u, w)) {
+                eval_frag((float)lx, (float)ly, e, f, u, w)) {
                 // the forward's update, rounding for rounding
                 const float Tn = __fmul_rn(T, __fsub_rn(1.0f, f.alpha));
                 const float wT = __fmul_rn(f.alpha, T);
@@ -710,7 +753,7 @@ blend_bwd_pg_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
                 const float c1 = e.rgbo.y - (sg.o1[k] - C1) * iT;
                 const float c2 = e.rgbo.z - (sg.o2[k] - C2) * iT;
                 const float dalpha = T * (g0 * c0 + g1 * c1 + g2 * c2);
-                frag_grads(e, f, u, w, dalpha, wT, g0, g1, g2, d);
+                frag_moments(f, u, w, dalpha, wT, g0, g1, g2, d);
                 T = Tn;
             }
             To = T;
@@ -720,10 +763,13 @@ blend_bwd_pg_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
         }
         if (has && (d[0] != 0.f || d[1] != 0.f || d[2] != 0.f || d[3] != 0.f || d[4] != 0.f || d[5] != 0.f ||
                     d[6] != 0.f || d[7] != 0.f || d[8] != 0.f)) {
+            float4 ga, gb;
+            float gblue;
+            entry_grads(e, d, ga, gb, gblue);
             ScreenGrad* dst = sgrad + (int64_t)v * n + gid;
-            atomicAdd(&dst->g0, make_float4(d[0], d[1], d[2], d[3]));
-            atomicAdd(&dst->g1, make_float4(d[4], d[5], d[6], d[7]));
-            atomicAdd(&dst->g2.x, d[8]);
+            atomicAdd(&dst->g0, ga);
+            atomicAdd(&dst->g1, gb);
+            atomicAdd(&dst->g2.x, gblue);
         }
         __syncwarp();  // s_list and the stages are reused by the next bucket
     }
