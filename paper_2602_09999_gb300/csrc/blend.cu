@@ -55,11 +55,23 @@ constexpr float kTwoLn2 = 1.3862943611198906f;
 // coordinates are affine in the pixel position, so a pixel at (lx, ly)
 // within the tile has u' = uw0.x + coef.x lx + coef.y ly (and likewise
 // w'), which pixels of one row share in part (eval_frag).
+// The first 16 bytes also carry the entry's block mask (block_mask), so a
+// warp reads the mask and the coordinates in one load and skips the rest of
+// the entry when the mask misses its blocks.
 struct Entry {
     float2 uw0;
+    uint32_t mask, pad;
     float4 coef;
     float4 rgbo;  // r, g, b, o
 };
+
+// uw0 and the mask of a staged entry in one 16-byte shared-memory load.
+__device__ __forceinline__ uint32_t load_head(const Entry& s, float2& uw0)
+{
+    const float4 h = *reinterpret_cast<const float4*>(&s);
+    uw0 = make_float2(h.x, h.y);
+    return __float_as_uint(h.z);
+}
 
 // Thread -> pixel map with PPT pixels per thread: the CTA covers one 16x16
 // tile, split into 8 blocks of 8 columns x 4 rows (block b: columns
@@ -132,6 +144,8 @@ __device__ __forceinline__ void stage_entry(const Screen& rec, int x0, int y0, E
     e.uw0 = make_float2(__fmaf_rn(e.coef.x, dx0, __fmul_rn(e.coef.y, dy0)),
                         __fmaf_rn(e.coef.z, dy0, -__fmul_rn(e.coef.w, dx0)));
     e.rgbo = make_float4(rec.q2.x, rec.q2.y, rec.q2.z, rec.q1.z);
+    e.mask = block_mask(rec, x0, y0);
+    e.pad = 0;
 }
 
 // 2^x for x <= 0 on the special-function unit; results below 2^-126 flush to
@@ -159,8 +173,8 @@ __device__ __forceinline__ bool eval_frag(float lx, float ly, const Entry& e, Fr
     f.G = exp2_ftz(l2);
     const float oG = __fmul_rn(e.rgbo.w, f.G);
     f.clamped = oG >= kAlphaMax;
-    f.alpha = f.clamped ? kAlphaMax : oG;
-    return f.alpha >= kAlphaMin;
+    f.alpha = fminf(oG, kAlphaMax);
+    return oG >= kAlphaMin;  // false for a NaN oG, like the test on alpha
 }
 
 // Adds one blended fragment to the nine sums m[9] from which the entry's
@@ -308,7 +322,6 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
 {
     using Map = TileMap<PPT>;
     __shared__ Entry s_e[BATCH];
-    __shared__ uint8_t s_mask[BATCH];
     const Map tm(vt, tile);
     const int warp = threadIdx.x >> 5;
     const uint2 range = ranges[tile];
@@ -336,7 +349,6 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
             if (j < range.y) {
                 const Screen rec = scr[gids[j]];
                 stage_entry(rec, tm.x0, tm.y0, s_e[e]);
-                s_mask[e] = (uint8_t)block_mask(rec, tm.x0, tm.y0);
             }
         }
         __syncthreads();
@@ -350,17 +362,18 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
                     if (!done[k])
                         st[(tm.py[k] - tm.y0) * kTile + (tm.px[k] - tm.x0)] = make_float4(T[k], C0[k], C1[k], C2[k]);
             }
-            const uint32_t wm = ((uint32_t)s_mask[jj] >> (warp * PPT)) & ((1u << PPT) - 1u);
+            Entry e;
+            const uint32_t wm = (load_head(s_e[jj], e.uw0) >> (warp * PPT)) & ((1u << PPT) - 1u);
             if (!wm) continue;  // uniform over the warp
-            const Entry e = s_e[jj];
-            all_done = true;
+            e.coef = s_e[jj].coef;
+            e.rgbo = s_e[jj].rgbo;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (done[k]) continue;
+                // a stopped pixel evaluates along with the warp's others but
+                // takes no decision (no branch of its own)
                 Frag f;
                 float u, w;
-                if (((wm >> k) & 1u) &&
-                    eval_frag(tm.lx[k], tm.ly[k], e, f, u, w)) {
+                if (((wm >> k) & 1u) && eval_frag(tm.lx[k], tm.ly[k], e, f, u, w) && !done[k]) {
                     const float test = __fmul_rn(T[k], __fsub_rn(1.0f, f.alpha));
                     if (test < kTMin) {
                         done[k] = true;
@@ -375,8 +388,10 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
                     last[k] = start + jj - range.x + 1;
                     ++blended[k];
                 }
-                all_done = false;
             }
+            all_done = true;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) all_done &= done[k];
         }
     }
     const int64_t P = (int64_t)tm.W * tm.H;
@@ -458,7 +473,6 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
 {
     using Map = TileMap<PPT>;
     __shared__ Entry s_e[BATCH];
-    __shared__ uint8_t s_mask[BATCH];
     __shared__ uint32_t s_gid[BATCH];
     // one row per value; the row padding puts the 9 values of one entry in
     // 9 different banks for the scattered shared atomics below
@@ -513,7 +527,6 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
                 const Screen rec = scr[g];
                 s_gid[e] = g;
                 stage_entry(rec, tm.x0, tm.y0, s_e[e]);
-                s_mask[e] = (uint8_t)block_mask(rec, tm.x0, tm.y0);
             }
 #pragma unroll
             for (int k = 0; k < 9; ++k) s_acc[k][e] = 0.f;
@@ -521,9 +534,11 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
         __syncthreads();
         for (int jj = 0; jj < cnt; ++jj) {
             const uint32_t pos = bend - jj - range.x;  // 1-based list position
-            const uint32_t wm = ((uint32_t)s_mask[jj] >> (warp * PPT)) & ((1u << PPT) - 1u);
+            Entry e;
+            const uint32_t wm = (load_head(s_e[jj], e.uw0) >> (warp * PPT)) & ((1u << PPT) - 1u);
             if (pos > warp_max || !wm) continue;  // uniform over the warp
-            const Entry e = s_e[jj];
+            e.coef = s_e[jj].coef;
+            e.rgbo = s_e[jj].rgbo;
             float d[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) d[k] = 0.f;
@@ -672,7 +687,7 @@ blend_bwd_pg_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
             gid = gids[j];
             const Screen rec = screen[(int64_t)v * n + gid];
             stage_entry(rec, x0, y0, e);
-            bmask = block_mask(rec, x0, y0);
+            bmask = e.mask;
         } else {
             e.uw0 = make_float2(0.f, 0.f);
             e.coef = make_float4(0.f, 0.f, 0.f, 0.f);

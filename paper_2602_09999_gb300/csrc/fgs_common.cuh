@@ -183,45 +183,51 @@ __device__ __forceinline__ float eigen_q(const EigenConic& e, float dx, float dy
 // of the quadratic form over the box of the tile's pixel centres (offsets
 // from the mean); keep the tile iff it is <= k.  The minimum of a convex
 // quadratic over a box is 0 when the mean is inside, else it lies on an edge,
-// where the 1D minimiser (from the conic entries) is clamped to the edge.
-__device__ __forceinline__ bool tile_keep(float mx, float my, const EigenConic& e, float k, int tx,
-                                          int ty, int width, int height)
+// where the 1D minimiser is clamped to the edge.  With the conic entries
+// a = ls c^2 + lb s^2, b = (ls - lb) s c, cc = ls s^2 + lb c^2, the minimiser
+// on the edge x = X lies at y = ry X (ry = -b / cc) and on the edge y = Y at
+// x = rx Y (rx = -b / a); these slopes are per Gaussian (make_cull), so the
+// per-tile test is multiplications, clamps and four evaluations of the form.
+struct TileCull {
+    float mx, my, k, rx, ry;
+    EigenConic e;
+};
+
+__device__ __forceinline__ TileCull make_cull(float mx, float my, const EigenConic& e, float k)
+{
+    TileCull c;
+    c.mx = mx;
+    c.my = my;
+    c.k = k;
+    c.e = e;
+    const float a = __fmaf_rn(e.ls, __fmul_rn(e.c, e.c), __fmul_rn(e.lb, __fmul_rn(e.s, e.s)));
+    const float b = __fmul_rn(__fsub_rn(e.ls, e.lb), __fmul_rn(e.s, e.c));
+    const float cc = __fmaf_rn(e.ls, __fmul_rn(e.s, e.s), __fmul_rn(e.lb, __fmul_rn(e.c, e.c)));
+    c.ry = __fdiv_rn(-b, cc);
+    c.rx = __fdiv_rn(-b, a);
+    return c;
+}
+
+__device__ __forceinline__ bool tile_keep(const TileCull& c, int tx, int ty, int width, int height)
 {
     const float x_lo = __fadd_rn((float)(tx * kTile), 0.5f);
     const float x_hi = fminf(__fadd_rn((float)(tx * kTile + kTile - 1), 0.5f), __fadd_rn((float)width, -0.5f));
     const float y_lo = __fadd_rn((float)(ty * kTile), 0.5f);
     const float y_hi = fminf(__fadd_rn((float)(ty * kTile + kTile - 1), 0.5f), __fadd_rn((float)height, -0.5f));
-    const float x0 = __fsub_rn(x_lo, mx), x1 = __fsub_rn(x_hi, mx);
-    const float y0 = __fsub_rn(y_lo, my), y1 = __fsub_rn(y_hi, my);
+    const float x0 = __fsub_rn(x_lo, c.mx), x1 = __fsub_rn(x_hi, c.mx);
+    const float y0 = __fsub_rn(y_lo, c.my), y1 = __fsub_rn(y_hi, c.my);
     if (x0 <= 0.0f && 0.0f <= x1 && y0 <= 0.0f && 0.0f <= y1) return true;
-    // conic entries for the 1D minimisers: a = ls c^2 + lb s^2, b = (ls - lb) s c, cc = ls s^2 + lb c^2
-    const float a = __fmaf_rn(e.ls, __fmul_rn(e.c, e.c), __fmul_rn(e.lb, __fmul_rn(e.s, e.s)));
-    const float b = __fmul_rn(__fsub_rn(e.ls, e.lb), __fmul_rn(e.s, e.c));
-    const float cc = __fmaf_rn(e.ls, __fmul_rn(e.s, e.s), __fmul_rn(e.lb, __fmul_rn(e.c, e.c)));
-    float best = INFINITY;
-    {
-        float X = x0;
-        float Y = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, X), cc), y0), y1);
-        best = fminf(best, eigen_q(e, X, Y));
-        X = x1;
-        Y = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, X), cc), y0), y1);
-        best = fminf(best, eigen_q(e, X, Y));
-    }
-    {
-        float Y = y0;
-        float X = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, Y), a), x0), x1);
-        best = fminf(best, eigen_q(e, X, Y));
-        Y = y1;
-        X = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, Y), a), x0), x1);
-        best = fminf(best, eigen_q(e, X, Y));
-    }
-    return best <= k;
+    float best = eigen_q(c.e, x0, fminf(fmaxf(__fmul_rn(c.ry, x0), y0), y1));
+    best = fminf(best, eigen_q(c.e, x1, fminf(fmaxf(__fmul_rn(c.ry, x1), y0), y1)));
+    best = fminf(best, eigen_q(c.e, fminf(fmaxf(__fmul_rn(c.rx, y0), x0), x1), y0));
+    best = fminf(best, eigen_q(c.e, fminf(fmaxf(__fmul_rn(c.rx, y1), x0), x1), y1));
+    return best <= c.k;
 }
 
 // One evaluated fragment: alpha = min(0.99, o G), G = exp(power), the
 // offset from the mean and whether the clamp is active.
 struct Frag {
-    float alpha, G, dx, dy;
+    float alpha, G;
     bool clamped;
 };
 
@@ -268,6 +274,36 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, int degree, 
     Y[15] = -SHC::c3a * x * (xx - 3.0f * yy);
 }
 
+// sh_basis with every rounding explicit (see quat_to_rot_rn).
+__device__ __forceinline__ void sh_basis_rn(float x, float y, float z, int degree, float Y[16])
+{
+    Y[0] = SHC::c0;
+#pragma unroll
+    for (int k = 1; k < 16; ++k) Y[k] = 0.0f;
+    if (degree < 1) return;
+    Y[1] = __fmul_rn(-SHC::c1, y);
+    Y[2] = __fmul_rn(SHC::c1, z);
+    Y[3] = __fmul_rn(-SHC::c1, x);
+    if (degree < 2) return;
+    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    const float xmy = __fsub_rn(xx, yy);                                     // x^2 - y^2
+    const float r2 = __fsub_rn(__fsub_rn(__fmul_rn(2.0f, zz), xx), yy);      // 2 z^2 - x^2 - y^2
+    const float r4 = __fsub_rn(__fsub_rn(__fmul_rn(4.0f, zz), xx), yy);      // 4 z^2 - x^2 - y^2
+    Y[4] = __fmul_rn(__fmul_rn(SHC::c2a, x), y);
+    Y[5] = __fmul_rn(__fmul_rn(-SHC::c2a, y), z);
+    Y[6] = __fmul_rn(SHC::c2b, r2);
+    Y[7] = __fmul_rn(__fmul_rn(-SHC::c2a, x), z);
+    Y[8] = __fmul_rn(SHC::c2c, xmy);
+    if (degree < 3) return;
+    Y[9] = __fmul_rn(__fmul_rn(-SHC::c3a, y), __fmaf_rn(3.0f, xx, -yy));
+    Y[10] = __fmul_rn(__fmul_rn(__fmul_rn(SHC::c3b, x), y), z);
+    Y[11] = __fmul_rn(__fmul_rn(-SHC::c3c, y), r4);
+    Y[12] = __fmul_rn(__fmul_rn(SHC::c3d, z), __fmaf_rn(-3.0f, yy, __fmaf_rn(-3.0f, xx, __fmul_rn(2.0f, zz))));
+    Y[13] = __fmul_rn(__fmul_rn(-SHC::c3c, x), r4);
+    Y[14] = __fmul_rn(__fmul_rn(SHC::c3e, z), xmy);
+    Y[15] = __fmul_rn(__fmul_rn(-SHC::c3a, x), __fmaf_rn(-3.0f, yy, xx));
+}
+
 // d/d(x, y, z) of sum_k coef[k] Y_k for the polynomial forms above.
 __device__ __forceinline__ void sh_dir_grad(float x, float y, float z, int degree,
                                             const float coef[16], float g[3])
@@ -310,6 +346,24 @@ __device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, 
     R[6] = 2.0f * (x * z - w * y);
     R[7] = 2.0f * (y * z + w * x);
     R[8] = 1.0f - 2.0f * (x * x + y * y);
+}
+
+// The same rotation with every rounding explicit.  The forward preprocess
+// uses the _rn forms (this, sh_basis_rn, and explicit roundings in its
+// projection and colour), so its static and motion instantiations, inlined
+// into different kernels, compute the same screen state bit for bit whatever
+// the compiler contracts around them.  The backward keeps the plain forms.
+__device__ __forceinline__ void quat_to_rot_rn(float w, float x, float y, float z, float R[9])
+{
+    R[0] = __fmaf_rn(-2.0f, __fmaf_rn(y, y, __fmul_rn(z, z)), 1.0f);
+    R[1] = __fmul_rn(2.0f, __fmaf_rn(x, y, -__fmul_rn(w, z)));
+    R[2] = __fmul_rn(2.0f, __fmaf_rn(x, z, __fmul_rn(w, y)));
+    R[3] = __fmul_rn(2.0f, __fmaf_rn(x, y, __fmul_rn(w, z)));
+    R[4] = __fmaf_rn(-2.0f, __fmaf_rn(x, x, __fmul_rn(z, z)), 1.0f);
+    R[5] = __fmul_rn(2.0f, __fmaf_rn(y, z, -__fmul_rn(w, x)));
+    R[6] = __fmul_rn(2.0f, __fmaf_rn(x, z, -__fmul_rn(w, y)));
+    R[7] = __fmul_rn(2.0f, __fmaf_rn(y, z, __fmul_rn(w, x)));
+    R[8] = __fmaf_rn(-2.0f, __fmaf_rn(x, x, __fmul_rn(y, y)), 1.0f);
 }
 
 __device__ __forceinline__ void set_flag(WsHeader* h, uint32_t bit) { atomicOr(&h->flags, bit); }

@@ -56,6 +56,7 @@ struct Geo {
     int tx0, ty0, tw, ntiles;  // tile rectangle (ntiles = 0: not rendered)
 };
 
+// Every rounding is explicit (see quat_to_rot_rn).
 __device__ __forceinline__ void project(const Cam& cam, const float mu[3], const float M[9], float o,
                                         Geo& g)
 {
@@ -63,65 +64,68 @@ __device__ __forceinline__ void project(const Cam& cam, const float mu[3], const
     float t[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
-        t[r] = cam.R[3 * r] * mu[0] + cam.R[3 * r + 1] * mu[1] + cam.R[3 * r + 2] * mu[2] + cam.t[r];
+        t[r] = __fadd_rn(__fmaf_rn(cam.R[3 * r + 2], mu[2],
+                                   __fmaf_rn(cam.R[3 * r + 1], mu[1], __fmul_rn(cam.R[3 * r], mu[0]))),
+                         cam.t[r]);
     if (!(t[2] > cam.near_plane)) return;
-    const float iz = 1.0f / t[2];
+    const float iz = __fdiv_rn(1.0f, t[2]);
     // Eq. 2: J (2x3) and T2 = J Rcam; M2 = T2 M, Sigma2D = M2 M2^T
-    const float j00 = cam.fx * iz, j02 = -cam.fx * t[0] * iz * iz;
-    const float j11 = cam.fy * iz, j12 = -cam.fy * t[1] * iz * iz;
+    const float j00 = __fmul_rn(cam.fx, iz), j02 = -__fmul_rn(__fmul_rn(__fmul_rn(cam.fx, t[0]), iz), iz);
+    const float j11 = __fmul_rn(cam.fy, iz), j12 = -__fmul_rn(__fmul_rn(__fmul_rn(cam.fy, t[1]), iz), iz);
     float T2[6];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        T2[c] = j00 * cam.R[c] + j02 * cam.R[6 + c];
-        T2[3 + c] = j11 * cam.R[3 + c] + j12 * cam.R[6 + c];
+        T2[c] = __fmaf_rn(j02, cam.R[6 + c], __fmul_rn(j00, cam.R[c]));
+        T2[3 + c] = __fmaf_rn(j12, cam.R[6 + c], __fmul_rn(j11, cam.R[3 + c]));
     }
     float M2[6];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            M2[3 * r + c] = T2[3 * r] * M[c] + T2[3 * r + 1] * M[3 + c] + T2[3 * r + 2] * M[6 + c];
-    const float ca = M2[0] * M2[0] + M2[1] * M2[1] + M2[2] * M2[2];
-    const float cb = M2[0] * M2[3] + M2[1] * M2[4] + M2[2] * M2[5];
-    const float cc = M2[3] * M2[3] + M2[4] * M2[4] + M2[5] * M2[5];
+            M2[3 * r + c] = __fmaf_rn(T2[3 * r + 2], M[6 + c],
+                                      __fmaf_rn(T2[3 * r + 1], M[3 + c], __fmul_rn(T2[3 * r], M[c])));
+    const float ca = __fmaf_rn(M2[2], M2[2], __fmaf_rn(M2[1], M2[1], __fmul_rn(M2[0], M2[0])));
+    const float cb = __fmaf_rn(M2[2], M2[5], __fmaf_rn(M2[1], M2[4], __fmul_rn(M2[0], M2[3])));
+    const float cc = __fmaf_rn(M2[5], M2[5], __fmaf_rn(M2[4], M2[4], __fmul_rn(M2[3], M2[3])));
     // Cauchy-Binet: det(M2 M2^T) = sum of squared 2x2 minors (no cancellation)
-    const float m01 = M2[0] * M2[4] - M2[1] * M2[3];
-    const float m02 = M2[0] * M2[5] - M2[2] * M2[3];
-    const float m12 = M2[1] * M2[5] - M2[2] * M2[4];
-    const float det2 = m01 * m01 + m02 * m02 + m12 * m12;
+    const float m01 = __fmaf_rn(M2[0], M2[4], -__fmul_rn(M2[1], M2[3]));
+    const float m02 = __fmaf_rn(M2[0], M2[5], -__fmul_rn(M2[2], M2[3]));
+    const float m12 = __fmaf_rn(M2[1], M2[5], -__fmul_rn(M2[2], M2[4]));
+    const float det2 = __fmaf_rn(m12, m12, __fmaf_rn(m02, m02, __fmul_rn(m01, m01)));
     if (!(det2 >= kDetMin)) return;
-    const float da = ca + kDilation, dc = cc + kDilation;
-    const float detd = det2 + kDilation * (ca + cc) + kDilation * kDilation;
+    const float da = __fadd_rn(ca, kDilation), dc = __fadd_rn(cc, kDilation);
+    const float detd = __fadd_rn(__fmaf_rn(kDilation, __fadd_rn(ca, cc), det2), kDilation * kDilation);
     // conic = (Sigma2D + 0.3 I)^-1 in eigen form: the dilated covariance has
     // eigenvalues lmax = (da + dc)/2 + r, r = sqrt(((ca - cc)/2)^2 + cb^2) (no
     // cancellation) and lmin = detd / lmax.  Its major axis makes the angle th
     // with cos 2th = h / r, sin 2th = cb / r (h = (ca - cc)/2); the half-angle
     // identities give (cos th, sin th) with the larger one from a sum of
     // non-negative terms and the other from sin 2th = 2 sin th cos th.
-    const float h = 0.5f * (ca - cc);
-    const float r = sqrtf(h * h + cb * cb);
-    const float lmax = 0.5f * (da + dc) + r;
-    g.e.ls = 1.0f / lmax;
-    g.e.lb = lmax / detd;
+    const float h = __fmul_rn(0.5f, __fsub_rn(ca, cc));
+    const float r = __fsqrt_rn(__fmaf_rn(h, h, __fmul_rn(cb, cb)));
+    const float lmax = __fadd_rn(__fmul_rn(0.5f, __fadd_rn(da, dc)), r);
+    g.e.ls = __fdiv_rn(1.0f, lmax);
+    g.e.lb = __fdiv_rn(lmax, detd);
     if (!(r > 0.0f)) {
         g.e.c = 1.0f;
         g.e.s = 0.0f;
     } else if (h >= 0.0f) {
-        g.e.c = sqrtf((r + h) / (2.0f * r));
-        g.e.s = cb / (2.0f * r * g.e.c);
+        g.e.c = __fsqrt_rn(__fdiv_rn(__fadd_rn(r, h), __fmul_rn(2.0f, r)));
+        g.e.s = __fdiv_rn(cb, __fmul_rn(__fmul_rn(2.0f, r), g.e.c));
     } else {
-        g.e.s = copysignf(sqrtf((r - h) / (2.0f * r)), cb);
-        g.e.c = cb / (2.0f * r * g.e.s);
+        g.e.s = copysignf(__fsqrt_rn(__fdiv_rn(__fsub_rn(r, h), __fmul_rn(2.0f, r))), cb);
+        g.e.c = __fdiv_rn(cb, __fmul_rn(__fmul_rn(2.0f, r), g.e.s));
     }
-    g.mx = cam.fx * t[0] * iz + cam.cx;
-    g.my = cam.fy * t[1] * iz + cam.cy;
+    g.mx = __fmaf_rn(__fmul_rn(cam.fx, t[0]), iz, cam.cx);
+    g.my = __fmaf_rn(__fmul_rn(cam.fy, t[1]), iz, cam.cy);
     g.depth = t[2];
     g.k = opacity_k(o);
-    const float ex = sqrtf(g.k * da), ey = sqrtf(g.k * dc);
-    const float u0 = fmaxf(ceilf(g.mx - ex - 0.5f), 0.0f);
-    const float u1 = fminf(floorf(g.mx + ex - 0.5f), (float)(cam.width - 1));
-    const float v0 = fmaxf(ceilf(g.my - ey - 0.5f), 0.0f);
-    const float v1 = fminf(floorf(g.my + ey - 0.5f), (float)(cam.height - 1));
+    const float ex = __fsqrt_rn(__fmul_rn(g.k, da)), ey = __fsqrt_rn(__fmul_rn(g.k, dc));
+    const float u0 = fmaxf(ceilf(__fsub_rn(__fsub_rn(g.mx, ex), 0.5f)), 0.0f);
+    const float u1 = fminf(floorf(__fsub_rn(__fadd_rn(g.mx, ex), 0.5f)), (float)(cam.width - 1));
+    const float v0 = fmaxf(ceilf(__fsub_rn(__fsub_rn(g.my, ey), 0.5f)), 0.0f);
+    const float v1 = fminf(floorf(__fsub_rn(__fadd_rn(g.my, ey), 0.5f)), (float)(cam.height - 1));
     if (!(u0 <= u1 && v0 <= v1)) return;
     g.tx0 = (int)u0 / kTile;
     g.ty0 = (int)v0 / kTile;
@@ -140,28 +144,44 @@ __device__ __forceinline__ uint32_t count_tiles(const Geo& g, bool has, int widt
     uint32_t count = 0;
     keep = 0;
     const bool big = has && g.ntiles > kBigRect;
+    TileCull cull;
+    if (has) cull = make_cull(g.mx, g.my, g.e, g.k);
     if (has && !big) {
-        for (int t = 0; t < g.ntiles; ++t)
-            if (tile_keep(g.mx, g.my, g.e, g.k, g.tx0 + t % g.tw, g.ty0 + t / g.tw, width, height))
-                keep |= 1u << t;
+        int t = 0;
+        for (int ty = g.ty0; t < g.ntiles; ++ty)
+            for (int tx = g.tx0; tx < g.tx0 + g.tw; ++tx, ++t)
+                if (tile_keep(cull, tx, ty, width, height)) keep |= 1u << t;
         count = __popc(keep);
     }
     unsigned bigmask = __ballot_sync(0xffffffffu, big);
     while (bigmask) {
         const int src = __ffs(bigmask) - 1;
         bigmask &= bigmask - 1;
-        const float mx = __shfl_sync(0xffffffffu, g.mx, src), my = __shfl_sync(0xffffffffu, g.my, src);
-        EigenConic e;
-        e.lb = __shfl_sync(0xffffffffu, g.e.lb, src);
-        e.ls = __shfl_sync(0xffffffffu, g.e.ls, src);
-        e.c = __shfl_sync(0xffffffffu, g.e.c, src);
-        e.s = __shfl_sync(0xffffffffu, g.e.s, src);
-        const float k = __shfl_sync(0xffffffffu, g.k, src);
+        TileCull c;
+        c.mx = __shfl_sync(0xffffffffu, cull.mx, src);
+        c.my = __shfl_sync(0xffffffffu, cull.my, src);
+        c.k = __shfl_sync(0xffffffffu, cull.k, src);
+        c.rx = __shfl_sync(0xffffffffu, cull.rx, src);
+        c.ry = __shfl_sync(0xffffffffu, cull.ry, src);
+        c.e.lb = __shfl_sync(0xffffffffu, cull.e.lb, src);
+        c.e.ls = __shfl_sync(0xffffffffu, cull.e.ls, src);
+        c.e.c = __shfl_sync(0xffffffffu, cull.e.c, src);
+        c.e.s = __shfl_sync(0xffffffffu, cull.e.s, src);
         const int tx0 = __shfl_sync(0xffffffffu, g.tx0, src), ty0 = __shfl_sync(0xffffffffu, g.ty0, src);
         const int tw = __shfl_sync(0xffffffffu, g.tw, src), nt = __shfl_sync(0xffffffffu, g.ntiles, src);
+        // lane's tile t = lane + 32 j at (col, row) of the rectangle, stepped without divisions
+        const int step_r = 32 / tw, step_c = 32 - step_r * tw;
+        int row = lane / tw, col = lane - row * tw;
         uint32_t part = 0;
-        for (int t = lane; t < nt; t += 32)
-            part += tile_keep(mx, my, e, k, tx0 + t % tw, ty0 + t / tw, width, height);
+        for (int t = lane; t < nt; t += 32) {
+            part += tile_keep(c, tx0 + col, ty0 + row, width, height);
+            col += step_c;
+            row += step_r;
+            if (col >= tw) {
+                col -= tw;
+                ++row;
+            }
+        }
         part = __reduce_add_sync(0xffffffffu, part);
         if (lane == src) count = part;
     }
@@ -197,10 +217,10 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
         mu[2] = means[3 * i + 2];
         const float4 q4 = *reinterpret_cast<const float4*>(quats + 4 * i);  // rows are 16-byte aligned
         const float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
-        const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-        const float inv = qn > 0.f ? 1.0f / qn : 0.f;
+        const float qn = __fsqrt_rn(__fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmaf_rn(qx, qx, __fmul_rn(qw, qw)))));
+        const float inv = qn > 0.f ? __fdiv_rn(1.0f, qn) : 0.f;
         float Rq[9];
-        quat_to_rot(qw * inv, qx * inv, qy * inv, qz * inv, Rq);
+        quat_to_rot_rn(__fmul_rn(qw, inv), __fmul_rn(qx, inv), __fmul_rn(qy, inv), __fmul_rn(qz, inv), Rq);
         const float s0 = __expf(log_scales[3 * i]), s1 = __expf(log_scales[3 * i + 1]),
                     s2 = __expf(log_scales[3 * i + 2]);
 #pragma unroll
@@ -209,7 +229,7 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
             M[3 * r + 1] = Rq[3 * r + 1] * s1;
             M[3 * r + 2] = Rq[3 * r + 2] * s2;
         }
-        o = 1.0f / (1.0f + __expf(-opac[i]));
+        o = __fdiv_rn(1.0f, __fadd_rn(1.0f, __expf(-opac[i])));
         ok = qn >= kQNormMin;
         if (MOTION) {
             vel[0] = mo.vel[3 * i]; vel[1] = mo.vel[3 * i + 1]; vel[2] = mo.vel[3 * i + 2];
@@ -224,8 +244,8 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
         if (MOTION) {
             const float dt = cam.time - t0;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) mv[a] = mu[a] + vel[a] * dt;
-            ov = o * temporal_weight(dt, mo.inv_var);
+            for (int a = 0; a < 3; ++a) mv[a] = __fmaf_rn(vel[a], dt, mu[a]);
+            ov = __fmul_rn(o, temporal_weight(dt, mo.inv_var));
         }
         Geo g;
         g.ntiles = 0;
@@ -246,21 +266,24 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
                                   (unsigned short)(g.tx0 + g.tw - 1),
                                   (unsigned short)(g.ty0 + g.ntiles / g.tw - 1));
             // SH colour from the view direction, streamed from memory
-            float d0 = mv[0] - cam.pos[0], d1 = mv[1] - cam.pos[1], d2 = mv[2] - cam.pos[2];
-            const float il = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-            d0 *= il; d1 *= il; d2 *= il;
+            float d0 = __fsub_rn(mv[0], cam.pos[0]), d1 = __fsub_rn(mv[1], cam.pos[1]),
+                  d2 = __fsub_rn(mv[2], cam.pos[2]);
+            const float il = rsqrtf(__fmaf_rn(d2, d2, __fmaf_rn(d1, d1, __fmul_rn(d0, d0))));
+            d0 = __fmul_rn(d0, il);
+            d1 = __fmul_rn(d1, il);
+            d2 = __fmul_rn(d2, il);
             float Y[16];
-            sh_basis(d0, d1, d2, sh_degree, Y);
-            float r0 = 0.5f + Y[0] * to_f32(sh_dc[3 * i]);
-            float r1 = 0.5f + Y[0] * to_f32(sh_dc[3 * i + 1]);
-            float r2 = 0.5f + Y[0] * to_f32(sh_dc[3 * i + 2]);
+            sh_basis_rn(d0, d1, d2, sh_degree, Y);
+            float r0 = __fmaf_rn(Y[0], to_f32(sh_dc[3 * i]), 0.5f);
+            float r1 = __fmaf_rn(Y[0], to_f32(sh_dc[3 * i + 1]), 0.5f);
+            float r2 = __fmaf_rn(Y[0], to_f32(sh_dc[3 * i + 2]), 0.5f);
             const SHT* rest = sh_rest + 45 * i;
 #pragma unroll
             for (int kk = 1; kk < 16; ++kk) {
                 if (kk < ncoef) {
-                    r0 += Y[kk] * to_f32(rest[3 * (kk - 1)]);
-                    r1 += Y[kk] * to_f32(rest[3 * (kk - 1) + 1]);
-                    r2 += Y[kk] * to_f32(rest[3 * (kk - 1) + 2]);
+                    r0 = __fmaf_rn(Y[kk], to_f32(rest[3 * (kk - 1)]), r0);
+                    r1 = __fmaf_rn(Y[kk], to_f32(rest[3 * (kk - 1) + 1]), r1);
+                    r2 = __fmaf_rn(Y[kk], to_f32(rest[3 * (kk - 1) + 2]), r2);
                 }
             }
             uint32_t bits = 8u;  // visible
@@ -470,12 +493,12 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
     while (bigmask) {
         const int src = __ffs(bigmask) - 1;
         bigmask &= bigmask - 1;
-        const float mx = __shfl_sync(0xffffffffu, q0.x, src), my = __shfl_sync(0xffffffffu, q0.y, src);
-        const EigenConic e = eigen_from_stored(__shfl_sync(0xffffffffu, q0.z, src),
-                                               __shfl_sync(0xffffffffu, q0.w, src),
-                                               __shfl_sync(0xffffffffu, q1.x, src),
-                                               __shfl_sync(0xffffffffu, q1.y, src));
-        const float k = opacity_k(__shfl_sync(0xffffffffu, q1.z, src));
+        const TileCull c = make_cull(__shfl_sync(0xffffffffu, q0.x, src), __shfl_sync(0xffffffffu, q0.y, src),
+                                     eigen_from_stored(__shfl_sync(0xffffffffu, q0.z, src),
+                                                       __shfl_sync(0xffffffffu, q0.w, src),
+                                                       __shfl_sync(0xffffffffu, q1.x, src),
+                                                       __shfl_sync(0xffffffffu, q1.y, src)),
+                                     opacity_k(__shfl_sync(0xffffffffu, q1.z, src)));
         const int sv = __shfl_sync(0xffffffffu, v, src);
         const uint32_t sid = (uint32_t)__shfl_sync(0xffffffffu, (unsigned long long)i, src);
         const int tx0 = __shfl_sync(0xffffffffu, (int)r.x, src), ty0 = __shfl_sync(0xffffffffu, (int)r.y, src);
@@ -483,10 +506,13 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
         uint64_t soff = __shfl_sync(0xffffffffu, (unsigned long long)off, src);
         const int width = vt.width[sv], height = vt.height[sv], tx_n = vt.tiles_x[sv];
         const uint32_t toff = (uint32_t)vt.tile_off[sv];
+        // lane's tile base + lane at (col, row) of the rectangle, stepped without divisions
+        const int step_r = 32 / stw, step_c = 32 - step_r * stw;
+        int row = lane / stw, col = lane - row * stw;
         for (int base = 0; base < snt; base += 32) {
             const int t = base + lane;
-            const int tx = tx0 + t % stw, ty = ty0 + t / stw;
-            const bool keep = t < snt && tile_keep(mx, my, e, k, tx, ty, width, height);
+            const int tx = tx0 + col, ty = ty0 + row;
+            const bool keep = t < snt && tile_keep(c, tx, ty, width, height);
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             const uint64_t pos = soff + __popc(m & ((1u << lane) - 1u));
             if (keep && pos < (uint64_t)k_max) {
@@ -494,6 +520,12 @@ duplicate_kernel(int64_t n, ViewTable vt, const Screen* __restrict__ screen,
                 vals[pos] = sid;
             }
             soff += __popc(m);
+            col += step_c;
+            row += step_r;
+            if (col >= stw) {
+                col -= stw;
+                ++row;
+            }
         }
     }
 }
