@@ -224,8 +224,8 @@ __device__ __forceinline__ bool tile_keep(const TileCull& c, int tx, int ty, int
     return best <= c.k;
 }
 
-// One evaluated fragment: alpha = min(0.99, o G), G = exp(power), the
-// offset from the mean and whether the clamp is active.
+// One evaluated fragment: alpha = min(0.99, o G), G = exp(power) and
+// whether the clamp is active.
 struct Frag {
     float alpha, G;
     bool clamped;
