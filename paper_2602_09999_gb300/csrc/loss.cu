@@ -9,7 +9,9 @@
 // D2 = dS/dE[xy] are per-pixel maps and * is the same zero-padded blur.
 //
 //   ssim_fwd : per 32x16 block of pixels and channel: the block with its
-//              5-pixel halo for x and y in shared memory, horizontal then
+//              5-pixel halo for x and y in shared memory (the next channel's
+//              halo copied in asynchronously, into a second buffer, while
+//              this channel computes), horizontal then
 //              vertical blur of the five moments, SSIM, D0..D2 written to the
 //              workspace maps, per-CTA sums of |x - y| and S.
 //   ssim_bwd : per 32x16 block and channel: halo block of D0..D2, blur, and
@@ -63,13 +65,28 @@ __device__ __forceinline__ void cta_sum2(float& a, float& b, float (*red)[kLY], 
     __syncthreads();
 }
 
+// 4-byte asynchronous copy global -> shared (cp.async), zero-filled when
+// `in` is false (no byte of src is then read).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool in)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(in ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Waits until at most N committed copy groups of this thread are in flight.
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __global__ void __launch_bounds__(kLX * kLY)
 ssim_fwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
                 const float* __restrict__ targets, float* __restrict__ maps,
                 double* __restrict__ partials)
 {
-    __shared__ __align__(8) float sx[kSpanY][kSpanXP];
-    __shared__ __align__(8) float sy[kSpanY][kSpanXP];
+    __shared__ __align__(8) float sxb[2][kSpanY][kSpanXP];
+    __shared__ __align__(8) float syb[2][kSpanY][kSpanXP];
     __shared__ float hs[5][kSpanY][kLTW + 1];
     __shared__ float red[2][kLY];
     const int b = blockIdx.x;
@@ -82,20 +99,34 @@ ssim_fwd_kernel(ViewTable vt, LossGrid lg, const float* __restrict__ images,
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kLX + tx;
     const int px = x0 + tx;
     float l1 = 0.f, ssum = 0.f;
-    for (int ch = 0; ch < 3; ++ch) {
-        const float* X = images + 3 * vt.pix_off[v] + ch * P;
-        const float* Yt = targets + 3 * vt.pix_off[v] + ch * P;
-        __syncthreads();
+    // channel c's halo into buffer c & 1, in flight while channel c - 1 computes
+    auto prefetch = [&](int c) {
+        const float* X = images + 3 * vt.pix_off[v] + c * P;
+        const float* Yt = targets + 3 * vt.pix_off[v] + c * P;
         for (int r = ty; r < kSpanY; r += kLY) {
             const int gy = y0 - kHalo + r;
-            for (int c = tx; c < kSpanX; c += kLX) {
-                const int gx = x0 - kHalo + c;
+            for (int cc = tx; cc < kSpanX; cc += kLX) {
+                const int gx = x0 - kHalo + cc;
                 const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-                sx[r][c] = in ? X[(int64_t)gy * W + gx] : 0.f;
-                sy[r][c] = in ? Yt[(int64_t)gy * W + gx] : 0.f;
+                const int64_t o = in ? (int64_t)gy * W + gx : 0;
+                cp_async4(&sxb[c & 1][r][cc], X + o, in);
+                cp_async4(&syb[c & 1][r][cc], Yt + o, in);
             }
         }
+        cp_async_commit();
+    };
+    prefetch(0);
+    for (int ch = 0; ch < 3; ++ch) {
+        __syncthreads();  // iteration ch - 1 is done with buffer (ch + 1) & 1
+        if (ch + 1 < 3) {
+            prefetch(ch + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();
+        float (*sx)[kSpanXP] = sxb[ch & 1];
+        float (*sy)[kSpanXP] = syb[ch & 1];
         // horizontal blur: each thread two adjacent columns of one row, from
         // the 12 pixels both windows cover (six 8-byte loads per image)
         for (int r = tid >> 4; r < kSpanY; r += kLX * kLY / 16) {
