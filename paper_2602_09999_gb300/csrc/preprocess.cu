@@ -207,7 +207,7 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
                       const SHT* __restrict__ sh_rest, const fgs_camera* __restrict__ cams,
                       ViewTable vt, Screen* __restrict__ screen, TileRect* __restrict__ rects,
                       uint32_t* __restrict__ local_off, uint32_t* __restrict__ block_sum,
-                      int nblk, Motion mo)
+                      int nblk, Motion mo, int ahead)
 {
     // two buffers, alternating by view: a warp still reading view v's totals
     // cannot be overtaken by a write of view v + 2 (view v + 1's barriers lie
@@ -215,6 +215,19 @@ preprocess_fwd_kernel(int64_t n, int sh_degree, const float* __restrict__ means,
     __shared__ uint32_t warp_tot[2][kPreBlock / 32];
     const int64_t i = (int64_t)blockIdx.x * kPreBlock + threadIdx.x;
     const bool valid = i < n;
+    {
+        // the parameter lines of the block `ahead` blocks on (half a wave of
+        // resident CTAs), asked of L2 so that its loads find them there
+        // (0.171 -> 0.167 ms at 3M Gaussians); 44 lines of 128 bytes
+        const int64_t j0 = ((int64_t)blockIdx.x + ahead) * kPreBlock;
+        const int t = threadIdx.x;
+        if (j0 + kPreBlock <= n) {
+            if (t < 12) prefetch_l2(means + 3 * j0 + 32 * t);
+            else if (t < 28) prefetch_l2(quats + 4 * j0 + 32 * (t - 12));
+            else if (t < 40) prefetch_l2(log_scales + 3 * j0 + 32 * (t - 28));
+            else if (t < 44) prefetch_l2(opac + j0 + 32 * (t - 40));
+        }
+    }
     float mu[3] = {0.f, 0.f, 0.f}, M[9], o = 0.f, vel[3] = {0.f, 0.f, 0.f}, t0 = 0.f;
     bool ok = false;
     if (valid) {
@@ -1139,10 +1152,14 @@ static cudaError_t launch_pre_fwd_t(int64_t n, int deg, const fgs_params* p, con
     const int nblk = (int)((n + kPreBlock - 1) / kPreBlock);
     const Motion mo = motion_of(p);
     auto kernel = mo.vel ? preprocess_fwd_kernel<SHT, true> : preprocess_fwd_kernel<SHT, false>;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ahead = (sms > 0 ? sms : 1) * 4;  // half of the 8 resident CTAs per SM
     kernel<<<nblk, kPreBlock, 0, st>>>(
         n, deg, (const float*)p->data[0], (const float*)p->data[1], (const float*)p->data[2],
         (const float*)p->data[3], (const SHT*)p->data[4], (const SHT*)p->data[5], cams, vt, screen,
-        rects, local_off, block_sum, nblk, mo);
+        rects, local_off, block_sum, nblk, mo, ahead);
     profile_mark(st, "preprocess_fwd");
     return cudaGetLastError();
 }
