@@ -554,9 +554,9 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewTable& vt, int64_t n, c
                 // transmittance in front of the entry; 1 - alpha >= 0.01, so the
                 // approximate divide (2 ulp) is in range
                 const float Ti = __fdividef(T[k], 1.0f - f.alpha);
-                // g . (c - A), shared by dL/dalpha and the update of the colour
-                // behind, A <- A + alpha (c - A)
-                const float gc = g0[k] * e.rgbo.x + g1[k] * e.rgbo.y + g2[k] * e.rgbo.z - S[k];
+                // g . (c - A) = g . c - S as three FMAs from -S, shared by
+                // dL/dalpha and the update of the colour behind, A <- A + alpha (c - A)
+                const float gc = fmaf(g0[k], e.rgbo.x, fmaf(g1[k], e.rgbo.y, fmaf(g2[k], e.rgbo.z, -S[k])));
                 const float dalpha = Ti * gc;
                 frag_moments(f, u, w, dalpha, f.alpha * Ti, g0[k], g1[k], g2[k], d);
                 S[k] += f.alpha * gc;
