@@ -234,8 +234,8 @@ typedef struct fgs_workspace_layout {
  * 256-byte aligned device memory and passes the same layout (host struct)
  * to the forward, loss and backward calls that share the workspace; each
  * call checks it against its cameras.  Returns FGS_ERR_* on bad arguments
- * (n outside 1..2^31-1, n_views outside 1..FGS_MAX_VIEWS, a camera size
- * outside 1..65535, k_max outside 0..2^31-1). */
+ * (n outside 1..2^31-1, n_views outside 1..FGS_MAX_VIEWS, n_views * n
+ * above 2^32-1, a camera size outside 1..65535, k_max outside 0..2^31-1). */
 int fgs_workspace_size(int64_t n, const fgs_camera *cams_host, int32_t n_views, int64_t k_max,
                        fgs_workspace_layout *out_host);
 

@@ -174,6 +174,9 @@ static int layout_impl(int64_t n, const fgs_camera* cams, int32_t nv, int64_t k_
     if (rc != FGS_OK) return rc;
     memset(L, 0, sizeof(*L));
     const int64_t vn = (int64_t)nv * n;
+    // a rendered (view, Gaussian) pair travels through the depth sort as
+    // the 32-bit value view * n + index
+    if (vn > 0xffffffffll) return FGS_ERR_SHAPE;
     const int64_t nblk = (n + kPreBlock - 1) / kPreBlock;
     size_t sz[FGS_WS_NUM_SLOTS];
     sz[FGS_WS_HEADER] = sizeof(WsHeader);

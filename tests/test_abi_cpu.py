@@ -80,13 +80,22 @@ def test_workspace_layout(lib):
 
 
 @pytest.mark.parametrize("n,nv,k,code", [(0, 1, 10, -2), (2 ** 31, 1, 10, -2), (10, 0, 10, -7),
-                                         (10, 17, 10, -7), (10, 1, -1, -9)])
+                                         (10, 17, 10, -7), (10, 1, -1, -9),
+                                         # view * n + index must fit the 32-bit pair value
+                                         (2 ** 28, 16, 10, -2)])
 def test_workspace_argument_errors(lib, n, nv, k, code):
     cams = [scenes.look_at((0, 0, 4), (0, 0, 0), 64, 64)] * max(nv, 1)
     ca = B.camera_array(cams)
     with pytest.raises(B.FGSError) as e:
         B.fgs_workspace_size(n, ca, nv, k)
     assert e.value.code == code
+
+
+def test_largest_pair_count_accepted(lib):
+    # n_views * n = 2^32 - 16: the layout is host arithmetic, nothing is allocated
+    cams = [scenes.look_at((0, 0, 4), (0, 0, 0), 64, 64)] * 16
+    L = B.fgs_workspace_size(2 ** 28 - 1, B.camera_array(cams), 16, 10)
+    assert L.bytes[B.FGS_WS_DEPTH_KEYS] == 4 * 16 * (2 ** 28 - 1)
 
 
 def test_bad_camera_size_rejected(lib):
