@@ -374,7 +374,8 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewTable& vt, int64_t n, c
                 Frag f;
                 float u, w;
                 if (((wm >> k) & 1u) && eval_frag(tm.lx[k], tm.ly[k], e, f, u, w) && !done[k]) {
-                    const float test = __fmul_rn(T[k], __fsub_rn(1.0f, f.alpha));
+                    // T (1 - alpha) in one rounding
+                    const float test = __fmaf_rn(-f.alpha, T[k], T[k]);
                     if (test < kTMin) {
                         done[k] = true;
                         continue;
@@ -756,7 +757,7 @@ blend_bwd_pg_kernel(ViewTable vt, int64_t n, const uint2* __restrict__ ranges,
             if (has && pos <= sg.last[k] && ((bmask >> ((lx >> 3) | ((ly >> 2) << 1))) & 1u) &&
                 eval_frag((float)lx, (float)ly, e, f, u, w)) {
                 // the forward's update, rounding for rounding
-                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, f.alpha));
+                const float Tn = __fmaf_rn(-f.alpha, T, T);
                 const float wT = __fmul_rn(f.alpha, T);
                 C0 = __fmaf_rn(wT, e.rgbo.x, C0);
                 C1 = __fmaf_rn(wT, e.rgbo.y, C1);
