@@ -189,7 +189,20 @@ typedef struct fgs_tuning {
     int32_t tile_sort_digit_bits;        /* radix digit of the tile sort: 8 or 11 (0: 8); the
                                             layout's sorted_in_alt must then be the parity of
                                             ceil(sort_bits / digit bits) */
+    int32_t duplicate_order;             /* FGS_DUPLICATE_STRIDED (default) or FGS_DUPLICATE_SPLIT */
 } fgs_tuning;
+
+/* How the duplication step (Sec. 3.2 "Sorting": one key per kept tile of
+ * every rendered Gaussian, in depth order) assigns rendered pairs to
+ * threads; the emitted instances are the same either way.  STRIDED: one
+ * kernel, lane l of warp w taking pair l * W + w, so the near splats with
+ * large rectangles (first in depth order) spread over all warps, each
+ * culled by its whole warp; a warp's stores land in 32 far-apart runs.
+ * SPLIT: consecutive threads take consecutive pairs (one contiguous run of
+ * stores per warp) and list the large rectangles, which a second kernel
+ * culls one warp per entry; it pays where the instance arrays exceed L2
+ * (batches of many views). */
+enum { FGS_DUPLICATE_STRIDED = 0, FGS_DUPLICATE_SPLIT = 1 };
 
 /* Order of the blend backward (the same gradients up to float32 rounding).
  * PER_PIXEL: one thread per pixel walks its tile's list back to front,

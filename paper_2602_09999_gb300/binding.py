@@ -70,7 +70,8 @@ class fgs_tuning(ctypes.Structure):
     _fields_ = [("blend_pixels_per_thread", ctypes.c_int32), ("blend_batch", ctypes.c_int32),
                 ("blend_schedule", ctypes.c_int32), ("blend_backward", ctypes.c_int32),
                 ("backward_pixels_per_thread", ctypes.c_int32), ("backward_batch", ctypes.c_int32),
-                ("depth_sort_digit_bits", ctypes.c_int32), ("tile_sort_digit_bits", ctypes.c_int32)]
+                ("depth_sort_digit_bits", ctypes.c_int32), ("tile_sort_digit_bits", ctypes.c_int32),
+                ("duplicate_order", ctypes.c_int32)]
 
 
 BLEND_CONFIGS = ((1, 256), (2, 128), (2, 256), (4, 64), (4, 128), (4, 256))
@@ -78,6 +79,8 @@ SORT_DIGIT_BITS = (8, 11)   # radix digit widths of the render path's two sorts
 FGS_SCHEDULE_QUEUE, FGS_SCHEDULE_GRID = 0, 1
 BLEND_SCHEDULES = (FGS_SCHEDULE_QUEUE, FGS_SCHEDULE_GRID)
 FGS_BACKWARD_PER_PIXEL, FGS_BACKWARD_PER_GAUSSIAN = 0, 1
+FGS_DUPLICATE_STRIDED, FGS_DUPLICATE_SPLIT = 0, 1
+DUPLICATE_ORDERS = (FGS_DUPLICATE_STRIDED, FGS_DUPLICATE_SPLIT)
 
 
 class fgs_workspace_layout(ctypes.Structure):

@@ -17,7 +17,7 @@ cudaError_t launch_compact_visible(int64_t n, const ViewTable& vt, const Screen*
 cudaError_t launch_sorted_duplicate(int64_t n, const ViewTable& vt, const Screen* screen,
                                     const TileRect* rects, const uint32_t* svals, uint32_t* sorted_off,
                                     uint32_t* sorted_block, WsHeader* hdr, int64_t k_max, uint32_t* keys,
-                                    uint32_t* vals, cudaStream_t st);
+                                    uint32_t* vals, uint32_t* big, int order, cudaStream_t st);
 int64_t count_scan_blocks(int64_t pairs);
 cudaError_t launch_preprocess_bwd(int64_t n, int deg, const fgs_params* p, const fgs_camera* cams,
                                   const ViewTable& vt, const Screen* screen, const TileRect* rects,
@@ -252,6 +252,8 @@ static int check_layout(void* ws, const fgs_workspace_layout* L, const fgs_camer
     // where the tile sort leaves its result follows from its digit width
     if (L->sorted_in_alt != (radix_passes(L->sort_bits, digit_bits(L->tuning.tile_sort_digit_bits)) & 1))
         return FGS_ERR_WORKSPACE;
+    if (L->tuning.duplicate_order != FGS_DUPLICATE_STRIDED && L->tuning.duplicate_order != FGS_DUPLICATE_SPLIT)
+        return FGS_ERR_ARG;
     if (L->tuning.blend_backward != FGS_BACKWARD_PER_PIXEL &&
         L->tuning.blend_backward != FGS_BACKWARD_PER_GAUSSIAN)
         return FGS_ERR_ARG;
@@ -349,10 +351,12 @@ int fgs_render_forward(void* ws, const fgs_workspace_layout* L, const fgs_params
                                     hist, true, digit_bits(L->tuning.depth_sort_digit_bits), st, &e);
     if (e != cudaSuccess) return FGS_ERR_CUDA;
     // stage 2: their instances, emitted in depth order, stably by tile id
+    // (the depth keys are spent: their slot holds the split duplication's
+    // list of large rectangles)
     if ((rc = cuda_rc(launch_sorted_duplicate(n, vt, screen, rects, dalt ? dvals_alt : dvals,
                                               slot<uint32_t>(ws, L, FGS_WS_SORTED_OFF),
                                               slot<uint32_t>(ws, L, FGS_WS_SORTED_BLOCK), hdr, L->k_max,
-                                              keys, vals, st))) != FGS_OK)
+                                              keys, vals, dkeys, L->tuning.duplicate_order, st))) != FGS_OK)
         return rc;
     const uint32_t* k_dev = &hdr->counters[0];
     const int alt = radix_sort_u32(keys, vals, keys_alt, vals_alt, L->k_max, k_dev, L->sort_bits, hist,

@@ -58,15 +58,16 @@ def _store(table):
     os.replace(tmp, CACHE)
 
 
-CHOICE_FIELDS = 7
+CHOICE_FIELDS = 8
 
 
 def apply(layout, choice):
     """choice = (pixels per thread, batch[, schedule[, backward pixels per
     thread, backward batch[, depth-sort digit bits, tile-sort digit
-    bits]]]); a backward pair of (0, 0) or none means the forward's pair,
-    digit bits of 0 or none mean 8.  The layout's sorted_in_alt follows the
-    tile sort's pass count."""
+    bits[, duplication order]]]]); a backward pair of (0, 0) or none means
+    the forward's pair, digit bits of 0 or none mean 8, no duplication order
+    means the strided one.  The layout's sorted_in_alt follows the tile
+    sort's pass count."""
     layout.tuning.blend_pixels_per_thread = int(choice[0])
     layout.tuning.blend_batch = int(choice[1])
     layout.tuning.blend_schedule = int(choice[2]) if len(choice) > 2 else B.FGS_SCHEDULE_QUEUE
@@ -78,6 +79,7 @@ def apply(layout, choice):
     layout.tuning.tile_sort_digit_bits = int(digits[1])
     rb = int(digits[1]) or 8
     layout.sorted_in_alt = ((int(layout.sort_bits) + rb - 1) // rb) & 1
+    layout.tuning.duplicate_order = int(choice[7]) if len(choice) > 7 else B.FGS_DUPLICATE_STRIDED
 
 
 def label(choice) -> str:
@@ -87,6 +89,8 @@ def label(choice) -> str:
         text += f"+bwd{choice[3]}x{choice[4]}"
     if len(choice) > 6 and (choice[5] or choice[6]):
         text += f"+sort{choice[5] or 8}/{choice[6] or 8}"
+    if len(choice) > 7 and choice[7] == B.FGS_DUPLICATE_SPLIT:
+        text += "+dupsplit"
     return text
 
 
@@ -144,6 +148,11 @@ def autotune(trainer, reps: int = 3, use_cache: bool = True, configs=None):
     for cfg in sorts:
         time_choice(cfg)
     best = min([best] + sorts, key=lambda c: timings[label(c)])
+    # then the duplication order, everything else fixed
+    best = tuple(best[:7]) + (B.FGS_DUPLICATE_STRIDED,)
+    split = tuple(best[:7]) + (B.FGS_DUPLICATE_SPLIT,)
+    time_choice(split)
+    best = min([best, split], key=lambda c: timings[label(c)])
     apply(trainer.rast.layout, best)
     if use_cache:
         table[key] = {"choice": list(best), "ms": timings}

@@ -40,10 +40,11 @@ def test_library_exports_every_declared_function(lib):
 def test_struct_sizes_match_c(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "fastergs.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(fgs_camera),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(fgs_camera),'
                    ' sizeof(fgs_params), sizeof(fgs_workspace_layout), sizeof(fgs_adam_state),'
                    ' offsetof(fgs_adam_state, step_size), offsetof(fgs_workspace_layout, tuning),'
-                   ' offsetof(fgs_tuning, backward_pixels_per_thread), offsetof(fgs_tuning, backward_batch));'
+                   ' offsetof(fgs_tuning, backward_pixels_per_thread), offsetof(fgs_tuning, backward_batch),'
+                   ' offsetof(fgs_tuning, duplicate_order));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -55,7 +56,8 @@ def test_struct_sizes_match_c(tmp_path):
                                      B.fgs_adam_state.step_size.offset,
                                      B.fgs_workspace_layout.tuning.offset,
                                      B.fgs_tuning.backward_pixels_per_thread.offset,
-                                     B.fgs_tuning.backward_batch.offset]
+                                     B.fgs_tuning.backward_batch.offset,
+                                     B.fgs_tuning.duplicate_order.offset]
 
 
 def test_workspace_layout(lib):
@@ -290,8 +292,31 @@ def test_tuning_choice_encoding(lib):
     second = [best + tuple(pb) for pb in B.BLEND_CONFIGS if tuple(pb) != best[:2]]
     third = [tuple(pb) + (0, 4, 64) for pb in B.BLEND_CONFIGS if tuple(pb) != best[:2]]
     sorts = [best + (0, 0, d, t) for d in B.SORT_DIGIT_BITS for t in B.SORT_DIGIT_BITS if (d, t) != (8, 8)]
-    labels = [tune.label(c) for c in first + second + third + sorts]
+    dup = [best + (0, 0, 0, 0, B.FGS_DUPLICATE_SPLIT)]
+    labels = [tune.label(c) for c in first + second + third + sorts + dup]
     assert len(set(labels)) == len(labels)
+    assert tune.label(best + (0, 0, 0, 0, B.FGS_DUPLICATE_STRIDED)) == tune.label(best)
+
+
+def test_duplicate_order_choice(lib):
+    """The duplication order: strided by default, split when the choice's
+    eighth field asks for it; any other value is refused on the host."""
+    from paper_2602_09999_gb300 import tune
+    cam = B.camera_array([scenes.tiny_camera(100, 70)])
+    layout = B.fgs_workspace_size(1000, cam, 1, 64_000)
+    assert layout.tuning.duplicate_order == B.FGS_DUPLICATE_STRIDED
+    tune.apply(layout, (2, 128, 0, 0, 0, 0, 0, B.FGS_DUPLICATE_SPLIT))
+    assert layout.tuning.duplicate_order == B.FGS_DUPLICATE_SPLIT
+    assert tune.label((2, 128, 0, 0, 0, 0, 0, 1)) == "2x128/queue+dupsplit"
+    tune.apply(layout, (2, 128, 0, 0, 0, 8, 8))
+    assert layout.tuning.duplicate_order == B.FGS_DUPLICATE_STRIDED
+    fake_ws = ctypes.c_void_p(1 << 20)
+    p = B.params_struct(1000, [1 << 40] * 6, [B.FGS_F32] * 6)
+    for bad in (2, -1):
+        layout.tuning.duplicate_order = bad
+        with pytest.raises(B.FGSError) as e:
+            B.fgs_render_forward(fake_ws, layout, p, 3, cam, 1 << 30, (0, 0, 0), 1 << 31, None)
+        assert e.value.code == -9, bad
 
 
 def test_sort_digit_width_choice(lib):

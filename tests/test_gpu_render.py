@@ -528,10 +528,11 @@ def test_autotuner_picks_a_supported_configuration(tmp_path, monkeypatch):
     assert tuple(choice[:2]) in B.BLEND_CONFIGS and choice[2] in B.BLEND_SCHEDULES
     assert tuple(choice[3:5]) == (0, 0) or tuple(choice[3:5]) in B.BLEND_CONFIGS
     assert tuple(choice[5:7]) == (0, 0) or all(d in B.SORT_DIGIT_BITS for d in choice[5:7])
+    assert choice[7] in B.DUPLICATE_ORDERS
     # every choice, then the backward's other pairs, then the forward's, then
-    # the sort digit widths
+    # the sort digit widths, then the split duplication order
     assert len(ms) == (len(B.BLEND_CONFIGS) * len(B.BLEND_SCHEDULES) + 2 * (len(B.BLEND_CONFIGS) - 1)
-                       + len(B.SORT_DIGIT_BITS) ** 2 - 1)
+                       + len(B.SORT_DIGIT_BITS) ** 2 - 1 + 1)
     again, _ = tune.autotune(tr)           # cached
     assert tuple(again) == tuple(choice)
 
@@ -558,6 +559,41 @@ def test_sort_digit_widths_give_the_same_lists(digits):
             if name in ("keys", "vals"):
                 a, b = a[:K], b[:K]
             assert torch.equal(a, b), (digits, name)
+
+
+def test_duplicate_orders_give_the_same_lists():
+    """The duplication order changes speed only: the split order (consecutive
+    entries per warp, the large rectangles listed and culled one warp per
+    entry by a second kernel) emits the instances the strided order does, so
+    the sorted lists, ranges, image and per-pixel state are bit-identical: on
+    a two-view batch, on a close view where many rectangles are large (the
+    list must not be empty), and when the instances overflow k_max (the kept
+    prefix is the same)."""
+    from paper_2602_09999_gb300 import tune
+    outdoor = scenes.outdoor_scene(60_000, seed=31)
+    cases = [(outdoor, scenes.orbit_cameras(2, 640, 480, radius=6.0, seed=32), None, False),
+             (scenes.small_scene(20_000, seed=33, log_scale_mean=-1.5), [scenes.tiny_camera(320, 240)], None,
+              True),
+             (outdoor, scenes.orbit_cameras(1, 640, 480, radius=6.0, seed=34), 20_000, False)]
+    for params, cams, k_max, many_big in cases:
+        rast, views, t, images = gpu_forward(params, cams, k_max=k_max)
+        flags, inst = rast.error()
+        assert bool(flags & B.FGS_FLAG_CAPACITY) == (k_max is not None)
+        ref = [x.clone() for x in rast.sorted_lists()] + [images.clone()] + [x.clone() for x in rast.per_pixel()]
+        tune.apply(rast.layout, (2, 128, 0, 0, 0, 0, 0, B.FGS_DUPLICATE_SPLIT))
+        images2 = torch.zeros_like(images)
+        rast.forward(T.params_struct(t), 3, (0.0, 0.0, 0.0), images2)
+        torch.cuda.synchronize()
+        # the workspace header's third counter: the split order's list length
+        n_big = int(rast.ws[24:28].view(torch.int32).item())
+        if many_big:
+            assert n_big > 100, n_big
+        got = list(rast.sorted_lists()) + [images2] + list(rast.per_pixel())
+        K = min(inst, rast.k_max)
+        for a, b, name in zip(ref, got, ("keys", "vals", "ranges", "image", "T", "n_contrib")):
+            if name in ("keys", "vals"):
+                a, b = a[:K], b[:K]
+            assert torch.equal(a, b), (len(cams), k_max, name)
 
 
 def test_unsupported_configuration_is_rejected():
