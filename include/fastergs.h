@@ -148,7 +148,9 @@ enum fgs_ws_slot {
     FGS_WS_TILE_QUEUE,  /* uint32 [4 + total_tiles]: work-queue counters (forward head and
                            exits, backward head and exits), then every tile of every view in
                            descending order of list length (written by each forward) */
-    FGS_WS_DEPTH_KEYS,  /* uint32 [n_views*n]: depth bits of the rendered (view, Gaussian) pairs */
+    FGS_WS_DEPTH_KEYS,  /* uint32 [n_views*n]: depth bits of the rendered (view, Gaussian) pairs;
+                           after the depth sort, the split duplication order's list of pairs
+                           with large rectangles */
     FGS_WS_DEPTH_VALS,  /* uint32 [n_views*n]: view * n + Gaussian index of those pairs */
     FGS_WS_DEPTH_KEYS_ALT, /* uint32 [n_views*n]: depth-sort ping-pong buffers */
     FGS_WS_DEPTH_VALS_ALT,
