@@ -11,8 +11,8 @@ with that choice fixed (the backward's best pair can differ from the
 forward's: it sums each entry's gradients over the warp once per entry, so
 more pixels per thread spread that cost over more pixels), then the
 forward's other pairs with the backward's fixed, then the radix digit width
-(8 or 11 bits) of the depth sort and of the tile sort, keeps the fastest, and
-caches it in a JSON file keyed by GPU name, Gaussian count and pixel count
+(8 or 11 bits) of the depth sort and of the tile sort, then the duplication
+order (strided or split), keeps the fastest, and caches it in a JSON file keyed by GPU name, Gaussian count and pixel count
 (rounded to powers of two), view count, backward order and storage types,
 so later runs of the same shape skip the search.
 """
